@@ -1,0 +1,662 @@
+/*
+ * FP64 CPU oracle for the neural-BRDF evaluation of "Real-Time Neural
+ * Appearance Models" (Zeltner et al., ACM TOG 2024).
+ *
+ * TEST INFRASTRUCTURE.  Only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg load this library.  It shares no code with the CUDA path:
+ * everything below is written out plainly, one query at a time, in double
+ * precision, following the paper's description:
+ *
+ *   f(x, wi, wo) ~ g(z(x), T wi, T wo; theta)                  (Eq. 3)
+ *   z(x): hierarchical latent texture, level from the footprint area,
+ *         one of the two neighbouring levels picked by Russian roulette
+ *         (stochastic) or both blended (trilinear), bilinear inside a level
+ *                                                              (Sec. 4.1)
+ *   T: rows (t, b, n) of a shading frame decoded from z        (Eq. 4, Sec. 4.2)
+ *      with b = n x t / |n x t|                                (Sec. 9)
+ *   g: MLP with ReLU hidden layers and a linear RGB output     (Sec. 7, Sec. 8)
+ *   FP16 parameters by post-training quantisation              (Sec. 5.2)
+ *   training loss: L1 in log space                             (Sec. 5.2)
+ *
+ * Readings where the paper is silent (texel centres, level sizes, addressing,
+ * lod clamp and tie-break, frame MLP form and degenerate frames, decoder input
+ * order, activations, loss form, FP8 quantisation) are listed in the design
+ * notes and restated at each function below.
+ *
+ * Pins: tests/test_oracle_pins.py checks every function here against closed
+ * forms, invariants, library routines and brute force on tiny inputs.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_C 8          /* latent channels (Sec. 4: eight-dimensional code) */
+#define ORC_MAXW 256     /* widest layer the oracle accepts */
+#define ORC_MAXL 8       /* most decoder layers */
+
+/* ------------------------------------------------------------------------- */
+/* number formats                                                             */
+/* ------------------------------------------------------------------------- */
+
+/* IEEE 754 binary16 -> double: sign, 5-bit exponent (bias 15), 10-bit
+ * fraction; exponent 0 is subnormal (no implicit one), 31 is inf/NaN. */
+double orc_f16_to_f64(uint16_t h) {
+  int s = (h >> 15) & 1, e = (h >> 10) & 31, f = h & 1023;
+  double v;
+  if (e == 0) v = ldexp((double)f, -24);
+  else if (e == 31) v = f ? NAN : INFINITY;
+  else v = ldexp((double)(1024 + f), e - 25);
+  return s ? -v : v;
+}
+
+/* Round a double to the nearest binary16 value, ties to even; overflow past
+ * the largest finite value (65504) rounds to infinity as IEEE prescribes. */
+uint16_t orc_f64_to_f16(double x) {
+  if (isnan(x)) return 0x7e00;
+  uint16_t sign = signbit(x) ? 0x8000 : 0;
+  double a = fabs(x);
+  if (a >= 65520.0) return sign | 0x7c00; /* halfway to 2^16 and beyond */
+  int e;
+  frexp(a, &e);           /* a = m 2^e, m in [0.5, 1) */
+  int ex = e - 1;         /* a in [2^ex, 2^(ex+1)) */
+  if (ex < -14) ex = -14; /* subnormal spacing 2^-24 */
+  double q = ldexp(a, 10 - ex); /* units of the spacing 2^(ex-10) */
+  double r = nearbyint(q);      /* current rounding mode: ties to even */
+  double v = ldexp(r, ex - 10);
+  if (v == 0.0) return sign;
+  /* re-encode the exact value v */
+  int e2;
+  frexp(v, &e2);
+  int E = e2 - 1;
+  if (E < -14) return sign | (uint16_t)ldexp(v, 24); /* subnormal */
+  if (E > 15) return sign | 0x7c00;
+  uint16_t frac = (uint16_t)(ldexp(v, 10 - E) - 1024.0);
+  return sign | (uint16_t)((E + 15) << 10) | frac;
+}
+
+double orc_round_f16(double x) { return orc_f16_to_f64(orc_f64_to_f16(x)); }
+
+/* OCP 8-bit floating point, E4M3FN variant: bias 7, no infinities, only
+ * S.1111.111 is NaN, largest finite magnitude 448 = 1.75 * 2^8. */
+double orc_e4m3_to_f64(uint8_t b) {
+  int s = (b >> 7) & 1, e = (b >> 3) & 15, f = b & 7;
+  double v;
+  if (e == 15 && f == 7) v = NAN;
+  else if (e == 0) v = ldexp((double)f, -9);
+  else v = ldexp((double)(8 + f), e - 10);
+  return s ? -v : v;
+}
+
+/* Round to nearest E4M3FN, ties to even, saturating at +-448 (the
+ * "satfinite" conversion).  NaN maps to the NaN code 0x7f. */
+uint8_t orc_f64_to_e4m3(double x) {
+  if (isnan(x)) return 0x7f;
+  uint8_t sign = signbit(x) ? 0x80 : 0;
+  double a = fabs(x);
+  if (a >= 448.0) return sign | 0x7e;
+  int e;
+  frexp(a, &e);
+  int ex = e - 1;
+  if (ex < -6) ex = -6; /* subnormal spacing 2^-9 */
+  double r = nearbyint(ldexp(a, 3 - ex));
+  double v = ldexp(r, ex - 3);
+  if (v >= 448.0) return sign | 0x7e;
+  if (v == 0.0) return sign;
+  int e2;
+  frexp(v, &e2);
+  int E = e2 - 1;
+  if (E < -6) return sign | (uint8_t)ldexp(v, 9);
+  uint8_t frac = (uint8_t)(ldexp(v, 3 - E) - 8.0);
+  return sign | (uint8_t)((E + 7) << 3) | frac;
+}
+
+double orc_round_e4m3(double x) { return orc_e4m3_to_f64(orc_f64_to_e4m3(x)); }
+
+/* Per-layer FP8 weight quantisation (beyond the paper, which names lower
+ * precision as future work in Sec. 5.2): s = absmax(W) / 448 in FP32, each
+ * code = E4M3(W / s) with the division done in FP32, the precision in which
+ * the quantised code is decided.  Writes s and the dequantised weights. */
+void orc_quantize_e4m3_layer(const float* W, int64_t n, float* scale_out, double* deq_out) {
+  float amax = 0.0f;
+  for (int64_t i = 0; i < n; ++i) {
+    float a = fabsf(W[i]);
+    if (a > amax) amax = a;
+  }
+  float s = amax > 0.0f ? amax / 448.0f : 1.0f;
+  *scale_out = s;
+  for (int64_t i = 0; i < n; ++i) {
+    float q = W[i] / s;
+    deq_out[i] = orc_round_e4m3((double)q) * (double)s;
+  }
+}
+
+/* ------------------------------------------------------------------------- */
+/* model description                                                         */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t W0, H0, L, C;     /* finest level size, level count, channels (8) */
+  int32_t latent_f16;       /* 1: pyramid holds binary16 bit patterns, 0: float32 */
+  int32_t address;          /* 0: wrap (repeat), 1: clamp to edge */
+  int32_t filter;           /* 0: trilinear, 1: stochastic (Russian roulette) */
+  int32_t out_cosine;       /* 1: multiply the output by max(0, wi.z) */
+  int32_t frame_hidden;     /* hidden width of the frame MLP, 0: T = I */
+  int32_t n_layers;         /* decoder linear layers */
+  int32_t widths[ORC_MAXL + 1]; /* decoder widths, widths[0] = 14 */
+  int32_t act_round;        /* decoder operand rounding: 0 none, 1 fp16, 2 fp8 */
+  const void* pyramid;      /* levels packed finest first, [texel][C] */
+  const double* frame_params; /* Wf1[h][8], bf1[h], Wf2[6][h], bf2[6] */
+  const double* dec_params;   /* per layer W[out][in] then b[out] */
+  const double* act_scale;    /* act_round == 2: input scale s_l of each decoder layer */
+} orc_model;
+
+typedef struct {
+  const float *u, *v, *lod, *wix, *wiy, *wiz, *wox, *woy, *woz, *xi;
+} orc_queries;
+
+/* Level sizes: level l is max(1, W0 >> l) by max(1, H0 >> l) texels, levels
+ * stored one after the other starting with the finest. */
+static int64_t level_offset(const orc_model* m, int l, int* Wl, int* Hl) {
+  int64_t off = 0;
+  for (int k = 0; k < l; ++k) {
+    int w = m->W0 >> k, h = m->H0 >> k;
+    off += (int64_t)(w > 0 ? w : 1) * (h > 0 ? h : 1);
+  }
+  int w = m->W0 >> l, h = m->H0 >> l;
+  *Wl = w > 0 ? w : 1;
+  *Hl = h > 0 ? h : 1;
+  return off;
+}
+
+static double texel(const orc_model* m, int64_t idx, int c) {
+  if (m->latent_f16) return orc_f16_to_f64(((const uint16_t*)m->pyramid)[idx * m->C + c]);
+  return (double)((const float*)m->pyramid)[idx * m->C + c];
+}
+
+/* Integer texel coordinate under the addressing mode: wrap repeats the level
+ * with period n, clamp holds the edge texel. */
+static int64_t address(const orc_model* m, double i, int n) {
+  if (m->address == 1) {
+    if (i < 0) return 0;
+    if (i > n - 1) return n - 1;
+    return (int64_t)i;
+  }
+  double r = i - (double)n * floor(i / (double)n);
+  int64_t k = (int64_t)r;
+  if (k >= n) k -= n; /* guards r == n after rounding */
+  return k;
+}
+
+/* One bilinear tap set at level l: texel centres sit at (i + 1/2) / W_l, so
+ * the continuous texel coordinate is x = u W_l - 1/2; the four texels around
+ * it get the usual bilinear weights.  Returns the taps' indices and weights. */
+static void bilinear_taps(const orc_model* m, int l, double u, double v,
+                          int64_t idx[4], double w[4]) {
+  int Wl, Hl;
+  int64_t off = level_offset(m, l, &Wl, &Hl);
+  double x = u * Wl - 0.5, y = v * Hl - 0.5;
+  double x0 = floor(x), y0 = floor(y);
+  double fx = x - x0, fy = y - y0;
+  int64_t ix0 = address(m, x0, Wl), ix1 = address(m, x0 + 1.0, Wl);
+  int64_t iy0 = address(m, y0, Hl), iy1 = address(m, y0 + 1.0, Hl);
+  idx[0] = off + iy0 * Wl + ix0; w[0] = (1.0 - fx) * (1.0 - fy);
+  idx[1] = off + iy0 * Wl + ix1; w[1] = fx * (1.0 - fy);
+  idx[2] = off + iy1 * Wl + ix0; w[2] = (1.0 - fx) * fy;
+  idx[3] = off + iy1 * Wl + ix1; w[3] = fx * fy;
+}
+
+/* Level selection (Sec. 4.1): the level index may be fractional.  Reading:
+ * l = clamp(lod, 0, L-1) (NaN -> 0), l0 = floor(l), l1 = min(l0+1, L-1),
+ * t = l - l0.  Trilinear blends the two bilinear fetches with weights 1-t, t;
+ * the stochastic variant takes l1 when xi < t and l0 otherwise, so that its
+ * expectation over xi ~ U[0,1) is the trilinear result.
+ * Fills up to 8 taps; returns the tap count. */
+static int latent_taps(const orc_model* m, double u, double v, double lod, double xi,
+                       int64_t idx[8], double w[8]) {
+  double l = lod;
+  if (!(l > 0.0)) l = 0.0; /* also maps NaN to 0 */
+  if (l > m->L - 1) l = m->L - 1;
+  double l0 = floor(l);
+  double t = l - l0;
+  int il0 = (int)l0;
+  int il1 = il0 + 1 < m->L ? il0 + 1 : m->L - 1;
+  if (m->filter == 1) {
+    int lv = (xi < t) ? il1 : il0;
+    bilinear_taps(m, lv, u, v, idx, w);
+    return 4;
+  }
+  bilinear_taps(m, il0, u, v, idx, w);
+  bilinear_taps(m, il1, u, v, idx + 4, w + 4);
+  for (int k = 0; k < 4; ++k) {
+    w[k] *= (1.0 - t);
+    w[k + 4] *= t;
+  }
+  return 8;
+}
+
+static void latent(const orc_model* m, double u, double v, double lod, double xi, double z[ORC_C]) {
+  int64_t idx[8];
+  double w[8];
+  int nt = latent_taps(m, u, v, lod, xi, idx, w);
+  for (int c = 0; c < ORC_C; ++c) z[c] = 0.0;
+  for (int k = 0; k < nt; ++k)
+    for (int c = 0; c < ORC_C; ++c) z[c] += w[k] * texel(m, idx[k], c);
+}
+
+/* ------------------------------------------------------------------------- */
+/* shading frame (Sec. 4.2, Eq. 4; bitangent from Sec. 9)                     */
+/* ------------------------------------------------------------------------- */
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Tangent orthogonal to a unit n when the decoded tangent is unusable:
+ * the branch-free orthonormal basis of Duff et al. (JCGT 6(1), 2017). */
+static void basis_tangent(const double n[3], double t[3]) {
+  double s = copysign(1.0, n[2]);
+  double a = -1.0 / (s + n[2]);
+  double b = n[0] * n[1] * a;
+  t[0] = 1.0 + s * n[0] * n[0] * a;
+  t[1] = s * b;
+  t[2] = -s * n[0];
+}
+
+typedef struct {
+  double n[3], t[3], b[3];
+  double nraw_len, tp_len, c_len, s; /* |n_raw|, |t'|, |n x t|, t_raw.n */
+  int n_degenerate, t_degenerate;
+} frame_state;
+
+/* r = (n_raw, t_raw).  Reading of the frame step: normalise n; Gram-Schmidt
+ * the tangent against n and normalise; b = n x t / |n x t|.  Degenerate
+ * cases: |n_raw| < 1e-20 gives n = (0,0,1); |t'| <= 1e-6 |t_raw| takes the
+ * tangent from n alone (Duff et al.).  T's rows are (t, b, n). */
+static void build_frame(const double r[6], frame_state* f) {
+  const double* nr = r;
+  const double* tr = r + 3;
+  double nl = sqrt(dot3(nr, nr));
+  f->nraw_len = nl;
+  f->n_degenerate = !(nl >= 1e-20);
+  if (f->n_degenerate) {
+    f->n[0] = 0; f->n[1] = 0; f->n[2] = 1;
+  } else {
+    for (int k = 0; k < 3; ++k) f->n[k] = nr[k] / nl;
+  }
+  double s = dot3(tr, f->n);
+  f->s = s;
+  double tp[3];
+  for (int k = 0; k < 3; ++k) tp[k] = tr[k] - s * f->n[k];
+  double tpl = sqrt(dot3(tp, tp));
+  double trl = sqrt(dot3(tr, tr));
+  f->tp_len = tpl;
+  f->t_degenerate = !(tpl > 1e-6 * trl);
+  if (f->t_degenerate) basis_tangent(f->n, f->t);
+  else for (int k = 0; k < 3; ++k) f->t[k] = tp[k] / tpl;
+  double c[3];
+  cross3(f->n, f->t, c);
+  double cl = sqrt(dot3(c, c));
+  f->c_len = cl;
+  for (int k = 0; k < 3; ++k) f->b[k] = c[k] / cl;
+}
+
+/* ------------------------------------------------------------------------- */
+/* one query, forward, keeping what the backward pass needs                   */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  int64_t idx[8];
+  double w[8];
+  int ntaps;
+  double z[ORC_C];        /* filtered latent */
+  double hf_pre[ORC_MAXW];
+  double hf[ORC_MAXW];
+  double r[6];
+  frame_state fr;
+  double wi[3], wo[3];
+  double pre[ORC_MAXL][ORC_MAXW]; /* decoder pre-activations */
+  double act[ORC_MAXL + 1][ORC_MAXW]; /* decoder layer inputs, act[0] = x */
+  double y[3];
+  double cosf;            /* output factor: 1 or max(0, wi.z) */
+} trace;
+
+/* Rounding of the decoder's MMA operands, emulated in FP64 so that the oracle
+ * can evaluate the reduced-precision forms of the method step by step:
+ * act_round 1 rounds every decoder-layer input to binary16 (FP16 inference,
+ * Sec. 5.2: FP16 parameters at load; the MMA operands are FP16, Sec. 7.2);
+ * act_round 2 quantises decoder-layer l's input a to E4M3(a / s_l) s_l with a
+ * static per-layer scale s_l, the code decided in FP32.  The frame path is
+ * never rounded: it is evaluated at FP32 accuracy in every precision. */
+static double round_act(const orc_model* m, double x, int dec_layer) {
+  if (m->act_round == 1) return orc_round_f16(x);
+  if (m->act_round == 2) {
+    float s = (float)m->act_scale[dec_layer];
+    float inv = 1.0f / s;
+    float q = (float)x * inv;
+    return orc_round_e4m3((double)q) * (double)s;
+  }
+  return x;
+}
+
+static void forward(const orc_model* m, const orc_queries* q, int64_t i, trace* tr) {
+  double u = q->u[i], v = q->v[i], lod = q->lod[i];
+  double xi = q->xi ? q->xi[i] : 0.0;
+  tr->ntaps = latent_taps(m, u, v, lod, xi, tr->idx, tr->w);
+  for (int c = 0; c < ORC_C; ++c) tr->z[c] = 0.0;
+  for (int k = 0; k < tr->ntaps; ++k)
+    for (int c = 0; c < ORC_C; ++c) tr->z[c] += tr->w[k] * texel(m, tr->idx[k], c);
+  tr->wi[0] = q->wix[i]; tr->wi[1] = q->wiy[i]; tr->wi[2] = q->wiz[i];
+  tr->wo[0] = q->wox[i]; tr->wo[1] = q->woy[i]; tr->wo[2] = q->woz[i];
+
+  double wi_l[3], wo_l[3];
+  if (m->frame_hidden > 0) {
+    int H = m->frame_hidden;
+    const double* Wf1 = m->frame_params;
+    const double* bf1 = Wf1 + H * ORC_C;
+    const double* Wf2 = bf1 + H;
+    const double* bf2 = Wf2 + 6 * H;
+    for (int j = 0; j < H; ++j) {
+      double s = bf1[j];
+      for (int c = 0; c < ORC_C; ++c) s += Wf1[j * ORC_C + c] * tr->z[c];
+      tr->hf_pre[j] = s;
+      tr->hf[j] = s > 0.0 ? s : 0.0;
+    }
+    for (int j = 0; j < 6; ++j) {
+      double s = bf2[j];
+      for (int k = 0; k < H; ++k) s += Wf2[j * H + k] * tr->hf[k];
+      tr->r[j] = s;
+    }
+    build_frame(tr->r, &tr->fr);
+    wi_l[0] = dot3(tr->fr.t, tr->wi); wi_l[1] = dot3(tr->fr.b, tr->wi); wi_l[2] = dot3(tr->fr.n, tr->wi);
+    wo_l[0] = dot3(tr->fr.t, tr->wo); wo_l[1] = dot3(tr->fr.b, tr->wo); wo_l[2] = dot3(tr->fr.n, tr->wo);
+  } else {
+    for (int k = 0; k < 3; ++k) { wi_l[k] = tr->wi[k]; wo_l[k] = tr->wo[k]; }
+  }
+  /* decoder input order: z0..z7, wi', wo' */
+  double* x = tr->act[0];
+  for (int c = 0; c < ORC_C; ++c) x[c] = round_act(m, tr->z[c], 0);
+  for (int k = 0; k < 3; ++k) {
+    x[ORC_C + k] = round_act(m, wi_l[k], 0);
+    x[ORC_C + 3 + k] = round_act(m, wo_l[k], 0);
+  }
+
+  const double* p = m->dec_params;
+  for (int l = 0; l < m->n_layers; ++l) {
+    int in = m->widths[l], out = m->widths[l + 1];
+    const double* W = p;
+    const double* b = p + (int64_t)in * out;
+    p = b + out;
+    int last = (l == m->n_layers - 1);
+    for (int j = 0; j < out; ++j) {
+      double s = b[j];
+      for (int k = 0; k < in; ++k) s += W[j * in + k] * tr->act[l][k];
+      tr->pre[l][j] = s;
+      if (!last) {
+        tr->act[l + 1][j] = round_act(m, s > 0.0 ? s : 0.0, l + 1);
+      }
+    }
+  }
+  int lastl = m->n_layers - 1;
+  tr->cosf = 1.0;
+  if (m->out_cosine) tr->cosf = tr->wi[2] > 0.0 ? tr->wi[2] : 0.0;
+  for (int c = 0; c < 3; ++c) tr->y[c] = tr->pre[lastl][c] * tr->cosf;
+}
+
+/* ------------------------------------------------------------------------- */
+/* exported batch entry points                                                */
+/* ------------------------------------------------------------------------- */
+void orc_latent_batch(const orc_model* m, const orc_queries* q, int64_t n, double* z_out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double xi = q->xi ? q->xi[i] : 0.0;
+    latent(m, q->u[i], q->v[i], q->lod[i], xi, z_out + i * ORC_C);
+  }
+}
+
+/* T rows (t, b, n) for each r = (n_raw, t_raw); out [n][9]. */
+void orc_frame_batch(const double* r, int64_t n, double* T_out) {
+  for (int64_t i = 0; i < n; ++i) {
+    frame_state f;
+    build_frame(r + i * 6, &f);
+    double* T = T_out + i * 9;
+    for (int k = 0; k < 3; ++k) { T[k] = f.t[k]; T[3 + k] = f.b[k]; T[6 + k] = f.n[k]; }
+  }
+}
+
+/* The decoder MLP alone on given inputs x [n][widths[0]] -> y [n][widths[L]]. */
+void orc_mlp_batch(const orc_model* m, const double* x, int64_t n, double* y_out) {
+  int outw = m->widths[m->n_layers];
+  double a[ORC_MAXW], h[ORC_MAXW];
+  for (int64_t i = 0; i < n; ++i) {
+    for (int k = 0; k < m->widths[0]; ++k) a[k] = x[i * m->widths[0] + k];
+    const double* p = m->dec_params;
+    for (int l = 0; l < m->n_layers; ++l) {
+      int in = m->widths[l], out = m->widths[l + 1];
+      const double* W = p;
+      const double* b = p + (int64_t)in * out;
+      p = b + out;
+      for (int j = 0; j < out; ++j) {
+        double s = b[j];
+        for (int k = 0; k < in; ++k) s += W[j * in + k] * a[k];
+        h[j] = (l < m->n_layers - 1) ? (s > 0.0 ? s : 0.0) : s;
+      }
+      for (int j = 0; j < out; ++j) a[j] = h[j];
+    }
+    for (int c = 0; c < outw; ++c) y_out[i * outw + c] = a[c];
+  }
+}
+
+typedef struct {
+  const orc_model* m;
+  const orc_queries* q;
+  int64_t begin, end;
+  double* out;
+} eval_job;
+
+static void* eval_worker(void* arg) {
+  eval_job* j = (eval_job*)arg;
+  trace* tr = (trace*)malloc(sizeof(trace));
+  for (int64_t i = j->begin; i < j->end; ++i) {
+    forward(j->m, j->q, i, tr);
+    for (int c = 0; c < 3; ++c) j->out[i * 3 + c] = tr->y[c];
+  }
+  free(tr);
+  return NULL;
+}
+
+/* Full evaluation of n queries -> rgb [n][3], split over nthreads. */
+void orc_eval(const orc_model* m, const orc_queries* q, int64_t n, double* rgb_out, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  if (n < 4096) nthreads = 1;
+  pthread_t th[256];
+  eval_job jobs[256];
+  int64_t chunk = (n + nthreads - 1) / nthreads;
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t].m = m; jobs[t].q = q; jobs[t].out = rgb_out;
+    jobs[t].begin = (int64_t)t * chunk;
+    jobs[t].end = jobs[t].begin + chunk < n ? jobs[t].begin + chunk : n;
+    if (jobs[t].begin > n) jobs[t].begin = n;
+  }
+  if (nthreads == 1) { eval_worker(&jobs[0]); return; }
+  for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, eval_worker, &jobs[t]);
+  for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
+}
+
+/* Largest |input| of each decoder layer over a batch (FP64 forward without
+ * rounding): the static per-layer activation ranges for FP8 scales. */
+void orc_decoder_input_absmax(const orc_model* m, const orc_queries* q, int64_t n, double* amax_out) {
+  trace* tr = (trace*)malloc(sizeof(trace));
+  for (int l = 0; l < m->n_layers; ++l) amax_out[l] = 0.0;
+  orc_model mm = *m;
+  mm.act_round = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    forward(&mm, q, i, tr);
+    for (int l = 0; l < m->n_layers; ++l)
+      for (int k = 0; k < m->widths[l]; ++k) {
+        double a = fabs(tr->act[l][k]);
+        if (a > amax_out[l]) amax_out[l] = a;
+      }
+  }
+  free(tr);
+}
+
+/* ------------------------------------------------------------------------- */
+/* training loss (Sec. 5.2: L1 in log space)                                  */
+/* ------------------------------------------------------------------------- */
+/* Reading: L = mean |log(1 + max(g,0)) - log(1 + y)| + 0.01 mean max(-g, 0)
+ * over the n x 3 outputs; the second term keeps a gradient on negative g.
+ * Subgradients: sign(0) = 0, d max(g,0)/dg = 0 at g = 0. */
+double orc_loss(const double* g, const float* y, int64_t n, double* dldg_out) {
+  double acc = 0.0;
+  double inv = 1.0 / (3.0 * (double)n);
+  for (int64_t i = 0; i < 3 * n; ++i) {
+    double gp = g[i] > 0.0 ? g[i] : 0.0;
+    double d = log1p(gp) - log1p((double)y[i]);
+    acc += fabs(d);
+    double grad = 0.0;
+    if (g[i] > 0.0) grad = (d > 0.0 ? 1.0 : (d < 0.0 ? -1.0 : 0.0)) / (1.0 + g[i]);
+    if (g[i] < 0.0) {
+      acc += 0.01 * (-g[i]);
+      grad += -0.01;
+    }
+    if (dldg_out) dldg_out[i] = grad * inv;
+  }
+  return acc * inv;
+}
+
+/* ------------------------------------------------------------------------- */
+/* reverse mode                                                               */
+/* ------------------------------------------------------------------------- */
+/* Gradient of sum_i <dl_dy[i], y_i> with respect to the frame MLP parameters,
+ * the decoder parameters (same layouts as the model's arrays) and the
+ * pyramid ([texel][C]).  Accumulates into the outputs.  Exact derivative of
+ * the forward above (no activation rounding), with two readings: ReLU'(0) = 0,
+ * and no gradient flows through the degenerate-frame fallbacks (a
+ * degenerate n is a constant; the fallback tangent depends on n only). */
+void orc_grad(const orc_model* m, const orc_queries* q, int64_t n, const double* dl_dy,
+              double* g_frame, double* g_dec, double* g_pyr) {
+  trace* tr = (trace*)malloc(sizeof(trace));
+  orc_model mm = *m;
+  mm.act_round = 0;
+  double da[ORC_MAXW], dpre[ORC_MAXW];
+  for (int64_t i = 0; i < n; ++i) {
+    forward(&mm, q, i, tr);
+    int L = m->n_layers;
+    /* output */
+    for (int j = 0; j < m->widths[L]; ++j) dpre[j] = (j < 3 ? dl_dy[i * 3 + j] : 0.0) * tr->cosf;
+    /* decoder layers, last to first; parameter offsets */
+    int64_t offs[ORC_MAXL];
+    int64_t o = 0;
+    for (int l = 0; l < L; ++l) {
+      offs[l] = o;
+      o += (int64_t)m->widths[l] * m->widths[l + 1] + m->widths[l + 1];
+    }
+    for (int l = L - 1; l >= 0; --l) {
+      int in = m->widths[l], out = m->widths[l + 1];
+      const double* W = m->dec_params + offs[l];
+      double* gW = g_dec + offs[l];
+      double* gb = gW + (int64_t)in * out;
+      for (int j = 0; j < out; ++j) {
+        gb[j] += dpre[j];
+        for (int k = 0; k < in; ++k) gW[j * in + k] += dpre[j] * tr->act[l][k];
+      }
+      for (int k = 0; k < in; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < out; ++j) s += W[j * in + k] * dpre[j];
+        da[k] = s;
+      }
+      if (l > 0)
+        for (int k = 0; k < in; ++k) dpre[k] = tr->pre[l - 1][k] > 0.0 ? da[k] : 0.0;
+    }
+    /* da = dL/dx, x = (z, T wi, T wo) */
+    double dz[ORC_C];
+    for (int c = 0; c < ORC_C; ++c) dz[c] = da[c];
+    if (m->frame_hidden > 0) {
+      const double* dwi = da + ORC_C;
+      const double* dwo = da + ORC_C + 3;
+      frame_state* f = &tr->fr;
+      /* rows of T: t, b, n;  x' = T w  =>  dT_row_k += dx'_k * w */
+      double dt[3], db[3], dn[3];
+      for (int k = 0; k < 3; ++k) {
+        dt[k] = dwi[0] * tr->wi[k] + dwo[0] * tr->wo[k];
+        db[k] = dwi[1] * tr->wi[k] + dwo[1] * tr->wo[k];
+        dn[k] = dwi[2] * tr->wi[k] + dwo[2] * tr->wo[k];
+      }
+      /* b = c / |c|, c = n x t */
+      double bdb = dot3(f->b, db), gc[3], tmp[3];
+      for (int k = 0; k < 3; ++k) gc[k] = (db[k] - f->b[k] * bdb) / f->c_len;
+      cross3(f->t, gc, tmp);
+      for (int k = 0; k < 3; ++k) dn[k] += tmp[k];
+      cross3(gc, f->n, tmp);
+      for (int k = 0; k < 3; ++k) dt[k] += tmp[k];
+      double dr[6] = {0, 0, 0, 0, 0, 0};
+      const double* traw = tr->r + 3;
+      if (!f->t_degenerate) {
+        /* t = t' / |t'|, t' = t_raw - (t_raw.n) n */
+        double tdt = dot3(f->t, dt), dtp[3];
+        for (int k = 0; k < 3; ++k) dtp[k] = (dt[k] - f->t[k] * tdt) / f->tp_len;
+        double ndtp = dot3(f->n, dtp);
+        for (int k = 0; k < 3; ++k) {
+          dr[3 + k] += dtp[k] - f->n[k] * ndtp;
+          dn[k] += -ndtp * traw[k] - f->s * dtp[k];
+        }
+      }
+      if (!f->n_degenerate) {
+        double ndn = dot3(f->n, dn);
+        for (int k = 0; k < 3; ++k) dr[k] += (dn[k] - f->n[k] * ndn) / f->nraw_len;
+      }
+      /* frame MLP */
+      int H = m->frame_hidden;
+      const double* Wf1 = m->frame_params;
+      const double* Wf2 = Wf1 + H * ORC_C + H;
+      double* gWf1 = g_frame;
+      double* gbf1 = gWf1 + H * ORC_C;
+      double* gWf2 = gbf1 + H;
+      double* gbf2 = gWf2 + 6 * H;
+      double dh[ORC_MAXW];
+      for (int j = 0; j < 6; ++j) {
+        gbf2[j] += dr[j];
+        for (int k = 0; k < H; ++k) gWf2[j * H + k] += dr[j] * tr->hf[k];
+      }
+      for (int k = 0; k < H; ++k) {
+        double s = 0.0;
+        for (int j = 0; j < 6; ++j) s += Wf2[j * H + k] * dr[j];
+        dh[k] = tr->hf_pre[k] > 0.0 ? s : 0.0;
+      }
+      for (int k = 0; k < H; ++k) {
+        gbf1[k] += dh[k];
+        for (int c = 0; c < ORC_C; ++c) gWf1[k * ORC_C + c] += dh[k] * tr->z[c];
+      }
+      for (int c = 0; c < ORC_C; ++c) {
+        double s = 0.0;
+        for (int k = 0; k < H; ++k) s += Wf1[k * ORC_C + c] * dh[k];
+        dz[c] += s;
+      }
+    }
+    /* z = sum_k w_k texel_k */
+    if (g_pyr)
+      for (int k = 0; k < tr->ntaps; ++k)
+        for (int c = 0; c < ORC_C; ++c) g_pyr[tr->idx[k] * ORC_C + c] += tr->w[k] * dz[c];
+  }
+  free(tr);
+}
+
+/* Hash (FNV-1a) of the on/off pattern of every ReLU a query passes through
+ * (frame hidden layer and decoder hidden layers), one per query.  Finite
+ * difference checks use it to skip parameters whose step crosses a kink. */
+void orc_relu_pattern(const orc_model* m, const orc_queries* q, int64_t n, uint64_t* out) {
+  trace* tr = (trace*)malloc(sizeof(trace));
+  orc_model mm = *m;
+  mm.act_round = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    forward(&mm, q, i, tr);
+    uint64_t h = 1469598103934665603ull;
+    for (int j = 0; j < m->frame_hidden; ++j) h = (h ^ (uint64_t)(tr->hf_pre[j] > 0.0)) * 1099511628211ull;
+    for (int l = 0; l + 1 < m->n_layers; ++l)
+      for (int j = 0; j < m->widths[l + 1]; ++j) h = (h ^ (uint64_t)(tr->pre[l][j] > 0.0)) * 1099511628211ull;
+    out[i] = h;
+  }
+  free(tr);
+}

@@ -1,0 +1,329 @@
+"""Python front end of the FP64 CPU oracle (oracle/nam_oracle.c).
+
+TEST INFRASTRUCTURE: only the tests, the smoke check and the benchmark's
+CPU-baseline leg import this module.  It builds the C library with gcc on
+first use (or from `build()`), and marshals numpy arrays into it.  It never
+imports the CUDA package, and the CUDA package never imports it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nam_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+
+FILTER_TRILINEAR, FILTER_STOCHASTIC = 0, 1
+ADDRESS_WRAP, ADDRESS_CLAMP = 0, 1
+ROUND_NONE, ROUND_FP16, ROUND_FP8 = 0, 1, 2  # decoder MMA operands
+MAXL = 8
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with gcc (plain C, -O2, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Model(C.Structure):
+    _fields_ = [("W0", C.c_int32), ("H0", C.c_int32), ("L", C.c_int32), ("C", C.c_int32),
+                ("latent_f16", C.c_int32), ("address", C.c_int32), ("filter", C.c_int32),
+                ("out_cosine", C.c_int32), ("frame_hidden", C.c_int32), ("n_layers", C.c_int32),
+                ("widths", C.c_int32 * (MAXL + 1)), ("act_round", C.c_int32),
+                ("pyramid", C.c_void_p), ("frame_params", C.c_void_p),
+                ("dec_params", C.c_void_p), ("act_scale", C.c_void_p)]
+
+
+class _Queries(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("u", "v", "lod", "wix", "wiy", "wiz", "wox", "woy", "woz", "xi")]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        d, p, i64, u16, u8 = C.c_double, C.c_void_p, C.c_int64, C.c_uint16, C.c_uint8
+        _lib.orc_f16_to_f64.restype = d; _lib.orc_f16_to_f64.argtypes = [u16]
+        _lib.orc_f64_to_f16.restype = u16; _lib.orc_f64_to_f16.argtypes = [d]
+        _lib.orc_round_f16.restype = d; _lib.orc_round_f16.argtypes = [d]
+        _lib.orc_e4m3_to_f64.restype = d; _lib.orc_e4m3_to_f64.argtypes = [u8]
+        _lib.orc_f64_to_e4m3.restype = u8; _lib.orc_f64_to_e4m3.argtypes = [d]
+        _lib.orc_round_e4m3.restype = d; _lib.orc_round_e4m3.argtypes = [d]
+        _lib.orc_quantize_e4m3_layer.argtypes = [p, i64, p, p]
+        _lib.orc_latent_batch.argtypes = [p, p, i64, p]
+        _lib.orc_frame_batch.argtypes = [p, i64, p]
+        _lib.orc_mlp_batch.argtypes = [p, p, i64, p]
+        _lib.orc_eval.argtypes = [p, p, i64, p, C.c_int]
+        _lib.orc_decoder_input_absmax.argtypes = [p, p, i64, p]
+        _lib.orc_loss.restype = d; _lib.orc_loss.argtypes = [p, p, i64, p]
+        _lib.orc_grad.argtypes = [p, p, i64, p, p, p, p]
+        _lib.orc_relu_pattern.argtypes = [p, p, i64, p]
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+# ----------------------------------------------------------------------------
+# number formats
+# ----------------------------------------------------------------------------
+def f16_bits_to_f64(bits):
+    L = lib()
+    return np.array([L.orc_f16_to_f64(int(b)) for b in np.asarray(bits).ravel()])
+
+
+def round_f16(x):
+    L = lib()
+    x = np.asarray(x, dtype=np.float64)
+    return np.array([L.orc_round_f16(float(v)) for v in x.ravel()]).reshape(x.shape)
+
+
+def f64_to_f16_bits(x):
+    L = lib()
+    x = np.asarray(x, dtype=np.float64)
+    return np.array([L.orc_f64_to_f16(float(v)) for v in x.ravel()], dtype=np.uint16).reshape(x.shape)
+
+
+def e4m3_to_f64(codes):
+    L = lib()
+    return np.array([L.orc_e4m3_to_f64(int(b)) for b in np.asarray(codes).ravel()])
+
+
+def f64_to_e4m3(x):
+    L = lib()
+    x = np.asarray(x, dtype=np.float64)
+    return np.array([L.orc_f64_to_e4m3(float(v)) for v in x.ravel()], dtype=np.uint8).reshape(x.shape)
+
+
+def quantize_e4m3_layer(W):
+    """(scale, dequantised weights) of one layer, codes decided in FP32."""
+    W = np.ascontiguousarray(W, dtype=np.float32)
+    s = np.zeros(1, dtype=np.float32)
+    out = np.zeros(W.shape, dtype=np.float64)
+    lib().orc_quantize_e4m3_layer(_ptr(W), W.size, _ptr(s), _ptr(out))
+    return float(s[0]), out
+
+
+# ----------------------------------------------------------------------------
+# model
+# ----------------------------------------------------------------------------
+class Model:
+    """A neural material as the oracle sees it.
+
+    pyramid: [texels, 8] float16 or float32; frame: None or [(Wf1,bf1),(Wf2,bf2)];
+    decoder: [(W,b), ...] with W [out][in].  `params` selects the parameter
+    values: "master" (as given), "fp16" (each rounded to binary16 by the
+    oracle's own rounding), "fp8" (frame in fp16, decoder weights E4M3 with a
+    per-layer absmax scale, decoder biases in FP32).
+    """
+
+    def __init__(self, W0, H0, L, pyramid, frame, decoder, *, filter=FILTER_TRILINEAR,
+                 address=ADDRESS_WRAP, out_cosine=False, params="master", act_round=ROUND_NONE,
+                 act_scale=None):
+        self.W0, self.H0, self.L = W0, H0, L
+        self.pyramid = np.ascontiguousarray(pyramid)
+        assert self.pyramid.shape[1] == 8
+        f16 = self.pyramid.dtype == np.float16
+        if f16:
+            self._pyr = self.pyramid.view(np.uint16)
+        else:
+            self._pyr = np.ascontiguousarray(self.pyramid, dtype=np.float32)
+        self.frame = frame
+        self.decoder = decoder
+        self.widths = [decoder[0][0].shape[1]] + [W.shape[0] for W, _ in decoder]
+        self.weight_scales = None
+        if frame is not None:
+            fp = np.concatenate([frame[0][0].ravel(), frame[0][1], frame[1][0].ravel(), frame[1][1]])
+            fp = fp.astype(np.float64)
+            if params in ("fp16", "fp8"):
+                fp = round_f16(fp)
+        else:
+            fp = None
+        chunks = []
+        scales = []
+        for W, b in decoder:
+            if params == "fp16":
+                chunks += [round_f16(W.astype(np.float64)).ravel(), round_f16(b.astype(np.float64))]
+            elif params == "fp8":
+                s, Wd = quantize_e4m3_layer(W)
+                scales.append(s)
+                chunks += [Wd.ravel(), b.astype(np.float64)]
+            else:
+                chunks += [W.astype(np.float64).ravel(), b.astype(np.float64)]
+        if params == "fp8":
+            self.weight_scales = scales
+        self.frame_params = fp
+        self.dec_params = np.ascontiguousarray(np.concatenate(chunks))
+        self.act_scale = None if act_scale is None else np.ascontiguousarray(act_scale, dtype=np.float64)
+        s = _Model()
+        s.W0, s.H0, s.L, s.C = W0, H0, L, 8
+        s.latent_f16 = int(f16)
+        s.address = address
+        s.filter = filter
+        s.out_cosine = int(bool(out_cosine))
+        s.frame_hidden = 0 if frame is None else frame[0][0].shape[0]
+        s.n_layers = len(decoder)
+        for i, w in enumerate(self.widths):
+            s.widths[i] = w
+        s.act_round = act_round
+        s.pyramid = self._pyr.ctypes.data
+        s.frame_params = None if fp is None else fp.ctypes.data
+        s.dec_params = self.dec_params.ctypes.data
+        s.act_scale = None if self.act_scale is None else self.act_scale.ctypes.data
+        self._s = s
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        m = w["model"]
+        return cls(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"], **kw)
+
+    def texel_count(self):
+        return self.pyramid.shape[0]
+
+    def n_frame_params(self):
+        return 0 if self.frame_params is None else self.frame_params.size
+
+    def n_dec_params(self):
+        return self.dec_params.size
+
+
+class _QueryView:
+    def __init__(self, q, n):
+        self.arrays = {}
+        for k in _Queries._fields_:
+            name = k[0]
+            a = q.get(name)
+            if a is None:
+                self.arrays[name] = None
+                continue
+            a = np.ascontiguousarray(a, dtype=np.float32)
+            assert a.shape[0] >= n
+            self.arrays[name] = a
+        s = _Queries()
+        for name, a in self.arrays.items():
+            setattr(s, name, None if a is None else a.ctypes.data)
+        self.s = s
+
+
+def _nq(q):
+    return int(q["u"].shape[0])
+
+
+def eval(model: Model, q, nthreads: int | None = None) -> np.ndarray:
+    n = _nq(q)
+    out = np.zeros((n, 3), dtype=np.float64)
+    if n == 0:
+        return out
+    qv = _QueryView(q, n)
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    lib().orc_eval(C.byref(model._s), C.byref(qv.s), n, _ptr(out), nthreads)
+    return out
+
+
+def latent(model: Model, q) -> np.ndarray:
+    n = _nq(q)
+    out = np.zeros((n, 8), dtype=np.float64)
+    qv = _QueryView(q, n)
+    lib().orc_latent_batch(C.byref(model._s), C.byref(qv.s), n, _ptr(out))
+    return out
+
+
+def frame(r) -> np.ndarray:
+    """[n,6] raw (n_raw, t_raw) -> [n,3,3] T with rows t, b, n."""
+    r = np.ascontiguousarray(r, dtype=np.float64).reshape(-1, 6)
+    out = np.zeros((r.shape[0], 9), dtype=np.float64)
+    lib().orc_frame_batch(_ptr(r), r.shape[0], _ptr(out))
+    return out.reshape(-1, 3, 3)
+
+
+def mlp(model: Model, x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0]
+    out = np.zeros((n, model.widths[-1]), dtype=np.float64)
+    lib().orc_mlp_batch(C.byref(model._s), _ptr(x), n, _ptr(out))
+    return out
+
+
+def decoder_input_absmax(model: Model, q) -> np.ndarray:
+    n = _nq(q)
+    out = np.zeros(len(model.decoder), dtype=np.float64)
+    qv = _QueryView(q, n)
+    lib().orc_decoder_input_absmax(C.byref(model._s), C.byref(qv.s), n, _ptr(out))
+    return out
+
+
+def relu_pattern(model: Model, q) -> np.ndarray:
+    """Per-query hash of the on/off state of every ReLU the query passes."""
+    n = _nq(q)
+    out = np.zeros(n, dtype=np.uint64)
+    qv = _QueryView(q, n)
+    lib().orc_relu_pattern(C.byref(model._s), C.byref(qv.s), n, _ptr(out))
+    return out
+
+
+def loss(g, y):
+    """(L, dL/dg) of the log-space L1 loss over [n,3] outputs."""
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    n = g.shape[0]
+    d = np.zeros_like(g)
+    val = lib().orc_loss(_ptr(g), _ptr(y), n, _ptr(d))
+    return val, d
+
+
+def grad(model: Model, q, dl_dy, with_pyramid=True):
+    """Gradients of sum <dl_dy, y> w.r.t. frame params, decoder params, pyramid."""
+    n = _nq(q)
+    dl = np.ascontiguousarray(dl_dy, dtype=np.float64).reshape(n, 3)
+    gf = np.zeros(model.n_frame_params(), dtype=np.float64)
+    gd = np.zeros(model.n_dec_params(), dtype=np.float64)
+    gp = np.zeros((model.texel_count(), 8), dtype=np.float64) if with_pyramid else None
+    qv = _QueryView(q, n)
+    lib().orc_grad(C.byref(model._s), C.byref(qv.s), n, _ptr(dl),
+                   _ptr(gf) if gf.size else None, _ptr(gd), _ptr(gp))
+    return {"frame": gf, "decoder": gd, "pyramid": gp}
+
+
+def split_decoder(model: Model, flat):
+    """Split a flat decoder-parameter vector into [(W, b), ...]."""
+    out, o = [], 0
+    for i in range(len(model.widths) - 1):
+        a, b = model.widths[i], model.widths[i + 1]
+        W = flat[o:o + a * b].reshape(b, a); o += a * b
+        bb = flat[o:o + b]; o += b
+        out.append((W, bb))
+    return out
+
+
+def split_frame(model: Model, flat):
+    H = model.frame[0][0].shape[0]
+    o = 0
+    Wf1 = flat[o:o + H * 8].reshape(H, 8); o += H * 8
+    bf1 = flat[o:o + H]; o += H
+    Wf2 = flat[o:o + 6 * H].reshape(6, H); o += 6 * H
+    bf2 = flat[o:o + 6]
+    return [(Wf1, bf1), (Wf2, bf2)]
+
+
+def relative_error(g, o):
+    """Max and mean of |g - o| / max(|o|, tau), tau = RMS of o over the batch."""
+    g = np.asarray(g, dtype=np.float64)
+    o = np.asarray(o, dtype=np.float64)
+    if o.size == 0:
+        return 0.0, 0.0
+    tau = float(np.sqrt(np.mean(o * o)))
+    tau = max(tau, 1e-30)
+    r = np.abs(g - o) / np.maximum(np.abs(o), tau)
+    return float(r.max()), float(r.mean())
