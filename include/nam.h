@@ -1,0 +1,320 @@
+/*
+ * nam.h -- C ABI of libnam, batched neural-BRDF evaluation on one GPU.
+ *
+ * The operation behind every entry point is the neural BRDF of Zeltner et
+ * al., "Real-Time Neural Appearance Models" (ACM TOG 2024):
+ *
+ *     f(x, wi, wo) ~ g( z(x), T wi, T wo ; theta )                (Eq. 3)
+ *
+ * z(x)  8-channel latent code read from a per-material hierarchical latent
+ *       texture (Sec. 4.1): level from the pixel footprint (the caller passes
+ *       it as `lod`), bilinear inside a level, the two neighbouring levels
+ *       either blended (trilinear) or picked by Russian roulette (stochastic).
+ * T     rows (t, b, n) of a shading frame decoded from z (Sec. 4.2, Eq. 4),
+ *       b = n x t / |n x t| (Sec. 9).  Here one frame from a frame MLP
+ *       8 -> H -> 6 (n_raw, t_raw) with Gram-Schmidt, or the identity.
+ * g     decoder MLP, ReLU hidden layers, linear RGB output (Sec. 7, Sec. 8),
+ *       input order (z0..z7, (T wi)xyz, (T wo)xyz).
+ *
+ * Conventions (hold for every call):
+ *  - Every function returns nam_status: NAM_OK (0) or a negative error code.
+ *    No C++ exception crosses the ABI.  nam_last_error_message() gives a
+ *    thread-local description of the last failure on the calling thread.
+ *  - Handles are opaque.  A context owns its materials; destroying the
+ *    context destroys them.
+ *  - Queries are planar float32 arrays (one per field), in the memory space
+ *    the call names (device for nam_eval, host for nam_eval_host and the
+ *    serving frames).  Outputs are float32 RGB, [n][3] row-major.
+ *  - Directions are unit vectors in the geometric frame (z = normal).
+ *  - Asynchronous calls enqueue on the caller's CUDA stream (a cudaStream_t
+ *    passed as void*, NULL = legacy default stream); outputs are valid after
+ *    that stream is synchronised.  A call that returns an error enqueues
+ *    nothing.
+ *  - Device-side errors (a bounded wait that ran out, a bounds check) are
+ *    recorded in the context and returned by the next synchronous call or by
+ *    nam_check_device_error().
+ */
+#ifndef NAM_H
+#define NAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* status                                                                   */
+/* ------------------------------------------------------------------------ */
+typedef int32_t nam_status;
+enum {
+  NAM_OK = 0,
+  NAM_ERR_INVALID_ARG = -1,   /* a pointer, size or enum is out of range */
+  NAM_ERR_OOM = -2,           /* device or pinned allocation failed */
+  NAM_ERR_BUDGET = -3,        /* resident bytes would exceed the HBM budget */
+  NAM_ERR_NOT_FOUND = -4,     /* unknown handle or ticket */
+  NAM_ERR_BUSY = -5,          /* the serving admission queue is full */
+  NAM_ERR_TIMEOUT = -6,       /* a host or device wait ran past its limit */
+  NAM_ERR_CUDA = -7,          /* a CUDA runtime call failed */
+  NAM_ERR_DEVICE_ASSERT = -8, /* a device-side check failed */
+  NAM_ERR_UNSUPPORTED = -9,   /* a valid but unimplemented combination */
+  NAM_ERR_CANCELLED = -10     /* the ticket was cancelled before it ran */
+};
+
+const char* nam_status_string(nam_status s);
+/* Thread-local description of the last error on this thread ("" if none).
+ * The pointer stays valid until the next nam_* call on this thread. */
+const char* nam_last_error_message(void);
+
+/* ------------------------------------------------------------------------ */
+/* context                                                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct nam_ctx nam_ctx;
+
+typedef struct {
+  int32_t device;             /* CUDA device ordinal */
+  int32_t serve_streams;      /* streams of the serving loop (0 -> 4) */
+  int32_t serve_queue_depth;  /* frames the admission queue holds (0 -> 256) */
+  int32_t reserved0;
+  uint64_t hbm_budget_bytes;  /* cap on resident bytes: materials + serving
+                                 buffers (0 -> no cap) */
+  uint64_t wait_timeout_ns;   /* limit of every device-side wait and of
+                                 nam_wait (0 -> 2 s) */
+} nam_config;
+
+/* Create a context on cfg->device (cfg NULL -> device 0, defaults).  The
+ * calling thread's current device is left unchanged.  Starts no thread until
+ * the first nam_submit. */
+nam_status nam_init(nam_ctx** out, const nam_config* cfg);
+/* Cancel queued serving frames, wait (bounded) for frames on the GPU, stop
+ * the serving thread, free every material and buffer, free the context. */
+nam_status nam_shutdown(nam_ctx* ctx);
+/* Device-side error word of the context: NAM_OK or the first error a kernel
+ * recorded since the last call; clears it.  Synchronises the device. */
+nam_status nam_check_device_error(nam_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* materials                                                                */
+/* ------------------------------------------------------------------------ */
+typedef struct nam_material_s* nam_material;
+
+enum { NAM_LATENT_F32 = 0, NAM_LATENT_F16 = 1 };
+/* Arithmetic of the MLPs.  F32: plain FP32 FMA on CUDA cores, one query per
+ * thread.  F16: parameters quantised to binary16 at creation (post-training
+ * quantisation, Sec. 5.2), decoder layers on tensor cores with FP16 operands
+ * and FP32 accumulation; the frame MLP keeps FP32 accuracy by splitting its
+ * FP16 operands in two.  FP8: as F16 but each decoder layer's weights and
+ * input activations are E4M3 with a per-layer scale (weights: absmax/448 of
+ * the FP32 master; activations: the static scale passed in fp8_act_scale),
+ * FP32 accumulation, FP32 bias. */
+enum { NAM_PREC_F32 = 0, NAM_PREC_F16 = 1, NAM_PREC_FP8 = 2 };
+enum { NAM_FILTER_TRILINEAR = 0, NAM_FILTER_STOCHASTIC = 1 };
+enum { NAM_ADDRESS_WRAP = 0, NAM_ADDRESS_CLAMP = 1 };
+
+#define NAM_MAX_LEVELS 16
+#define NAM_MAX_LAYERS 8
+
+typedef struct {
+  /* latent pyramid (Sec. 4.1): level l is max(1, base_w >> l) x
+   * max(1, base_h >> l) texels, levels stored finest first, texel-major,
+   * 8 channels per texel: pyramid[(offset_l + y * W_l + x) * 8 + c]. */
+  int32_t base_w, base_h;
+  int32_t levels;             /* 1 .. min(NAM_MAX_LEVELS, 1 + log2(max(w,h))) */
+  int32_t channels;           /* must be 8 */
+  int32_t latent_dtype;       /* NAM_LATENT_F32 or NAM_LATENT_F16 */
+  int32_t params_on_device;   /* 1: pyramid and weight pointers are device memory */
+  const void* pyramid;        /* copied at creation */
+
+  /* frame MLP 8 -> frame_hidden -> 6, ReLU hidden, linear out r = (n_raw,
+   * t_raw).  frame_hidden = 0: no frame MLP, T = I (directions are already
+   * local).  Weights FP32, [Wf1 (h x 8), bf1 (h), Wf2 (6 x h), bf2 (6)],
+   * matrices [out][in] row-major. */
+  int32_t frame_hidden;       /* 0 or 16 */
+  int32_t n_layers;           /* decoder linear layers: 3 (two hidden layers) */
+  const float* frame_weights;
+  /* decoder widths[0] = 14, widths[1..n_layers-1] = H (16, 32 or 64, all
+   * equal), widths[n_layers] = 3.  Weights FP32 master values, per layer
+   * W (out x in) then b (out), layers in order. */
+  int32_t widths[NAM_MAX_LAYERS + 1];
+  const float* decoder_weights;
+
+  int32_t precision;          /* NAM_PREC_* */
+  int32_t filter;             /* NAM_FILTER_* */
+  int32_t address;            /* NAM_ADDRESS_* */
+  int32_t trainable;          /* 1: keep FP32 masters on the device for
+                                 nam_backward / nam_train_step (F32 only) */
+  const float* fp8_act_scale; /* NAM_PREC_FP8: host array, input scale of
+                                 each decoder layer (n_layers values > 0) */
+} nam_material_desc;
+
+typedef struct {
+  uint64_t resident_bytes;    /* device bytes this material holds */
+  int64_t texels;             /* texels over all levels */
+  int64_t n_params;           /* FP32 master parameters (frame + decoder) */
+  int32_t precision, filter, address, levels;
+  float fp8_weight_scale[NAM_MAX_LAYERS]; /* NAM_PREC_FP8: per decoder layer */
+} nam_material_info;
+
+/* Copy the pyramid and weights to the device in the layout the kernels read
+ * (FP16/FP8 weights quantised here).  NAM_ERR_BUDGET if the context's
+ * resident bytes would pass its budget; NAM_ERR_UNSUPPORTED for widths or a
+ * precision/filter combination without a kernel. */
+nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc* d, nam_material* out);
+nam_status nam_destroy_material(nam_ctx* ctx, nam_material m);
+nam_status nam_material_get_info(nam_ctx* ctx, nam_material m, nam_material_info* out);
+/* Trainable materials: device pointers to the FP32 masters the kernels read,
+ * params [n_params] (frame then decoder, layouts as in the descriptor) and
+ * pyramid [texels][8].  Owned by the material; valid until it is destroyed.
+ * Writing them between launches (on the launch stream) changes the model. */
+nam_status nam_material_params(nam_ctx* ctx, nam_material m, float** params_dev, float** pyramid_dev);
+
+/* ------------------------------------------------------------------------ */
+/* evaluation                                                               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const float *u, *v;         /* texture coordinates (wrap or clamp per material) */
+  const float *lod;           /* fractional level; clamped to [0, levels-1], NaN -> 0 */
+  const float *wix, *wiy, *wiz;
+  const float *wox, *woy, *woz;
+  const float *xi;            /* U[0,1) variate for the stochastic level pick:
+                                 the coarser level iff xi < frac(lod).
+                                 Required for NAM_FILTER_STOCHASTIC, else ignored. */
+} nam_queries;
+
+enum { NAM_OUT_COSINE = 1u << 0 };  /* multiply the RGB by max(0, wi.z) (Eq. 1) */
+
+/* Evaluate n queries whose arrays are device memory; writes rgb_out (device,
+ * [n][3]).  n = 0 is a no-op.  Asynchronous on `stream`. */
+nam_status nam_eval(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
+                    float* rgb_out, void* stream, uint32_t flags);
+
+/* Same with HOST query and output arrays: copies the inputs to a device
+ * staging area owned by the context, evaluates, copies the RGB back and
+ * synchronises the stream.  Pinned host memory gives full copy bandwidth. */
+nam_status nam_eval_host(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
+                         float* rgb_out, void* stream, uint32_t flags);
+
+/* A contiguous run of queries [start, start+count) evaluated with
+ * materials[material]. */
+typedef struct {
+  int64_t start;
+  int32_t count;
+  int32_t material;
+} nam_work_item;
+
+/* Evaluate work items (device array `items`, n_items entries) that each use
+ * one of nmat materials (device queries and output, as nam_eval).  All
+ * materials must share precision and decoder widths.  Each item's queries
+ * run on the path a single-material launch would use, so a query's result
+ * does not depend on the other items. */
+nam_status nam_eval_multi(nam_ctx* ctx, const nam_material* materials, int32_t nmat,
+                          const nam_queries* q, const nam_work_item* items_dev, int32_t n_items,
+                          float* rgb_out, void* stream, uint32_t flags);
+
+/* ------------------------------------------------------------------------ */
+/* differentiation and training (Sec. 5.2)                                  */
+/* ------------------------------------------------------------------------ */
+/* Reverse mode of nam_eval for a trainable (F32) material: given grad_rgb
+ * (device [n][3]) accumulates (adds, does not zero) the gradient of
+ * sum <grad_rgb, rgb> into grad_params (device [n_params], layout of the
+ * masters) and grad_pyramid (device [texels][8]; may be NULL).  Weight
+ * gradients are reduced per CTA then added with one atomic per parameter and
+ * CTA; pyramid gradients are scattered with atomics (tap weight x dL/dz).
+ * ReLU'(0) = 0.  No gradient flows through the degenerate-frame fallbacks. */
+nam_status nam_backward(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
+                        const float* grad_rgb, float* grad_params, float* grad_pyramid,
+                        void* stream, uint32_t flags);
+
+typedef struct {
+  float lr_params, lr_pyramid;  /* learning rates of the MLP weights and of the latents */
+  float beta1, beta2, eps;
+  int32_t step;                 /* 1-based step used for bias correction */
+} nam_adam;
+
+/* One training step on a trainable material: forward, loss
+ * L = mean |log(1+max(g,0)) - log(1+y)| + 0.01 mean max(-g,0) over the n x 3
+ * outputs (L1 in log space, Sec. 5.2), backward, Adam on the MLP masters
+ * and the pyramid.  target_rgb is device [n][3]; *loss_out (host) receives L
+ * of this step's forward (the call synchronises the stream to read it).
+ * Optimiser moments live in the material. */
+nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
+                          int64_t n, const nam_adam* opt, float* loss_out, void* stream, uint32_t flags);
+
+/* ------------------------------------------------------------------------ */
+/* serving: continuous batching of frames (Sec. 7.3 coherency analogue)      */
+/* ------------------------------------------------------------------------ */
+typedef uint64_t nam_ticket;
+
+typedef struct {
+  int64_t n_queries;          /* queries of the frame */
+  nam_queries q;              /* HOST arrays, n_queries each, valid until the ticket completes */
+  const nam_work_item* items; /* HOST array: the frame's tiles, each one material */
+  int32_t n_items;
+  int32_t n_materials;
+  const nam_material* materials; /* HOST array of n_materials handles, resident in this context */
+  float* rgb_out;             /* HOST [n_queries][3], written before the ticket completes */
+  uint32_t flags;             /* NAM_OUT_* */
+  int32_t reserved0;
+  double arrival_s;           /* arrival time on the nam_now() clock; <= 0 -> now */
+} nam_frame;
+
+typedef struct {
+  double arrival_s, admit_s, start_s, finish_s;  /* nam_now() clock */
+  int64_t n_queries;
+  nam_status status;          /* NAM_OK once done; an error if it failed */
+  int32_t reserved0;
+} nam_frame_stats;
+
+typedef struct {
+  uint64_t resident_bytes;    /* materials + serving buffers in use */
+  uint64_t budget_bytes;
+  int64_t queued, in_flight, completed, failed;
+  int64_t queries_completed;
+  double p50_latency_ms, p99_latency_ms;  /* over the last <= 4096 completed frames */
+  double evals_per_s;         /* completed queries / (last finish - first arrival) */
+} nam_stats;
+
+/* Seconds on a monotonic host clock shared by the serving calls. */
+double nam_now(void);
+/* Queue a frame (non-blocking).  A serving thread admits queued frames in
+ * arrival order as soon as their device buffers fit in the budget and a
+ * stream slot is free, so frames that arrive while others run start at once
+ * and overlap with them on the GPU.  NAM_ERR_BUSY if the queue is full;
+ * NAM_ERR_BUDGET if the frame alone can never fit. */
+nam_status nam_submit(nam_ctx* ctx, const nam_frame* f, nam_ticket* out);
+/* Non-blocking: *done = 1 once the frame's output is in rgb_out (or it
+ * failed); fills *st if not NULL. */
+nam_status nam_poll(nam_ctx* ctx, nam_ticket t, int32_t* done, nam_frame_stats* st);
+/* Block until the ticket completes or timeout_ns passes (NAM_ERR_TIMEOUT). */
+nam_status nam_wait(nam_ctx* ctx, nam_ticket t, uint64_t timeout_ns, nam_frame_stats* st);
+/* Cancel a queued (not yet admitted) frame: it completes with
+ * NAM_ERR_CANCELLED.  NAM_ERR_BUSY if it is already on the GPU. */
+nam_status nam_cancel(nam_ctx* ctx, nam_ticket t);
+nam_status nam_get_stats(nam_ctx* ctx, nam_stats* out);
+
+/* ------------------------------------------------------------------------ */
+/* test hooks (host-side fault injection; no GPU fault is ever made)         */
+/* ------------------------------------------------------------------------ */
+enum {
+  NAM_FAULT_NONE = 0,
+  NAM_FAULT_ALLOC = 1,        /* the next device allocation fails (NAM_ERR_OOM) */
+  NAM_FAULT_LAUNCH = 2,       /* the next serving launch fails (NAM_ERR_CUDA) */
+  NAM_FAULT_STALL = 3         /* the serving thread stops admitting frames */
+};
+nam_status nam_inject_fault(nam_ctx* ctx, int32_t fault);
+
+/* ------------------------------------------------------------------------ */
+/* diagnostics                                                              */
+/* ------------------------------------------------------------------------ */
+/* One tensor-core MMA in isolation: D[128][64] = A[128][32] B[64][32]^T with
+ * binary16 operands given (host) in the kernels' canonical K-major layout
+ * (element (r, k) of an R-row operand at byte (k/8)*R*16 + r*16 + (k%8)*2),
+ * FP32 result (host, row-major).  Checks the descriptor and TMEM conventions
+ * the evaluation kernels rely on.  Synchronous. */
+nam_status nam_debug_mma_selftest(nam_ctx* ctx, const uint16_t* A_host, const uint16_t* B_host, float* D_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NAM_H */

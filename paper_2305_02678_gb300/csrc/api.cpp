@@ -1,0 +1,569 @@
+// C ABI of libnam: contexts, materials, evaluation entry points.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "nam_internal.h"
+#include "nam_ctx.h"
+
+namespace nam {
+int launch_mma_selftest(const uint8_t* A, const uint8_t* B, float* D, uint64_t timeout_ns, int* err, void* stream);
+}
+
+using namespace nam;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+nam_status nam::fail(nam_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+nam_status nam::cuda_fail(int e, const char* what) {
+  return fail(e == (int)cudaErrorMemoryAllocation ? NAM_ERR_OOM : NAM_ERR_CUDA, "%s: %s (%d)", what,
+              cudaGetErrorString((cudaError_t)e), e);
+}
+
+extern "C" const char* nam_status_string(nam_status s) {
+  switch (s) {
+    case NAM_OK: return "ok";
+    case NAM_ERR_INVALID_ARG: return "invalid argument";
+    case NAM_ERR_OOM: return "out of memory";
+    case NAM_ERR_BUDGET: return "HBM budget exceeded";
+    case NAM_ERR_NOT_FOUND: return "not found";
+    case NAM_ERR_BUSY: return "busy";
+    case NAM_ERR_TIMEOUT: return "timeout";
+    case NAM_ERR_CUDA: return "CUDA error";
+    case NAM_ERR_DEVICE_ASSERT: return "device-side check failed";
+    case NAM_ERR_UNSUPPORTED: return "unsupported";
+    case NAM_ERR_CANCELLED: return "cancelled";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* nam_last_error_message(void) { return g_err.c_str(); }
+
+// ---------------------------------------------------------------------------
+// device guard
+// ---------------------------------------------------------------------------
+nam::DeviceGuard::DeviceGuard(int dev) {
+  cudaGetDevice(&prev_);
+  if (prev_ != dev) cudaSetDevice(dev);
+  dev_ = dev;
+}
+nam::DeviceGuard::~DeviceGuard() {
+  if (prev_ != dev_) cudaSetDevice(prev_);
+}
+
+// Device allocation that honours the fault-injection hook.
+int nam::dev_alloc(nam_ctx* ctx, void** p, size_t bytes) {
+  if (ctx->fault_alloc.exchange(false)) {
+    *p = nullptr;
+    return (int)cudaErrorMemoryAllocation;
+  }
+  return (int)cudaMalloc(p, bytes ? bytes : 16);
+}
+
+bool nam::budget_reserve(nam_ctx* ctx, uint64_t bytes) {
+  uint64_t cur = ctx->resident.load();
+  for (;;) {
+    if (ctx->budget && cur + bytes > ctx->budget) return false;
+    if (ctx->resident.compare_exchange_weak(cur, cur + bytes)) return true;
+  }
+}
+void nam::budget_release(nam_ctx* ctx, uint64_t bytes) { ctx->resident.fetch_sub(bytes); }
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" nam_status nam_init(nam_ctx** out, const nam_config* cfg) {
+  if (!out) return fail(NAM_ERR_INVALID_ARG, "nam_init: out is NULL");
+  *out = nullptr;
+  nam_config c{};
+  if (cfg) c = *cfg;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail((int)e, "nam_init: cudaGetDeviceCount");
+  if (c.device < 0 || c.device >= ndev) return fail(NAM_ERR_INVALID_ARG, "nam_init: device %d of %d", c.device, ndev);
+  DeviceGuard g(c.device);
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, c.device);
+  if (e != cudaSuccess) return cuda_fail((int)e, "nam_init: cudaGetDeviceProperties");
+  if (prop.major < 10) return fail(NAM_ERR_UNSUPPORTED, "nam_init: device %s is sm_%d%d, libnam needs sm_103a", prop.name, prop.major, prop.minor);
+  nam_ctx* ctx = new nam_ctx();
+  ctx->device = c.device;
+  ctx->num_sms = prop.multiProcessorCount;
+  ctx->budget = c.hbm_budget_bytes;
+  ctx->timeout_ns = c.wait_timeout_ns ? c.wait_timeout_ns : 2000000000ull;
+  ctx->serve_streams = c.serve_streams > 0 ? c.serve_streams : 4;
+  ctx->serve_queue_depth = c.serve_queue_depth > 0 ? c.serve_queue_depth : 256;
+  e = cudaMalloc(&ctx->err_word, sizeof(int));
+  if (e != cudaSuccess) {
+    delete ctx;
+    return cuda_fail((int)e, "nam_init: error word");
+  }
+  cudaMemset(ctx->err_word, 0, sizeof(int));
+  cudaDeviceSynchronize();
+  *out = ctx;
+  return NAM_OK;
+}
+
+static void free_material(nam_ctx* ctx, nam_material m) {
+  DeviceGuard g(ctx->device);
+  cudaFree(m->pyramid);
+  cudaFree(m->blob);
+  cudaFree(m->params);
+  cudaFree(m->adam_m);
+  cudaFree(m->adam_v);
+  cudaFree(m->grad);
+  cudaFree(m->train_scratch);
+  budget_release(ctx, m->info.resident_bytes);
+  delete m;
+}
+
+extern "C" nam_status nam_shutdown(nam_ctx* ctx) {
+  if (!ctx) return fail(NAM_ERR_INVALID_ARG, "nam_shutdown: NULL context");
+  serve_stop(ctx);
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  for (nam_material m : ctx->materials) free_material(ctx, m);
+  ctx->materials.clear();
+  cudaFree(ctx->err_word);
+  cudaFree(ctx->stage_dev);
+  if (ctx->stage_stream) cudaStreamDestroy((cudaStream_t)ctx->stage_stream);
+  delete ctx;
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_check_device_error(nam_ctx* ctx) {
+  if (!ctx) return fail(NAM_ERR_INVALID_ARG, "NULL context");
+  DeviceGuard g(ctx->device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail((int)e, "nam_check_device_error");
+  int code = 0;
+  cudaMemcpy(&code, ctx->err_word, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemset(ctx->err_word, 0, sizeof(int));
+  if (code == DEVERR_WAIT_TIMEOUT) return fail(NAM_ERR_TIMEOUT, "a device-side wait ran past its limit");
+  if (code) return fail(NAM_ERR_DEVICE_ASSERT, "device-side check failed (code %d)", code);
+  return NAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// materials
+// ---------------------------------------------------------------------------
+static bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+nam_status nam::validate_desc(const nam_material_desc* d, Shape* shape, PyrDesc* pyr) {
+  if (!d) return fail(NAM_ERR_INVALID_ARG, "descriptor is NULL");
+  if (d->channels != 8) return fail(NAM_ERR_INVALID_ARG, "channels must be 8 (got %d)", d->channels);
+  if (d->base_w < 1 || d->base_h < 1 || d->base_w > (1 << 20) || d->base_h > (1 << 20))
+    return fail(NAM_ERR_INVALID_ARG, "bad base size %dx%d", d->base_w, d->base_h);
+  int maxl = 1;
+  while ((std::max(d->base_w, d->base_h) >> maxl) > 0) ++maxl;
+  if (d->levels < 1 || d->levels > NAM_MAX_LEVELS || d->levels > maxl)
+    return fail(NAM_ERR_INVALID_ARG, "levels %d not in [1, %d]", d->levels, std::min(maxl, NAM_MAX_LEVELS));
+  if (d->latent_dtype != NAM_LATENT_F32 && d->latent_dtype != NAM_LATENT_F16)
+    return fail(NAM_ERR_INVALID_ARG, "bad latent dtype %d", d->latent_dtype);
+  if (!d->pyramid) return fail(NAM_ERR_INVALID_ARG, "pyramid is NULL");
+  if (d->frame_hidden != 0 && d->frame_hidden != 16)
+    return fail(NAM_ERR_UNSUPPORTED, "frame_hidden must be 0 or 16 (got %d)", d->frame_hidden);
+  if (d->frame_hidden && !d->frame_weights) return fail(NAM_ERR_INVALID_ARG, "frame weights are NULL");
+  if (!d->decoder_weights) return fail(NAM_ERR_INVALID_ARG, "decoder weights are NULL");
+  if (d->n_layers != 3)
+    return fail(NAM_ERR_UNSUPPORTED, "n_layers must be 3: two hidden layers (got %d)", d->n_layers);
+  const int H = d->widths[1];
+  if (d->widths[0] != 14 || d->widths[d->n_layers] != 3)
+    return fail(NAM_ERR_UNSUPPORTED, "decoder must map 14 inputs to 3 outputs");
+  for (int l = 1; l < d->n_layers; ++l)
+    if (d->widths[l] != H) return fail(NAM_ERR_UNSUPPORTED, "hidden widths must be equal");
+  if (H != 16 && H != 32 && H != 64) return fail(NAM_ERR_UNSUPPORTED, "hidden width %d not in {16, 32, 64}", H);
+  if (d->precision < NAM_PREC_F32 || d->precision > NAM_PREC_FP8)
+    return fail(NAM_ERR_INVALID_ARG, "bad precision %d", d->precision);
+  if (d->filter != NAM_FILTER_TRILINEAR && d->filter != NAM_FILTER_STOCHASTIC)
+    return fail(NAM_ERR_INVALID_ARG, "bad filter %d", d->filter);
+  if (d->address != NAM_ADDRESS_WRAP && d->address != NAM_ADDRESS_CLAMP)
+    return fail(NAM_ERR_INVALID_ARG, "bad address mode %d", d->address);
+  if (d->trainable && (d->precision != NAM_PREC_F32 || d->latent_dtype != NAM_LATENT_F32))
+    return fail(NAM_ERR_UNSUPPORTED, "trainable materials need F32 precision and F32 latents");
+  if (d->precision == NAM_PREC_FP8) {
+    if (!d->fp8_act_scale) return fail(NAM_ERR_INVALID_ARG, "FP8 needs fp8_act_scale");
+    for (int l = 0; l < d->n_layers; ++l)
+      if (!(d->fp8_act_scale[l] > 0.0f) || !std::isfinite(d->fp8_act_scale[l]))
+        return fail(NAM_ERR_INVALID_ARG, "fp8_act_scale[%d] must be finite and > 0", l);
+  }
+  shape->H = H;
+  shape->NH = d->n_layers - 1;
+  shape->frame = d->frame_hidden ? 1 : 0;
+  std::memset(pyr, 0, sizeof *pyr);
+  pyr->levels = d->levels;
+  pyr->f16 = d->latent_dtype == NAM_LATENT_F16;
+  pyr->filter = d->filter;
+  pyr->address = d->address;
+  pyr->pow2 = 1;
+  int64_t off = 0;
+  for (int l = 0; l < d->levels; ++l) {
+    int w = std::max(1, d->base_w >> l), h = std::max(1, d->base_h >> l);
+    pyr->w[l] = w;
+    pyr->h[l] = h;
+    pyr->off[l] = off;
+    if (!is_pow2(w) || !is_pow2(h)) pyr->pow2 = 0;
+    off += (int64_t)w * h;
+  }
+  pyr->texels = off;
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc* d, nam_material* out) {
+  if (!ctx || !out) return fail(NAM_ERR_INVALID_ARG, "nam_create_material: NULL argument");
+  *out = nullptr;
+  Shape sh;
+  PyrDesc pd;
+  nam_status st = validate_desc(d, &sh, &pd);
+  if (st) return st;
+  DeviceGuard g(ctx->device);
+  const size_t texel_bytes = pd.f16 ? 16 : 32;
+  const size_t pyr_bytes = (size_t)pd.texels * texel_bytes;
+  const int64_t np = n_params_of(sh);
+  // host copies of the FP32 masters (the descriptor may point to device memory)
+  const int64_t nframe = sh.frame ? 246 : 0;
+  std::vector<float> master((size_t)np);
+  cudaMemcpyKind kind = d->params_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+  if (nframe) cudaMemcpy(master.data(), d->frame_weights, nframe * 4, kind);
+  cudaMemcpy(master.data() + nframe, d->decoder_weights, (np - nframe) * 4, kind);
+  for (float v : master)
+    if (!std::isfinite(v)) return fail(NAM_ERR_INVALID_ARG, "non-finite weight");
+
+  nam_material m = new nam_material_s();
+  m->desc = *d;
+  m->shape = sh;
+  m->pyr = pd;
+  m->n_params = np;
+  size_t blob_bytes = 0;
+  if (d->precision == NAM_PREC_F32) {
+    blob_bytes = 0;  // the FP32 kernels read the master layout directly
+  } else {
+    blob_bytes = tc_blob_bytes(sh, d->precision);
+    if (!blob_bytes) {
+      delete m;
+      return fail(NAM_ERR_UNSUPPORTED, "no tensor-core kernel for this shape/precision");
+    }
+  }
+  uint64_t resident = pyr_bytes + blob_bytes + (uint64_t)np * 4;
+  if (d->trainable) {
+    // FP32 pyramid masters are the pyramid itself; Adam moments + grads for
+    // params and pyramid, plus per-step scratch (grad_rgb, loss)
+    resident += 3ull * np * 4 + 3ull * pyr_bytes;
+  }
+  if (!budget_reserve(ctx, resident)) {
+    delete m;
+    return fail(NAM_ERR_BUDGET, "material needs %llu bytes; %llu of %llu in use", (unsigned long long)resident,
+                (unsigned long long)ctx->resident.load(), (unsigned long long)ctx->budget);
+  }
+  m->info.resident_bytes = resident;
+  int e = dev_alloc(ctx, &m->pyramid, pyr_bytes);
+  if (!e) e = dev_alloc(ctx, (void**)&m->params, np * 4);
+  if (!e && blob_bytes) e = dev_alloc(ctx, &m->blob, blob_bytes);
+  if (!e && d->trainable) {
+    e = dev_alloc(ctx, (void**)&m->adam_m, (np + pd.texels * 8) * 4);
+    if (!e) e = dev_alloc(ctx, (void**)&m->adam_v, (np + pd.texels * 8) * 4);
+    if (!e) e = dev_alloc(ctx, (void**)&m->grad, (np + pd.texels * 8) * 4);
+  }
+  if (e) {
+    free_material(ctx, m);
+    return cuda_fail(e, "nam_create_material: allocation");
+  }
+  e = (int)cudaMemcpy(m->pyramid, d->pyramid, pyr_bytes,
+                      d->params_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
+  if (!e) e = (int)cudaMemcpy(m->params, master.data(), np * 4, cudaMemcpyHostToDevice);
+  if (!e && blob_bytes) {
+    std::vector<uint8_t> blob(blob_bytes);
+    if (pack_tc_blob(sh, d->precision, nframe ? master.data() : nullptr, master.data() + nframe,
+                     d->fp8_act_scale, blob.data(), m->info.fp8_weight_scale) != 0) {
+      free_material(ctx, m);
+      return fail(NAM_ERR_UNSUPPORTED, "weight packing failed");
+    }
+    e = (int)cudaMemcpy(m->blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice);
+  }
+  if (!e && d->trainable) {
+    size_t nb = (np + pd.texels * 8) * 4;
+    cudaMemset(m->adam_m, 0, nb);
+    cudaMemset(m->adam_v, 0, nb);
+    e = (int)cudaMemset(m->grad, 0, nb);
+  }
+  if (e) {
+    free_material(ctx, m);
+    return cuda_fail(e, "nam_create_material: upload");
+  }
+  m->info.texels = pd.texels;
+  m->info.n_params = np;
+  m->info.precision = d->precision;
+  m->info.filter = d->filter;
+  m->info.address = d->address;
+  m->info.levels = d->levels;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->materials.insert(m);
+  }
+  *out = m;
+  return NAM_OK;
+}
+
+static bool owns(nam_ctx* ctx, nam_material m) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  return ctx->materials.count(m) != 0;
+}
+
+extern "C" nam_status nam_destroy_material(nam_ctx* ctx, nam_material m) {
+  if (!ctx || !m) return fail(NAM_ERR_INVALID_ARG, "NULL argument");
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->materials.count(m)) return fail(NAM_ERR_NOT_FOUND, "unknown material");
+    ctx->materials.erase(m);
+  }
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  free_material(ctx, m);
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_material_get_info(nam_ctx* ctx, nam_material m, nam_material_info* out) {
+  if (!ctx || !m || !out) return fail(NAM_ERR_INVALID_ARG, "NULL argument");
+  if (!owns(ctx, m)) return fail(NAM_ERR_NOT_FOUND, "unknown material");
+  *out = m->info;
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_material_params(nam_ctx* ctx, nam_material m, float** params_dev, float** pyramid_dev) {
+  if (!ctx || !m) return fail(NAM_ERR_INVALID_ARG, "NULL argument");
+  if (!owns(ctx, m)) return fail(NAM_ERR_NOT_FOUND, "unknown material");
+  if (!m->desc.trainable) return fail(NAM_ERR_UNSUPPORTED, "material is not trainable");
+  if (params_dev) *params_dev = m->params;
+  if (pyramid_dev) *pyramid_dev = (float*)m->pyramid;
+  return NAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// evaluation
+// ---------------------------------------------------------------------------
+nam_status nam::check_queries(const nam_material_s* m, const nam_queries* q) {
+  if (!q || !q->u || !q->v || !q->lod || !q->wix || !q->wiy || !q->wiz || !q->wox || !q->woy || !q->woz)
+    return fail(NAM_ERR_INVALID_ARG, "query arrays must not be NULL");
+  if (m->desc.filter == NAM_FILTER_STOCHASTIC && !q->xi)
+    return fail(NAM_ERR_INVALID_ARG, "stochastic filtering needs xi");
+  return NAM_OK;
+}
+
+void nam::fill_launch(nam_ctx* ctx, const nam_material_s* m, const nam_queries* q, int64_t n, float* rgb,
+                      uint32_t flags, LaunchCommon* L) {
+  std::memset(L, 0, sizeof *L);
+  L->pyr = m->pyr;
+  L->shape = m->shape;
+  L->q = QueryPtrs{q->u, q->v, q->lod, q->wix, q->wiy, q->wiz, q->wox, q->woy, q->woz, q->xi};
+  L->rgb = rgb;
+  L->n = n;
+  L->pyr0 = m->pyramid;
+  L->w0 = m->desc.precision == NAM_PREC_F32 ? (const void*)m->params : m->blob;
+  L->mats.nmat = 1;
+  L->flags = flags;
+  L->err = ctx->err_word;
+  L->timeout_ns = ctx->timeout_ns;
+  L->num_sms = ctx->num_sms;
+}
+
+int nam::launch_material(const LaunchCommon& L, int precision, void* stream) {
+  if (precision == NAM_PREC_F32) return launch_eval_f32(L, stream);
+  return launch_eval_tc(L, precision, stream);
+}
+
+extern "C" nam_status nam_eval(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n, float* rgb_out,
+                               void* stream, uint32_t flags) {
+  if (!ctx || !m) return fail(NAM_ERR_INVALID_ARG, "nam_eval: NULL context or material");
+  if (n < 0) return fail(NAM_ERR_INVALID_ARG, "nam_eval: n < 0");
+  if (n == 0) return NAM_OK;
+  if (!rgb_out) return fail(NAM_ERR_INVALID_ARG, "nam_eval: rgb_out is NULL");
+  if (!owns(ctx, m)) return fail(NAM_ERR_NOT_FOUND, "nam_eval: unknown material");
+  nam_status st = check_queries(m, q);
+  if (st) return st;
+  DeviceGuard g(ctx->device);
+  LaunchCommon L;
+  fill_launch(ctx, m, q, n, rgb_out, flags, &L);
+  int e = launch_material(L, m->desc.precision, stream);
+  if (e) return cuda_fail(e, "nam_eval: launch");
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_eval_host(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n, float* rgb_out,
+                                    void* stream, uint32_t flags) {
+  if (!ctx || !m) return fail(NAM_ERR_INVALID_ARG, "nam_eval_host: NULL context or material");
+  if (n < 0) return fail(NAM_ERR_INVALID_ARG, "nam_eval_host: n < 0");
+  if (n == 0) return NAM_OK;
+  if (!rgb_out) return fail(NAM_ERR_INVALID_ARG, "nam_eval_host: rgb_out is NULL");
+  if (!owns(ctx, m)) return fail(NAM_ERR_NOT_FOUND, "nam_eval_host: unknown material");
+  nam_status st = check_queries(m, q);
+  if (st) return st;
+  DeviceGuard g(ctx->device);
+  std::lock_guard<std::mutex> lk(ctx->stage_mu);
+  const bool has_xi = m->desc.filter == NAM_FILTER_STOCHASTIC;
+  const int nf = has_xi ? 10 : 9;
+  const size_t need = (size_t)n * 4 * (nf + 3);
+  if (need > ctx->stage_bytes) {
+    if (ctx->stage_dev) {
+      cudaFree(ctx->stage_dev);
+      budget_release(ctx, ctx->stage_bytes);
+      ctx->stage_dev = nullptr;
+      ctx->stage_bytes = 0;
+    }
+    if (!budget_reserve(ctx, need)) return fail(NAM_ERR_BUDGET, "nam_eval_host: staging needs %zu bytes", need);
+    int e = dev_alloc(ctx, &ctx->stage_dev, need);
+    if (e) {
+      budget_release(ctx, need);
+      return cuda_fail(e, "nam_eval_host: staging allocation");
+    }
+    ctx->stage_bytes = need;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  float* base = (float*)ctx->stage_dev;
+  const float* src[10] = {q->u, q->v, q->lod, q->wix, q->wiy, q->wiz, q->wox, q->woy, q->woz, q->xi};
+  float* dst[10];
+  for (int f = 0; f < nf; ++f) {
+    dst[f] = base + (size_t)f * n;
+    cudaError_t e = cudaMemcpyAsync(dst[f], src[f], (size_t)n * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail((int)e, "nam_eval_host: H2D");
+  }
+  float* rgb_dev = base + (size_t)nf * n;
+  nam_queries dq{dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], dst[7], dst[8], has_xi ? dst[9] : nullptr};
+  LaunchCommon L;
+  fill_launch(ctx, m, &dq, n, rgb_dev, flags, &L);
+  int e = launch_material(L, m->desc.precision, stream);
+  if (e) return cuda_fail(e, "nam_eval_host: launch");
+  cudaError_t ce = cudaMemcpyAsync(rgb_out, rgb_dev, (size_t)n * 12, cudaMemcpyDeviceToHost, s);
+  if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_eval_host: D2H");
+  ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_eval_host: sync");
+  return NAM_OK;
+}
+
+// Chunk table of a multi-material launch: every item split into runs of at
+// most 128 queries so that no tensor-core tile mixes materials.
+void nam::build_chunks(const nam_work_item* items, int32_t n_items, std::vector<Chunk>* out) {
+  out->clear();
+  for (int32_t i = 0; i < n_items; ++i) {
+    for (int32_t o = 0; o < items[i].count; o += 128) {
+      Chunk c;
+      c.start = items[i].start + o;
+      c.count = std::min(128, items[i].count - o);
+      c.material = items[i].material;
+      out->push_back(c);
+    }
+  }
+}
+
+nam_status nam::check_multi(nam_ctx* ctx, const nam_material* mats, int32_t nmat) {
+  if (!mats || nmat < 1) return fail(NAM_ERR_INVALID_ARG, "no materials");
+  const nam_material m0 = mats[0];
+  for (int32_t k = 0; k < nmat; ++k) {
+    if (!mats[k] || !owns(ctx, mats[k])) return fail(NAM_ERR_NOT_FOUND, "unknown material %d", k);
+    const nam_material m = mats[k];
+    if (m->desc.precision == NAM_PREC_F32) return fail(NAM_ERR_UNSUPPORTED, "multi-material launches use the tensor-core path");
+    if (m->desc.precision != m0->desc.precision || m->shape.H != m0->shape.H || m->shape.NH != m0->shape.NH ||
+        m->shape.frame != m0->shape.frame)
+      return fail(NAM_ERR_INVALID_ARG, "materials must share precision and MLP shape");
+    if (std::memcmp(&m->pyr, &m0->pyr, sizeof(PyrDesc)) != 0)
+      return fail(NAM_ERR_INVALID_ARG, "materials must share pyramid geometry, dtype, filter and addressing");
+  }
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_eval_multi(nam_ctx* ctx, const nam_material* mats, int32_t nmat, const nam_queries* q,
+                                     const nam_work_item* items, int32_t n_items, float* rgb_out, void* stream,
+                                     uint32_t flags) {
+  if (!ctx) return fail(NAM_ERR_INVALID_ARG, "nam_eval_multi: NULL context");
+  if (n_items < 0) return fail(NAM_ERR_INVALID_ARG, "n_items < 0");
+  if (n_items == 0) return NAM_OK;
+  if (!items || !rgb_out) return fail(NAM_ERR_INVALID_ARG, "NULL items or output");
+  nam_status st = check_multi(ctx, mats, nmat);
+  if (st) return st;
+  st = check_queries(mats[0], q);
+  if (st) return st;
+  for (int32_t i = 0; i < n_items; ++i)
+    if (items[i].material < 0 || items[i].material >= nmat || items[i].count < 0 || items[i].start < 0)
+      return fail(NAM_ERR_INVALID_ARG, "bad work item %d", i);
+  std::vector<Chunk> chunks;
+  build_chunks(items, n_items, &chunks);
+  if (chunks.empty()) return NAM_OK;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // one stream-ordered allocation: chunk table, pyramid pointers, weight pointers
+  const size_t cb = chunks.size() * sizeof(Chunk);
+  const size_t pb = (size_t)nmat * sizeof(void*);
+  std::vector<uint8_t> host(cb + 2 * pb);
+  std::memcpy(host.data(), chunks.data(), cb);
+  for (int32_t k = 0; k < nmat; ++k) {
+    const void* p = mats[k]->pyramid;
+    const void* w = mats[k]->blob;
+    std::memcpy(host.data() + cb + k * sizeof(void*), &p, sizeof p);
+    std::memcpy(host.data() + cb + pb + k * sizeof(void*), &w, sizeof w);
+  }
+  void* dev = nullptr;
+  cudaError_t e = cudaMallocAsync(&dev, host.size(), s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "nam_eval_multi: table allocation");
+  e = cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(dev, s);
+    return cuda_fail((int)e, "nam_eval_multi: table upload");
+  }
+  LaunchCommon L;
+  fill_launch(ctx, mats[0], q, 0, rgb_out, flags, &L);
+  L.chunks = (const Chunk*)dev;
+  L.n_chunks = (int32_t)chunks.size();
+  L.mats.pyramid = (const void* const*)((uint8_t*)dev + cb);
+  L.mats.weights = (const void* const*)((uint8_t*)dev + cb + pb);
+  L.mats.nmat = nmat;
+  int le = launch_material(L, mats[0]->desc.precision, stream);
+  cudaFreeAsync(dev, s);
+  if (le) return cuda_fail(le, "nam_eval_multi: launch");
+  return NAM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// diagnostics
+// ---------------------------------------------------------------------------
+extern "C" nam_status nam_debug_mma_selftest(nam_ctx* ctx, const uint16_t* A_host, const uint16_t* B_host,
+                                             float* D_host) {
+  if (!ctx || !A_host || !B_host || !D_host) return fail(NAM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(ctx->device);
+  void *A = nullptr, *B = nullptr, *D = nullptr;
+  cudaMalloc(&A, 8192);
+  cudaMalloc(&B, 4096);
+  cudaMalloc(&D, 128 * 64 * 4);
+  cudaMemcpy(A, A_host, 8192, cudaMemcpyHostToDevice);
+  cudaMemcpy(B, B_host, 4096, cudaMemcpyHostToDevice);
+  cudaMemset(D, 0, 128 * 64 * 4);
+  int e = launch_mma_selftest((const uint8_t*)A, (const uint8_t*)B, (float*)D, ctx->timeout_ns, ctx->err_word, nullptr);
+  if (!e) e = (int)cudaDeviceSynchronize();
+  if (!e) e = (int)cudaMemcpy(D_host, D, 128 * 64 * 4, cudaMemcpyDeviceToHost);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(D);
+  if (e) return cuda_fail(e, "nam_debug_mma_selftest");
+  return nam_check_device_error(ctx);
+}

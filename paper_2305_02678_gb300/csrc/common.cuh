@@ -1,0 +1,181 @@
+// Device helpers shared by the libnam kernels: latent-pyramid fetch and
+// shading-frame construction.  One thread evaluates one query.
+#pragma once
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "nam_internal.h"
+
+namespace nam {
+
+// Level index of a query (Sec. 4.1: the level may be fractional and lie
+// between two levels).  l = clamp(lod, 0, L-1) (NaN -> 0), l0 = floor(l),
+// l1 = min(l0+1, L-1), t = l - l0.
+struct LevelPick {
+  int l0, l1;
+  float t;
+};
+
+__device__ __forceinline__ LevelPick pick_levels(const PyrDesc& P, float lod) {
+  float l = fminf(fmaxf(lod, 0.0f), (float)(P.levels - 1));  // fmaxf(NaN, 0) = 0
+  float f = floorf(l);
+  LevelPick r;
+  r.l0 = (int)f;
+  r.l1 = min(r.l0 + 1, P.levels - 1);
+  r.t = l - f;
+  return r;
+}
+
+// Integer texel coordinate of the lower bilinear tap and its fraction, plus
+// the upper tap, under the material's addressing.  Texel centres sit at
+// (i + 1/2) / W, so the continuous coordinate is x = u W - 1/2.  For wrap the
+// integer part of u is removed first (exact in FP32), which for power-of-two
+// W gives the same x as u W - 1/2 modulo W, bit for bit.
+__device__ __forceinline__ void tap_axis(const PyrDesc& P, float u, int W, int& i0, int& i1, float& f) {
+  if (P.address == NAM_ADDRESS_CLAMP) {
+    float x = fmaf(u, (float)W, -0.5f);
+    float x0 = floorf(x);
+    f = x - x0;
+    // clamp in float first so that huge |u| cannot overflow the int conversion
+    float c0 = fminf(fmaxf(x0, 0.0f), (float)(W - 1));
+    float c1 = fminf(fmaxf(x0 + 1.0f, 0.0f), (float)(W - 1));
+    i0 = (int)c0;
+    i1 = (int)c1;
+  } else {
+    float uf = u - floorf(u);  // [0, 1]
+    float x = fmaf(uf, (float)W, -0.5f);
+    float x0 = floorf(x);
+    f = x - x0;
+    int k = (int)x0;  // in [-1, W]
+    if (P.pow2) {
+      i0 = k & (W - 1);
+      i1 = (k + 1) & (W - 1);
+    } else {
+      i0 = k < 0 ? k + W : (k >= W ? k - W : k);
+      int k1 = k + 1;
+      i1 = k1 >= W ? k1 - W : k1;
+    }
+  }
+}
+
+// Accumulate wgt * bilinear(level l) into z[8].
+template <bool F16>
+__device__ __forceinline__ void bilinear_acc(const PyrDesc& P, const void* pyr, int l, float u, float v,
+                                             float wgt, float z[8]) {
+  const int W = P.w[l], H = P.h[l];
+  int x0, x1, y0, y1;
+  float fx, fy;
+  tap_axis(P, u, W, x0, x1, fx);
+  tap_axis(P, v, H, y0, y1, fy);
+  const int64_t base = P.off[l];
+  const int64_t r0 = base + (int64_t)y0 * W, r1 = base + (int64_t)y1 * W;
+  const int64_t idx[4] = {r0 + x0, r0 + x1, r1 + x0, r1 + x1};
+  const float gx = 1.0f - fx, gy = 1.0f - fy;
+  const float w4[4] = {gx * gy * wgt, fx * gy * wgt, gx * fy * wgt, fx * fy * wgt};
+  if (F16) {
+    const uint4* p = reinterpret_cast<const uint4*>(pyr);
+    uint4 t[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) t[k] = __ldg(p + idx[k]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __half2* h = reinterpret_cast<const __half2*>(&t[k]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float2 f2 = __half22float2(h[c]);
+        z[2 * c] = fmaf(w4[k], f2.x, z[2 * c]);
+        z[2 * c + 1] = fmaf(w4[k], f2.y, z[2 * c + 1]);
+      }
+    }
+  } else {
+    const float4* p = reinterpret_cast<const float4*>(pyr);
+    float4 a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      a[k] = __ldg(p + 2 * idx[k]);
+      b[k] = __ldg(p + 2 * idx[k] + 1);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      z[0] = fmaf(w4[k], a[k].x, z[0]);
+      z[1] = fmaf(w4[k], a[k].y, z[1]);
+      z[2] = fmaf(w4[k], a[k].z, z[2]);
+      z[3] = fmaf(w4[k], a[k].w, z[3]);
+      z[4] = fmaf(w4[k], b[k].x, z[4]);
+      z[5] = fmaf(w4[k], b[k].y, z[5]);
+      z[6] = fmaf(w4[k], b[k].z, z[6]);
+      z[7] = fmaf(w4[k], b[k].w, z[7]);
+    }
+  }
+}
+
+// Filtered latent code z(x) (Sec. 4.1).  Trilinear blends the two levels
+// with weights 1-t and t (the upper level is skipped when t == 0, where its
+// weight is zero); stochastic takes l1 when xi < t and l0 otherwise.
+template <bool F16>
+__device__ __forceinline__ void fetch_latent(const PyrDesc& P, const void* pyr, float u, float v, float lod,
+                                             float xi, float z[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) z[c] = 0.0f;
+  LevelPick lp = pick_levels(P, lod);
+  if (P.filter == NAM_FILTER_STOCHASTIC) {
+    bilinear_acc<F16>(P, pyr, xi < lp.t ? lp.l1 : lp.l0, u, v, 1.0f, z);
+  } else {
+    bilinear_acc<F16>(P, pyr, lp.l0, u, v, 1.0f - lp.t, z);
+    if (lp.t != 0.0f) bilinear_acc<F16>(P, pyr, lp.l1, u, v, lp.t, z);
+  }
+}
+
+// Shading frame from r = (n_raw, t_raw) (Sec. 4.2, Eq. 4; b = n x t / |n x t|,
+// Sec. 9): n = n_raw / |n_raw|, t = Gram-Schmidt of t_raw against n,
+// normalised.  Degenerate inputs: |n_raw| < 1e-20 -> n = (0,0,1);
+// |t'| <= 1e-6 |t_raw| -> t from n alone (branch-free orthonormal basis of
+// Duff et al., JCGT 2017).  Writes T's rows t, b, n.
+struct Frame {
+  float t[3], b[3], n[3];
+};
+
+__device__ __forceinline__ Frame build_frame(const float r[6]) {
+  Frame F;
+  float nl = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  if (!(nl >= 1e-20f)) {
+    F.n[0] = 0.0f; F.n[1] = 0.0f; F.n[2] = 1.0f;
+  } else {
+    float inv = 1.0f / nl;
+    F.n[0] = r[0] * inv; F.n[1] = r[1] * inv; F.n[2] = r[2] * inv;
+  }
+  float s = r[3] * F.n[0] + r[4] * F.n[1] + r[5] * F.n[2];
+  float tp0 = r[3] - s * F.n[0], tp1 = r[4] - s * F.n[1], tp2 = r[5] - s * F.n[2];
+  float tpl = sqrtf(tp0 * tp0 + tp1 * tp1 + tp2 * tp2);
+  float trl = sqrtf(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
+  if (!(tpl > 1e-6f * trl)) {
+    float sg = copysignf(1.0f, F.n[2]);
+    float a = -1.0f / (sg + F.n[2]);
+    float bb = F.n[0] * F.n[1] * a;
+    F.t[0] = 1.0f + sg * F.n[0] * F.n[0] * a;
+    F.t[1] = sg * bb;
+    F.t[2] = -sg * F.n[0];
+  } else {
+    float inv = 1.0f / tpl;
+    F.t[0] = tp0 * inv; F.t[1] = tp1 * inv; F.t[2] = tp2 * inv;
+  }
+  float c0 = F.n[1] * F.t[2] - F.n[2] * F.t[1];
+  float c1 = F.n[2] * F.t[0] - F.n[0] * F.t[2];
+  float c2 = F.n[0] * F.t[1] - F.n[1] * F.t[0];
+  float inv = 1.0f / sqrtf(c0 * c0 + c1 * c1 + c2 * c2);
+  F.b[0] = c0 * inv; F.b[1] = c1 * inv; F.b[2] = c2 * inv;
+  return F;
+}
+
+__device__ __forceinline__ void to_local(const Frame& F, float x, float y, float z, float out[3]) {
+  out[0] = F.t[0] * x + F.t[1] * y + F.t[2] * z;
+  out[1] = F.b[0] * x + F.b[1] * y + F.b[2] * z;
+  out[2] = F.n[0] * x + F.n[1] * y + F.n[2] * z;
+}
+
+// Record a device-side error code (first one wins).
+__device__ __forceinline__ void record_error(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+}  // namespace nam

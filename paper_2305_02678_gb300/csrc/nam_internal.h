@@ -1,0 +1,106 @@
+// Internal types shared by the libnam translation units (not part of the ABI).
+#pragma once
+#include <stdint.h>
+
+#include "../../include/nam.h"
+
+namespace nam {
+
+// Device error codes recorded by kernels in the context's error word.
+enum DevError : int {
+  DEVERR_NONE = 0,
+  DEVERR_WAIT_TIMEOUT = 1,  // a bounded mbarrier wait ran out
+  DEVERR_BOUNDS = 2,        // an index failed a device-side check
+};
+
+// Latent pyramid geometry, passed by value to kernels.
+struct PyrDesc {
+  int32_t levels;
+  int32_t f16;      // 1: binary16 texels (16 B per texel), 0: float32 (32 B)
+  int32_t filter;   // NAM_FILTER_*
+  int32_t address;  // NAM_ADDRESS_*
+  int32_t pow2;     // every level width and height is a power of two
+  int32_t w[NAM_MAX_LEVELS], h[NAM_MAX_LEVELS];
+  int64_t off[NAM_MAX_LEVELS];  // first texel of each level
+  int64_t texels;
+};
+
+// Planar query arrays (device) with an optional base offset.
+struct QueryPtrs {
+  const float *u, *v, *lod, *wix, *wiy, *wiz, *wox, *woy, *woz, *xi;
+};
+
+// Decoder shape supported by the kernels: 14 -> H (x NH hidden layers) -> 3,
+// optional frame MLP 8 -> 16 -> 6.
+struct Shape {
+  int32_t H;        // hidden width: 16, 32, 64
+  int32_t NH;       // hidden layers: 2 or 3
+  int32_t frame;    // 1: frame MLP present
+};
+
+// A chunk of at most 128 consecutive queries that all use one material.
+struct Chunk {
+  int64_t start;
+  int32_t count;
+  int32_t material;
+};
+
+// Per-launch description of the materials a kernel may use.
+struct MatTable {
+  const void* const* pyramid;  // device array [nmat] of pyramid pointers
+  const void* const* weights;  // device array [nmat] of weight blobs
+  int32_t nmat;
+};
+
+// ---------------------------------------------------------------------------
+// launchers (return cudaError_t as int)
+// ---------------------------------------------------------------------------
+struct LaunchCommon {
+  PyrDesc pyr;
+  Shape shape;
+  QueryPtrs q;
+  float* rgb;
+  int64_t n;             // queries (single-material launches)
+  const Chunk* chunks;   // device chunk list (multi-material) or nullptr
+  int32_t n_chunks;      // chunks when `chunks` is set
+  MatTable mats;         // single material: nmat = 1
+  const void* pyr0;      // single material pyramid
+  const void* w0;        // single material weight blob
+  uint32_t flags;
+  int* err;
+  uint64_t timeout_ns;
+  int num_sms;
+};
+
+int launch_eval_f32(const LaunchCommon& L, void* stream);
+int launch_eval_tc(const LaunchCommon& L, int precision, void* stream);
+
+// Weight blob sizes and packing (host side).
+size_t f32_blob_floats(const Shape& s);
+void pack_f32_blob(const Shape& s, const float* frame, const float* dec, float* out);
+size_t tc_blob_bytes(const Shape& s, int precision);
+int pack_tc_blob(const Shape& s, int precision, const float* frame, const float* dec,
+                 const float* act_scale, uint8_t* out, float* weight_scales_out);
+
+// Backward / training.
+struct BackwardArgs {
+  PyrDesc pyr;
+  Shape shape;
+  QueryPtrs q;
+  int64_t n;
+  const void* pyramid;     // FP32 master pyramid
+  const float* params;     // FP32 master params (frame then decoder)
+  const float* grad_rgb;   // [n][3]
+  float* grad_params;
+  float* grad_pyramid;     // may be null
+  uint32_t flags;
+  int num_sms;
+};
+int launch_backward(const BackwardArgs& a, void* stream);
+int launch_loss(const float* rgb, const float* target, int64_t n, float* grad_rgb, float* loss_accum,
+                void* stream);
+int launch_adam(float* p, const float* g, float* m, float* v, int64_t count, float lr, float b1, float b2,
+                float eps, int step, void* stream);
+int64_t n_params_of(const Shape& s);
+
+}  // namespace nam

@@ -1,0 +1,399 @@
+// Serving: continuous batching of frames.
+//
+// nam_submit queues a frame (host arrays).  One scheduler thread per
+// context admits queued frames in arrival order as soon as a stream slot is
+// free and the frame's device buffers fit under the HBM budget; admission
+// enqueues, on that slot's stream, the host->device copies, one
+// multi-material tensor-core launch over the frame's tiles (each tile one
+// material, so every 128-query MMA tile is material-coherent, the analogue
+// of the paper's coherent warps, Sec. 7.3) and the device->host copy of the
+// RGB.  Frames on different slots run concurrently on the GPU, so a frame
+// that arrives while others are in flight starts as soon as a slot frees up.
+// Completion is observed with CUDA events; per-frame latency is
+// finish - arrival on the nam_now() clock.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+
+#include "nam_ctx.h"
+
+using namespace nam;
+
+namespace nam {
+
+struct Job {
+  nam_ticket ticket = 0;
+  nam_frame frame{};
+  std::vector<nam_material> mats;
+  std::vector<Chunk> chunks;
+  uint64_t bytes = 0;
+  int nf = 9;
+  nam_frame_stats st{};
+  bool done = false;
+  int slot = -1;
+  void* dev = nullptr;
+};
+
+struct Slot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  Job* job = nullptr;
+};
+
+struct ServeState {
+  std::mutex mu;
+  std::condition_variable cv;       // wakes the scheduler
+  std::condition_variable done_cv;  // wakes nam_wait
+  std::deque<Job*> queue;
+  std::map<nam_ticket, Job*> jobs;
+  std::deque<nam_ticket> finished_order;
+  std::vector<Slot> slots;
+  std::thread thread;
+  bool stop = false;
+  nam_ticket next_ticket = 1;
+  int64_t in_flight = 0, completed = 0, failed = 0, queries_completed = 0;
+  uint64_t serving_bytes = 0;
+  std::deque<double> latencies_ms;
+  double first_arrival = -1.0, last_finish = 0.0;
+};
+
+}  // namespace nam
+
+extern "C" double nam_now(void) {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+static void finish_job(ServeState* S, Job* j, nam_status status) {
+  // S->mu held
+  j->st.status = status;
+  j->st.finish_s = nam_now();
+  j->done = true;
+  if (status == NAM_OK) {
+    S->completed++;
+    S->queries_completed += j->frame.n_queries;
+    double lat = (j->st.finish_s - j->st.arrival_s) * 1e3;
+    S->latencies_ms.push_back(lat);
+    if (S->latencies_ms.size() > 4096) S->latencies_ms.pop_front();
+    if (S->first_arrival < 0 || j->st.arrival_s < S->first_arrival) S->first_arrival = j->st.arrival_s;
+    S->last_finish = std::max(S->last_finish, j->st.finish_s);
+  } else {
+    S->failed++;
+  }
+  S->finished_order.push_back(j->ticket);
+  while (S->finished_order.size() > 65536) {
+    auto it = S->jobs.find(S->finished_order.front());
+    if (it != S->jobs.end()) {
+      delete it->second;
+      S->jobs.erase(it);
+    }
+    S->finished_order.pop_front();
+  }
+  S->done_cv.notify_all();
+}
+
+// Enqueue one admitted frame on its slot (S->mu not held).  Returns a status.
+static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = slot.stream;
+  const int64_t n = j->frame.n_queries;
+  if (ctx->fault_alloc.exchange(false)) return fail(NAM_ERR_OOM, "injected allocation failure");
+  cudaError_t e = cudaMallocAsync(&j->dev, j->bytes, s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "serving: frame buffers");
+  uint8_t* base = (uint8_t*)j->dev;
+  const float* src[10] = {j->frame.q.u, j->frame.q.v, j->frame.q.lod, j->frame.q.wix, j->frame.q.wiy,
+                          j->frame.q.wiz, j->frame.q.wox, j->frame.q.woy, j->frame.q.woz, j->frame.q.xi};
+  float* dst[10] = {nullptr};
+  for (int f = 0; f < j->nf; ++f) {
+    dst[f] = (float*)(base + (size_t)f * n * 4);
+    e = cudaMemcpyAsync(dst[f], src[f], (size_t)n * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail((int)e, "serving: H2D");
+  }
+  float* rgb = (float*)(base + (size_t)j->nf * n * 4);
+  uint8_t* tab = (uint8_t*)(rgb + 3 * n);
+  const size_t cb = j->chunks.size() * sizeof(Chunk);
+  const size_t pb = j->mats.size() * sizeof(void*);
+  std::vector<uint8_t> host(cb + 2 * pb);
+  std::memcpy(host.data(), j->chunks.data(), cb);
+  for (size_t k = 0; k < j->mats.size(); ++k) {
+    const void* p = j->mats[k]->pyramid;
+    const void* w = j->mats[k]->blob;
+    std::memcpy(host.data() + cb + k * sizeof(void*), &p, sizeof p);
+    std::memcpy(host.data() + cb + pb + k * sizeof(void*), &w, sizeof w);
+  }
+  e = cudaMemcpyAsync(tab, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "serving: table upload");
+  nam_queries dq{dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], dst[7], dst[8], dst[9]};
+  LaunchCommon L;
+  fill_launch(ctx, j->mats[0], &dq, 0, rgb, j->frame.flags, &L);
+  L.chunks = (const Chunk*)tab;
+  L.n_chunks = (int32_t)j->chunks.size();
+  L.mats.pyramid = (const void* const*)(tab + cb);
+  L.mats.weights = (const void* const*)(tab + cb + pb);
+  L.mats.nmat = (int32_t)j->mats.size();
+  if (ctx->fault_launch.exchange(false)) return fail(NAM_ERR_CUDA, "injected launch failure");
+  int le = launch_material(L, j->mats[0]->desc.precision, s);
+  if (le) return cuda_fail(le, "serving: launch");
+  e = cudaMemcpyAsync(j->frame.rgb_out, rgb, (size_t)n * 12, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "serving: D2H");
+  cudaFreeAsync(j->dev, s);
+  j->dev = nullptr;
+  e = cudaEventRecord(slot.done, s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "serving: event");
+  return NAM_OK;
+}
+
+static void scheduler(nam_ctx* ctx) {
+  ServeState* S = ctx->serve;
+  DeviceGuard g(ctx->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (true) {
+    bool progressed = false;
+    // completions
+    for (Slot& sl : S->slots) {
+      if (!sl.job) continue;
+      cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaErrorNotReady) continue;
+      Job* j = sl.job;
+      sl.job = nullptr;
+      S->in_flight--;
+      budget_release(ctx, j->bytes);
+      S->serving_bytes -= j->bytes;
+      finish_job(S, j, q == cudaSuccess ? NAM_OK : NAM_ERR_CUDA);
+      progressed = true;
+    }
+    if (S->stop && S->in_flight == 0) break;
+    // admissions, in arrival order
+    if (!S->stop && !ctx->fault_stall.load()) {
+      for (Slot& sl : S->slots) {
+        if (sl.job || S->queue.empty()) continue;
+        Job* j = S->queue.front();
+        if (!budget_reserve(ctx, j->bytes)) break;  // head of line waits for memory
+        S->queue.pop_front();
+        S->serving_bytes += j->bytes;
+        S->in_flight++;
+        j->st.admit_s = nam_now();
+        sl.job = j;
+        lk.unlock();
+        j->st.start_s = nam_now();
+        nam_status st = launch_job(ctx, sl, j);
+        lk.lock();
+        if (st != NAM_OK) {
+          if (j->dev) cudaFreeAsync(j->dev, sl.stream);
+          cudaStreamSynchronize(sl.stream);
+          sl.job = nullptr;
+          S->in_flight--;
+          budget_release(ctx, j->bytes);
+          S->serving_bytes -= j->bytes;
+          finish_job(S, j, st);
+        }
+        progressed = true;
+      }
+    }
+    if (!progressed) S->cv.wait_for(lk, std::chrono::microseconds(S->in_flight ? 20 : 2000));
+  }
+}
+
+static nam_status ensure_serving(nam_ctx* ctx) {
+  std::lock_guard<std::mutex> lk(ctx->serve_mu);
+  if (ctx->serve) return NAM_OK;
+  DeviceGuard g(ctx->device);
+  ServeState* S = new ServeState();
+  S->slots.resize(ctx->serve_streams);
+  for (Slot& sl : S->slots) {
+    cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      for (Slot& x : S->slots) {
+        if (x.stream) cudaStreamDestroy(x.stream);
+        if (x.done) cudaEventDestroy(x.done);
+      }
+      delete S;
+      return cuda_fail((int)e, "serving: stream creation");
+    }
+  }
+  ctx->serve = S;
+  S->thread = std::thread(scheduler, ctx);
+  return NAM_OK;
+}
+
+void nam::serve_stop(nam_ctx* ctx) {
+  ServeState* S;
+  {
+    std::lock_guard<std::mutex> lk(ctx->serve_mu);
+    S = ctx->serve;
+    if (!S) return;
+  }
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    while (!S->queue.empty()) {
+      Job* j = S->queue.front();
+      S->queue.pop_front();
+      finish_job(S, j, NAM_ERR_CANCELLED);
+    }
+  }
+  ctx->fault_stall.store(false);
+  S->cv.notify_all();
+  S->thread.join();
+  DeviceGuard g(ctx->device);
+  for (Slot& sl : S->slots) {
+    cudaStreamSynchronize(sl.stream);
+    cudaStreamDestroy(sl.stream);
+    cudaEventDestroy(sl.done);
+  }
+  for (auto& kv : S->jobs) delete kv.second;
+  delete S;
+  ctx->serve = nullptr;
+}
+
+extern "C" nam_status nam_submit(nam_ctx* ctx, const nam_frame* f, nam_ticket* out) {
+  if (!ctx || !f || !out) return fail(NAM_ERR_INVALID_ARG, "nam_submit: NULL argument");
+  *out = 0;
+  if (f->n_queries <= 0 || f->n_items <= 0 || !f->items || !f->rgb_out)
+    return fail(NAM_ERR_INVALID_ARG, "nam_submit: empty frame");
+  nam_status st = check_multi(ctx, f->materials, f->n_materials);
+  if (st) return st;
+  st = check_queries(f->materials[0], &f->q);
+  if (st) return st;
+  Job* j = new Job();
+  j->frame = *f;
+  j->mats.assign(f->materials, f->materials + f->n_materials);
+  for (int32_t i = 0; i < f->n_items; ++i) {
+    const nam_work_item& it = f->items[i];
+    if (it.material < 0 || it.material >= f->n_materials || it.count < 0 || it.start < 0 ||
+        it.start + it.count > f->n_queries) {
+      delete j;
+      return fail(NAM_ERR_INVALID_ARG, "nam_submit: bad work item %d", i);
+    }
+  }
+  build_chunks(f->items, f->n_items, &j->chunks);
+  j->nf = f->materials[0]->desc.filter == NAM_FILTER_STOCHASTIC ? 10 : 9;
+  const int64_t n = f->n_queries;
+  j->bytes = (uint64_t)n * 4 * j->nf + (uint64_t)n * 12 + j->chunks.size() * sizeof(Chunk) +
+             2 * j->mats.size() * sizeof(void*) + 256;
+  j->st.arrival_s = f->arrival_s > 0 ? f->arrival_s : nam_now();
+  j->st.n_queries = n;
+  st = ensure_serving(ctx);
+  if (st) {
+    delete j;
+    return st;
+  }
+  ServeState* S = ctx->serve;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (ctx->budget) {
+      const uint64_t other = ctx->resident.load() - S->serving_bytes;
+      if (j->bytes + other > ctx->budget) {
+        delete j;
+        return fail(NAM_ERR_BUDGET, "nam_submit: frame needs %llu bytes, budget leaves %llu",
+                    (unsigned long long)j->bytes, (unsigned long long)(ctx->budget - std::min(other, ctx->budget)));
+      }
+    }
+    if ((int)S->queue.size() >= ctx->serve_queue_depth) {
+      delete j;
+      return fail(NAM_ERR_BUSY, "nam_submit: admission queue full");
+    }
+    j->ticket = S->next_ticket++;
+    S->jobs[j->ticket] = j;
+    S->queue.push_back(j);
+    *out = j->ticket;
+  }
+  S->cv.notify_all();
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_poll(nam_ctx* ctx, nam_ticket t, int32_t* done, nam_frame_stats* st) {
+  if (!ctx || !done) return fail(NAM_ERR_INVALID_ARG, "nam_poll: NULL argument");
+  ServeState* S = ctx->serve;
+  if (!S) return fail(NAM_ERR_NOT_FOUND, "nam_poll: no frames submitted");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(t);
+  if (it == S->jobs.end()) return fail(NAM_ERR_NOT_FOUND, "nam_poll: unknown ticket");
+  *done = it->second->done ? 1 : 0;
+  if (st) *st = it->second->st;
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_wait(nam_ctx* ctx, nam_ticket t, uint64_t timeout_ns, nam_frame_stats* st) {
+  if (!ctx) return fail(NAM_ERR_INVALID_ARG, "nam_wait: NULL context");
+  ServeState* S = ctx->serve;
+  if (!S) return fail(NAM_ERR_NOT_FOUND, "nam_wait: no frames submitted");
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(t);
+  if (it == S->jobs.end()) return fail(NAM_ERR_NOT_FOUND, "nam_wait: unknown ticket");
+  Job* j = it->second;
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::nanoseconds(timeout_ns ? timeout_ns : ctx->timeout_ns);
+  while (!j->done) {
+    if (S->done_cv.wait_until(lk, deadline) == std::cv_status::timeout && !j->done)
+      return fail(NAM_ERR_TIMEOUT, "nam_wait: ticket %llu not done", (unsigned long long)t);
+  }
+  if (st) *st = j->st;
+  if (j->st.status != NAM_OK) return fail(j->st.status, "frame %llu failed: %s", (unsigned long long)t, nam_status_string(j->st.status));
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_cancel(nam_ctx* ctx, nam_ticket t) {
+  if (!ctx) return fail(NAM_ERR_INVALID_ARG, "nam_cancel: NULL context");
+  ServeState* S = ctx->serve;
+  if (!S) return fail(NAM_ERR_NOT_FOUND, "nam_cancel: no frames submitted");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->jobs.find(t);
+  if (it == S->jobs.end()) return fail(NAM_ERR_NOT_FOUND, "nam_cancel: unknown ticket");
+  Job* j = it->second;
+  if (j->done) return NAM_OK;
+  auto qi = std::find(S->queue.begin(), S->queue.end(), j);
+  if (qi == S->queue.end()) return fail(NAM_ERR_BUSY, "nam_cancel: frame already on the GPU");
+  S->queue.erase(qi);
+  finish_job(S, j, NAM_ERR_CANCELLED);
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_get_stats(nam_ctx* ctx, nam_stats* out) {
+  if (!ctx || !out) return fail(NAM_ERR_INVALID_ARG, "nam_get_stats: NULL argument");
+  std::memset(out, 0, sizeof *out);
+  out->resident_bytes = ctx->resident.load();
+  out->budget_bytes = ctx->budget;
+  ServeState* S = ctx->serve;
+  if (!S) return NAM_OK;
+  std::lock_guard<std::mutex> lk(S->mu);
+  out->queued = (int64_t)S->queue.size();
+  out->in_flight = S->in_flight;
+  out->completed = S->completed;
+  out->failed = S->failed;
+  out->queries_completed = S->queries_completed;
+  if (!S->latencies_ms.empty()) {
+    std::vector<double> v(S->latencies_ms.begin(), S->latencies_ms.end());
+    std::sort(v.begin(), v.end());
+    auto pct = [&](double p) {
+      double pos = p * (v.size() - 1);
+      size_t lo = (size_t)pos;
+      size_t hi = std::min(lo + 1, v.size() - 1);
+      return v[lo] + (v[hi] - v[lo]) * (pos - lo);
+    };
+    out->p50_latency_ms = pct(0.50);
+    out->p99_latency_ms = pct(0.99);
+  }
+  if (S->last_finish > S->first_arrival && S->first_arrival >= 0)
+    out->evals_per_s = S->queries_completed / (S->last_finish - S->first_arrival);
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_inject_fault(nam_ctx* ctx, int32_t fault) {
+  if (!ctx) return fail(NAM_ERR_INVALID_ARG, "NULL context");
+  switch (fault) {
+    case NAM_FAULT_NONE:
+      ctx->fault_alloc = false;
+      ctx->fault_launch = false;
+      ctx->fault_stall = false;
+      break;
+    case NAM_FAULT_ALLOC: ctx->fault_alloc = true; break;
+    case NAM_FAULT_LAUNCH: ctx->fault_launch = true; break;
+    case NAM_FAULT_STALL: ctx->fault_stall = true; break;
+    default: return fail(NAM_ERR_INVALID_ARG, "unknown fault %d", fault);
+  }
+  if (ctx->serve) ctx->serve->cv.notify_all();
+  return NAM_OK;
+}

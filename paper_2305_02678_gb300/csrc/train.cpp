@@ -1,0 +1,111 @@
+// C ABI: reverse mode and the training step (Sec. 5.2).
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "nam_ctx.h"
+
+using namespace nam;
+
+static nam_status check_trainable(nam_ctx* ctx, nam_material m) {
+  if (!ctx || !m) return fail(NAM_ERR_INVALID_ARG, "NULL context or material");
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->materials.count(m)) return fail(NAM_ERR_NOT_FOUND, "unknown material");
+  }
+  if (!m->desc.trainable) return fail(NAM_ERR_UNSUPPORTED, "material is not trainable");
+  if (m->shape.NH != 2) return fail(NAM_ERR_UNSUPPORTED, "backward supports two hidden layers");
+  return NAM_OK;
+}
+
+static void fill_bwd(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n, const float* grad_rgb,
+                     float* grad_params, float* grad_pyramid, uint32_t flags, BackwardArgs* a) {
+  std::memset(a, 0, sizeof *a);
+  a->pyr = m->pyr;
+  a->shape = m->shape;
+  a->q = QueryPtrs{q->u, q->v, q->lod, q->wix, q->wiy, q->wiz, q->wox, q->woy, q->woz, q->xi};
+  a->n = n;
+  a->pyramid = m->pyramid;
+  a->params = m->params;
+  a->grad_rgb = grad_rgb;
+  a->grad_params = grad_params;
+  a->grad_pyramid = grad_pyramid;
+  a->flags = flags;
+  a->num_sms = ctx->num_sms;
+}
+
+extern "C" nam_status nam_backward(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
+                                   const float* grad_rgb, float* grad_params, float* grad_pyramid, void* stream,
+                                   uint32_t flags) {
+  nam_status st = check_trainable(ctx, m);
+  if (st) return st;
+  if (n < 0) return fail(NAM_ERR_INVALID_ARG, "n < 0");
+  if (n == 0) return NAM_OK;
+  if (!grad_rgb || !grad_params) return fail(NAM_ERR_INVALID_ARG, "NULL gradient buffer");
+  st = check_queries(m, q);
+  if (st) return st;
+  DeviceGuard g(ctx->device);
+  BackwardArgs a;
+  fill_bwd(ctx, m, q, n, grad_rgb, grad_params, grad_pyramid, flags, &a);
+  int e = launch_backward(a, stream);
+  if (e) return cuda_fail(e, "nam_backward: launch");
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
+                                     int64_t n, const nam_adam* opt, float* loss_out, void* stream, uint32_t flags) {
+  nam_status st = check_trainable(ctx, m);
+  if (st) return st;
+  if (n <= 0) return fail(NAM_ERR_INVALID_ARG, "n must be > 0");
+  if (!target_rgb || !opt) return fail(NAM_ERR_INVALID_ARG, "NULL target or optimiser settings");
+  if (opt->step < 1) return fail(NAM_ERR_INVALID_ARG, "Adam step is 1-based");
+  st = check_queries(m, q);
+  if (st) return st;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // per-material scratch: rgb [n][3], dL/drgb [n][3], loss accumulator
+  const size_t need = (size_t)n * 24 + 256;
+  if (need > m->train_scratch_bytes) {
+    if (m->train_scratch) {
+      cudaStreamSynchronize(s);
+      cudaFree(m->train_scratch);
+      budget_release(ctx, m->train_scratch_bytes);
+      m->info.resident_bytes -= m->train_scratch_bytes;
+      m->train_scratch = nullptr;
+      m->train_scratch_bytes = 0;
+    }
+    if (!budget_reserve(ctx, need)) return fail(NAM_ERR_BUDGET, "training scratch needs %zu bytes", need);
+    int e = dev_alloc(ctx, &m->train_scratch, need);
+    if (e) {
+      budget_release(ctx, need);
+      return cuda_fail(e, "nam_train_step: scratch");
+    }
+    m->train_scratch_bytes = need;
+    m->info.resident_bytes += need;
+  }
+  float* loss_acc = (float*)m->train_scratch;
+  float* rgb = loss_acc + 64;
+  float* grad_rgb = rgb + 3 * n;
+  cudaMemsetAsync(loss_acc, 0, sizeof(float), s);
+  LaunchCommon L;
+  fill_launch(ctx, m, q, n, rgb, flags, &L);
+  int e = launch_eval_f32(L, s);
+  if (!e) e = launch_loss(rgb, target_rgb, n, grad_rgb, loss_acc, s);
+  BackwardArgs a;
+  fill_bwd(ctx, m, q, n, grad_rgb, m->grad, m->grad + m->n_params, flags, &a);
+  if (!e) e = launch_backward(a, s);
+  const int64_t np = m->n_params, nt = m->pyr.texels * 8;
+  if (!e)
+    e = launch_adam(m->params, m->grad, m->adam_m, m->adam_v, np, opt->lr_params, opt->beta1, opt->beta2, opt->eps,
+                    opt->step, s);
+  if (!e)
+    e = launch_adam((float*)m->pyramid, m->grad + np, m->adam_m + np, m->adam_v + np, nt, opt->lr_pyramid,
+                    opt->beta1, opt->beta2, opt->eps, opt->step, s);
+  if (e) return cuda_fail(e, "nam_train_step: launch");
+  if (loss_out) {
+    cudaError_t ce = cudaMemcpyAsync(loss_out, loss_acc, sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_train_step: loss readback");
+  }
+  return NAM_OK;
+}

@@ -1,0 +1,270 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (max over queries and channels of |g - o| / max(|o|, tau), tau the
+RMS of the oracle's outputs):
+  FP32 path        1e-5 against the oracle with the same FP32 parameters;
+  FP16 path        2e-3 against the oracle evaluating the same FP16
+                   parameters with the same FP16 rounding of the decoder's
+                   MMA operands (what FP16 inference computes); the error
+                   against the unrounded oracle is reported.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import to_device
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 1e-5
+TOL_F16 = 2e-3
+
+
+@pytest.fixture(scope="module")
+def w1():
+    return W.workload(1)
+
+
+@pytest.fixture(scope="module")
+def w2():
+    return W.workload(2)
+
+
+@pytest.fixture(scope="module")
+def w2_small():
+    return W.workload(2, scale=1 / 8)
+
+
+def _eval(ctx, w, precision, q=None, filt=0, addr=0, flags=0, pyramid=None):
+    m = w["model"]
+    mat = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"] if pyramid is None else pyramid, m["frame"],
+                       m["decoder"], precision=precision, filter=filt, address=addr)
+    q = w["queries"] if q is None else q
+    if len(q["u"]) == 0:
+        import torch
+        out = torch.empty((0, 3), device="cuda")
+        from paper_2305_02678_gb300 import binding as B
+        B.nam_eval(ctx.h, mat.h, to_device(q), 0, out)
+        res = out.cpu().numpy()
+    else:
+        res = mat.eval(to_device(q), flags=flags).cpu().numpy()
+    mat.destroy()
+    ctx.check()
+    return res
+
+
+def _oracle(oracle, w, q=None, params="master", act_round=0, filt=0, addr=0, cos=False, pyramid=None):
+    m = w["model"]
+    om = oracle.Model(w["W0"], w["H0"], w["L"], w["pyramid"] if pyramid is None else pyramid, m["frame"],
+                      m["decoder"], filter=filt, address=addr, out_cosine=cos, params=params, act_round=act_round)
+    return oracle.eval(om, w["queries"] if q is None else q)
+
+
+@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("addr", [0, 1])
+@pytest.mark.parametrize("cos", [False, True])
+def test_fp32_small_workload(gctx, oracle, w1, filt, addr, cos):
+    from paper_2305_02678_gb300 import binding as B
+    g = _eval(gctx, w1, B.NAM_PREC_F32, filt=filt, addr=addr, flags=B.NAM_OUT_COSINE if cos else 0)
+    o = _oracle(oracle, w1, filt=filt, addr=addr, cos=cos)
+    err = oracle.relative_error(g, o)
+    print(f"fp32 65536q filt={filt} addr={addr} cos={cos}: max {err[0]:.3e} mean {err[1]:.3e}")
+    assert err[0] <= TOL_F32
+
+
+@pytest.mark.parametrize("filt", [0, 1])
+def test_fp32_frame_decoder(gctx, oracle, w2_small, filt):
+    from paper_2305_02678_gb300 import binding as B
+    g = _eval(gctx, w2_small, B.NAM_PREC_F32, filt=filt)
+    o = _oracle(oracle, w2_small, filt=filt)
+    err = oracle.relative_error(g, o)
+    print(f"fp32 frame 14-64-64-3 filt={filt}: max {err[0]:.3e} mean {err[1]:.3e}")
+    assert err[0] <= TOL_F32
+
+
+def test_fp16_1080p_full(gctx, oracle, w2):
+    """The benchmark workload at full size: 1920x1080 queries, 2048^2 x 8
+    FP16 pyramid, frame MLP 8-16-6, decoder 14-64-64-3."""
+    from paper_2305_02678_gb300 import binding as B
+    g = _eval(gctx, w2, B.NAM_PREC_F16)
+    emu = _oracle(oracle, w2, params="fp16", act_round=oracle.ROUND_FP16)
+    err = oracle.relative_error(g, emu)
+    exact = _oracle(oracle, w2, params="fp16")
+    err_exact = oracle.relative_error(g, exact)
+    print(f"fp16 1080p vs fp16-operand oracle: max {err[0]:.3e} mean {err[1]:.3e}; "
+          f"vs unrounded oracle: max {err_exact[0]:.3e} mean {err_exact[1]:.3e}")
+    assert err[0] <= TOL_F16
+    assert err_exact[1] <= 2e-3
+
+
+@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("addr", [0, 1])
+def test_fp16_filters_and_addressing(gctx, oracle, w2_small, filt, addr):
+    from paper_2305_02678_gb300 import binding as B
+    g = _eval(gctx, w2_small, B.NAM_PREC_F16, filt=filt, addr=addr)
+    o = _oracle(oracle, w2_small, params="fp16", act_round=oracle.ROUND_FP16, filt=filt, addr=addr)
+    err = oracle.relative_error(g, o)
+    print(f"fp16 filt={filt} addr={addr}: max {err[0]:.3e}")
+    assert err[0] <= TOL_F16
+
+
+@pytest.mark.parametrize("H", [16, 32, 64])
+@pytest.mark.parametrize("frame", [False, True])
+@pytest.mark.parametrize("latent", ["f16", "f32"])
+def test_fp16_shapes(gctx, oracle, H, frame, latent):
+    from paper_2305_02678_gb300 import binding as B
+    rng = W.rng_streams(100 + H, 3)
+    W0 = H0 = 128
+    L = 8
+    dt = np.float16 if latent == "f16" else np.float32
+    pyr = W.make_pyramid(rng[0], W0, H0, L, dtype=dt)
+    model = W.make_model(rng[1], (14, H, H, 3), (8, 16, 6) if frame else None)
+    q = W.uniform_queries(rng[2], 20000, 7.5)
+    w = dict(W0=W0, H0=H0, L=L, pyramid=pyr, model=model, queries=q)
+    g = _eval(gctx, w, B.NAM_PREC_F16)
+    o = _oracle(oracle, w, params="fp16", act_round=oracle.ROUND_FP16)
+    err = oracle.relative_error(g, o)
+    print(f"fp16 H={H} frame={frame} latent={latent}: max {err[0]:.3e}")
+    assert err[0] <= TOL_F16
+
+
+@pytest.mark.parametrize("n", [0, 1, 31, 33, 127, 128, 129, 1000, 4097])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ragged_sizes(gctx, oracle, w2_small, n, precision):
+    q = W.slice_queries(w2_small["queries"], 5, n)
+    g = _eval(gctx, w2_small, precision, q=q)
+    assert g.shape == (n, 3)
+    if n == 0:
+        return
+    kw = dict(params="fp16", act_round=oracle.ROUND_FP16) if precision == 1 else {}
+    o = _oracle(oracle, w2_small, q=q, **kw)
+    err = oracle.relative_error(g, o)
+    assert err[0] <= (TOL_F16 if precision == 1 else TOL_F32)
+
+
+def _edge_queries(W0, L):
+    """uv on texel centres and edges, outside [0,1], huge; lod at and beyond
+    the level range, integer, NaN; xi at 0 and just below 1."""
+    us, vs, lods, xis = [], [], [], []
+    for lev in range(L):
+        w = max(1, W0 >> lev)
+        for i in (0, 1, w // 2, w - 1):
+            for off in (0.0, 0.5, 1.0):
+                us.append((i + off) / w)
+                vs.append((w - 1 - i + off) / w)
+                lods.append(float(lev))
+                xis.append(0.0)
+    extra_u = [-1.0, -0.25, 1.0, 1.25, 7.5, -33.3, 1e4, 0.999999]
+    for u in extra_u:
+        for lod in (-5.0, 0.0, 0.25, L - 1.0, L - 0.5, L + 3.0, float("nan")):
+            for xi in (0.0, 0.9999):
+                us.append(u)
+                vs.append(1.0 - u)
+                lods.append(lod)
+                xis.append(xi)
+    n = len(us)
+    rng = np.random.default_rng(9)
+    wi = W.cosine_hemisphere(rng, n)
+    wo = W.cosine_hemisphere(rng, n)
+    f = np.float32
+    return {"u": np.array(us, f), "v": np.array(vs, f), "lod": np.array(lods, f),
+            "wix": wi[0].astype(f), "wiy": wi[1].astype(f), "wiz": wi[2].astype(f),
+            "wox": wo[0].astype(f), "woy": wo[1].astype(f), "woz": wo[2].astype(f), "xi": np.array(xis, f)}
+
+
+@pytest.mark.parametrize("filt", [0, 1])
+@pytest.mark.parametrize("addr", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_edge_coordinates(gctx, oracle, filt, addr, precision):
+    rng = W.rng_streams(55, 2)
+    W0 = H0 = 64
+    L = 7
+    pyr = W.make_pyramid(rng[0], W0, H0, L, dtype=np.float16)
+    model = W.make_model(rng[1], (14, 64, 64, 3), (8, 16, 6))
+    q = _edge_queries(W0, L)
+    w = dict(W0=W0, H0=H0, L=L, pyramid=pyr, model=model, queries=q)
+    g = _eval(gctx, w, precision, filt=filt, addr=addr)
+    kw = dict(params="fp16", act_round=oracle.ROUND_FP16) if precision == 1 else {}
+    o = _oracle(oracle, w, filt=filt, addr=addr, **kw)
+    err = oracle.relative_error(g, o)
+    assert np.isfinite(g).all()
+    assert err[0] <= (TOL_F16 if precision == 1 else TOL_F32), err
+
+
+def test_non_power_of_two_pyramid(gctx, oracle):
+    """Level sizes that are not powers of two: the FP32 texel coordinate
+    u W - 1/2 is then rounded (error <= W 2^-24 in texels), so the bound is
+    that rounding times the largest texel difference, not 1e-5."""
+    rng = W.rng_streams(56, 3)
+    W0, H0, L = 48, 40, 6
+    pyr = W.make_pyramid(rng[0], W0, H0, L, dtype=np.float32)
+    model = W.make_model(rng[1], (14, 32, 32, 3), None)
+    q = W.uniform_queries(rng[2], 5000, 5.0)
+    w = dict(W0=W0, H0=H0, L=L, pyramid=pyr, model=model, queries=q)
+    for addr in (0, 1):
+        g = _eval(gctx, w, 0, addr=addr)
+        o = _oracle(oracle, w, addr=addr)
+        assert oracle.relative_error(g, o)[0] <= 1e-4
+
+
+def test_deterministic_and_host_path_identical(gctx, w2_small):
+    import torch
+    m = w2_small["model"]
+    mat = gctx.material(w2_small["W0"], w2_small["H0"], w2_small["L"], w2_small["pyramid"], m["frame"], m["decoder"])
+    dq = to_device(w2_small["queries"])
+    a = mat.eval(dq).cpu().numpy()
+    b = mat.eval(dq).cpu().numpy()
+    assert np.array_equal(a, b)
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in w2_small["queries"].items()}
+    h = mat.eval_host(pinned)
+    assert np.array_equal(a, h)
+    mat.destroy()
+
+
+def test_multi_material_matches_single(gctx, oracle):
+    """Work items over several materials give bit-identical results to
+    evaluating each item's queries with its material alone."""
+    import torch
+    from paper_2305_02678_gb300 import binding as B
+    rng = W.rng_streams(57, 8)
+    W0 = H0 = 256
+    L = 9
+    mats, models, pyrs = [], [], []
+    for k in range(3):
+        pyr = W.make_pyramid(rng[k], W0, H0, L, dtype=np.float16)
+        model = W.make_model(rng[3 + k], (14, 64, 64, 3), (8, 16, 6))
+        pyrs.append(pyr)
+        models.append(model)
+        mats.append(gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"]))
+    q = W.uniform_queries(rng[6], 10000, 8.0)
+    items = [(0, 4096, 0), (4096, 1000, 2), (5096, 77, 1), (5173, 4827, 0)]
+    dq = to_device(q)
+    out = torch.zeros((10000, 3), device="cuda")
+    B.nam_eval_multi(gctx.h, [m.h for m in mats], dq, items, out, torch.cuda.current_stream())
+    got = out.cpu().numpy()
+    for s, c, k in items:
+        sub = {f: t[s:s + c] for f, t in dq.items()}
+        ref = mats[k].eval(sub).cpu().numpy()
+        assert np.array_equal(got[s:s + c], ref)
+    for m in mats:
+        m.destroy()
+    gctx.check()
+
+
+def test_invalid_arguments(gctx, w2_small):
+    from paper_2305_02678_gb300 import binding as B
+    m = w2_small["model"]
+    mat = gctx.material(w2_small["W0"], w2_small["H0"], w2_small["L"], w2_small["pyramid"], m["frame"], m["decoder"],
+                        filter=B.NAM_FILTER_STOCHASTIC)
+    dq = to_device(W.slice_queries(w2_small["queries"], 0, 100))
+    dq.pop("xi")
+    import torch
+    out = torch.empty((100, 3), device="cuda")
+    with pytest.raises(B.NamError) as e:
+        B.nam_eval(gctx.h, mat.h, dq, 100, out)
+    assert e.value.status == B.NAM_ERR_INVALID_ARG
+    mat.destroy()
+    with pytest.raises(B.NamError) as e:
+        gctx.material(w2_small["W0"], w2_small["H0"], w2_small["L"], w2_small["pyramid"], m["frame"],
+                      [(np.zeros((48, 14), np.float32), np.zeros(48, np.float32))] + m["decoder"][1:])
+    assert e.value.status in (B.NAM_ERR_UNSUPPORTED, B.NAM_ERR_INVALID_ARG)
