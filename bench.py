@@ -1,0 +1,511 @@
+#!/usr/bin/env python3
+"""Benchmark: batched neural-BRDF evaluation on one GB300 (or N replicas).
+
+One step = one pass of the whole evaluation path (latent fetch, frame MLP,
+frame build, direction transform, decoder MLP, RGB store) over one 1920x1080
+frame of queries (2,073,600) with the FP16 tensor-core path: 2048^2 x 8 FP16
+latent pyramid with 12 levels, frame MLP 8-16-6, decoder 14-64-64-3, uv from
+a random smooth warp, lod from the warp's footprint, cosine-hemisphere
+directions (synthetic, seeded).  The L2 is flushed (256 MiB write) before
+every timed step, outside the timed kernel.
+
+Printed (rank 0), one JSON line: evals/s of that step (value), the same
+through the C ABI with host buffers (e2e), the roofline of the kernel, the
+FP32 and FP8 forms of the same workload with their speed-ups, the serving
+stream's p50/p99 frame latency, the FP64 oracle on the host cores
+(cpu_baseline) and the clocks seen while timing.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--no-serve] [--serve-frames F] [--no-sweep]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "neural-BRDF evals/s FP16/FP8 vs plain FP32 at stated error; p50/p99 frame ms"
+WORKLOAD = "fp16-2048sq-1920x1080"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-frames", type=int, default=720)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas: no data-path collective)
+# ----------------------------------------------------------------------------
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ----------------------------------------------------------------------------
+# workload
+# ----------------------------------------------------------------------------
+def workload():
+    import workloads as W
+    return W.workload(2)
+
+
+def unique_texel_bytes(w):
+    """Compulsory texel bytes of one launch: distinct texels the 1080p frame
+    touches (both levels of every trilinear fetch) x 16 bytes."""
+    q = w["queries"]
+    W0, H0, L = w["W0"], w["H0"], w["L"]
+    sizes = [(max(1, W0 >> l), max(1, H0 >> l)) for l in range(L)]
+    offs = np.cumsum([0] + [a * b for a, b in sizes])
+    lod = np.nan_to_num(q["lod"].astype(np.float32), nan=0.0)
+    l = np.clip(lod, 0, L - 1)
+    l0 = np.floor(l).astype(np.int64)
+    t = l - l0
+    l1 = np.minimum(l0 + 1, L - 1)
+    idx = []
+    for lev_arr, keep in ((l0, np.ones_like(t, bool)), (l1, t != 0)):
+        u = q["u"][keep].astype(np.float32)
+        v = q["v"][keep].astype(np.float32)
+        lv = lev_arr[keep]
+        Wl = np.array([s[0] for s in sizes])[lv]
+        Hl = np.array([s[1] for s in sizes])[lv]
+        x = u * Wl.astype(np.float32) - np.float32(0.5)
+        y = v * Hl.astype(np.float32) - np.float32(0.5)
+        x0 = np.floor(x).astype(np.int64)
+        y0 = np.floor(y).astype(np.int64)
+        for dx in (0, 1):
+            for dy in (0, 1):
+                xi = np.mod(x0 + dx, Wl)
+                yi = np.mod(y0 + dy, Hl)
+                idx.append(offs[lv] + yi * Wl + xi)
+    return int(np.unique(np.concatenate(idx)).size) * 16
+
+
+def kernel_sha():
+    h = hashlib.sha256()
+    for f in ("fwd_tc.cu", "common.cuh", "tc_ptx.cuh"):
+        with open(os.path.join(ROOT, "paper_2305_02678_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the FP16 kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "eval_tc_fp16_1920x1080.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != kernel_sha():
+        return None
+    return float(m.group(1))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# ----------------------------------------------------------------------------
+# timing helpers
+# ----------------------------------------------------------------------------
+def time_launches(fn, steps, warmup, flush, stream):
+    """Per-step CUDA-event times (ms) of fn(), L2 flushed before each step."""
+    import torch
+    for _ in range(warmup):
+        flush()
+        fn()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        times.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    import workloads as W
+    from paper_2305_02678_gb300 import Context
+    from paper_2305_02678_gb300 import binding as B
+
+    world, rank, local = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    w = workload()
+    q = w["queries"]
+    n = int(q["u"].shape[0])
+    m = w["model"]
+    stream = torch.cuda.current_stream(dev)
+    ctx = Context(local)
+    mat16 = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"], precision=B.NAM_PREC_F16)
+    dq = {k: torch.from_numpy(v).to(dev) for k, v in q.items() if k != "xi"}
+    out16 = torch.empty((n, 3), device=dev)
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush():
+        flush_buf.fill_(1.0)
+
+    def step16():
+        B.nam_eval(ctx.h, mat16.h, dq, n, out16, stream, 0)
+
+    # ---- headline: FP16 path, device-resident inputs --------------------
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    t_wall0 = time.perf_counter()
+    times = time_launches(step16, args.steps, args.warmup, flush, stream)
+    t_wall = time.perf_counter() - t_wall0
+    clk = clocks.stop()
+    barrier(world)
+    ms = statistics.fmean(times)
+    ms_max = max_over_ranks(world, ms, dev)
+    ctx.check()
+    value = world * n / (ms_max * 1e-3)
+
+    # ---- e2e: host buffers through the C ABI, copies inside the timed region
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in q.items() if k != "xi"}
+    host_out = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+
+    def step_host():
+        B.nam_eval_host(ctx.h, mat16.h, pinned, n, host_out, stream, 0)
+
+    e2e_times = time_launches(step_host, max(3, args.steps // 2), 2, flush, stream)
+    e2e_ms = max_over_ranks(world, statistics.fmean(e2e_times), dev)
+    h2d = sum(int(t.numel()) * 4 for t in pinned.values())
+    d2h = n * 12
+
+    # ---- roofline of the FP16 kernel ------------------------------------
+    hbm, tflops, peak_kind = measured_peaks()
+    texel_bytes = unique_texel_bytes(w)
+    io_bytes = n * (9 * 4 + 12)
+    weight_bytes = int(mat16.info.resident_bytes - w["pyramid"].nbytes - mat16.info.n_params * 4)
+    alg_bytes = io_bytes + texel_bytes + weight_bytes
+    alg_flops = 2 * n * (8 * 16 + 16 * 6 + 14 * 64 + 64 * 64 + 64 * 3)
+    t_s = ms * 1e-3
+    achieved = alg_bytes / t_s / 1e9
+    t_roof = max(alg_bytes / (hbm * 1e9), alg_flops / (tflops * 1e12))
+    roofline = {"bound": "hbm" if alg_bytes / (hbm * 1e9) >= alg_flops / (tflops * 1e12) else "tensor",
+                "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": profiled_traffic(), "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": alg_flops,
+                "tensor_time_at_peak_us": round(alg_flops / (tflops * 1e12) * 1e6, 2),
+                "roofline_time_us": round(t_roof * 1e6, 2), "kernel": "eval_tc_kernel<64,frame,f16 latents>"}
+
+    # ---- precision sweep on the same workload ----------------------------
+    sweep = {}
+    if not args.no_sweep:
+        mat32 = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"],
+                             precision=B.NAM_PREC_F32)
+        out32 = torch.empty((n, 3), device=dev)
+        t32 = time_launches(lambda: B.nam_eval(ctx.h, mat32.h, dq, n, out32, stream, 0),
+                            max(3, args.steps // 4), 2, flush, stream)
+        ms32 = statistics.fmean(t32)
+        sweep["fp32_evals_per_s"] = n / (ms32 * 1e-3)
+        sweep["fp32_ms"] = round(ms32, 4)
+        sweep["fp16_speedup_vs_fp32"] = round(ms32 / ms, 2)
+        mat32.destroy()
+        sweep["fp8"] = "not built"
+    # ---- serving stream ---------------------------------------------------
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = run_serving(local, args.serve_frames)
+
+    # ---- CPU baseline: the FP64 oracle on the host cores -------------------
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = cpu_baseline(w, out16.cpu().numpy(), args.cpu_seconds)
+
+    mat16.destroy()
+    ctx.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_max, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "queries_per_step": n, "pyramid": "2048x2048x8 fp16, 12 levels",
+                       "frame_mlp": "8-16-6", "decoder": "14-64-64-3", "filter": "trilinear",
+                       "l2": "flushed (256 MiB write) before every timed step, outside the timed kernel",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": round(world * n / (e2e_ms * 1e-3), 1), "unit": "evals/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
+            "gpu_launches": args.steps,
+            "roofline": roofline,
+            "precision_sweep": sweep,
+            "serving": serving,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "timed_region_wall_s": round(t_wall, 3),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30):
+    """Serving stream: Poisson frame arrivals at `rate`/s, resolutions drawn
+    from 720p/1080p/1440p/2160p, 16 FP16 materials (own 2048^2 x 8 pyramid
+    and 14-64-64-3 decoder each), one material per 64x64 tile drawn
+    uniformly, frames admitted under a 40 GB budget.  Frames go through
+    nam_submit with pinned host inputs; latency = finish - arrival."""
+    import ctypes as C
+
+    import torch
+
+    import workloads as W
+    from paper_2305_02678_gb300 import Context
+    from paper_2305_02678_gb300 import binding as B
+
+    rngs = W.rng_streams(W.SEEDS[5], 2 * n_mat + 3)
+    ctx = Context(device, hbm_budget_bytes=budget, serve_streams=4, serve_queue_depth=1024)
+    mats = []
+    for k in range(n_mat):
+        pyr = W.make_pyramid(rngs[k], 2048, 2048, 12, dtype=np.float16)
+        model = W.make_model(rngs[n_mat + k], (14, 64, 64, 3), (8, 16, 6))
+        mats.append(ctx.material(2048, 2048, 12, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_F16))
+    mat_arr = (C.c_void_p * n_mat)(*[m.h for m in mats])
+    res = [(1280, 720), (1920, 1080), (2560, 1440), (3840, 2160)]
+    frames = []
+    for (wd, ht) in res:
+        q = W.warp_queries(rngs[2 * n_mat], wd, ht, 2048, 2048, order="tile")
+        pinned = {k: torch.from_numpy(v).pin_memory() for k, v in q.items() if k != "xi"}
+        out = torch.empty((wd * ht, 3), dtype=torch.float32).pin_memory()
+        tiles = W.tile_ranges(wd, ht)
+        frames.append((wd * ht, pinned, out, tiles))
+    rng = rngs[2 * n_mat + 1]
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_frames))
+    which = rng.integers(0, len(res), n_frames)
+    keep = []
+    tickets = []
+    t0 = B.nam_now() + 0.05
+    for i in range(n_frames):
+        n, pinned, out, tiles = frames[which[i]]
+        items = (B.nam_work_item * len(tiles))(*[B.nam_work_item(s, c, int(m)) for (s, c), m in
+                                                 zip(tiles, rng.integers(0, n_mat, len(tiles)))])
+        f = B.nam_frame()
+        f.n_queries = n
+        f.q = B.make_queries(pinned)
+        f.items = C.addressof(items)
+        f.n_items = len(tiles)
+        f.n_materials = n_mat
+        f.materials = C.addressof(mat_arr)
+        f.rgb_out = out.data_ptr()
+        f.flags = 0
+        f.arrival_s = t0 + arrivals[i]
+        keep.append(items)
+        now = B.nam_now()
+        if f.arrival_s > now:
+            time.sleep(f.arrival_s - now)
+        tickets.append(B.nam_submit(ctx.h, f))
+    failed = 0
+    for t in tickets:
+        st, _ = B.nam_wait(ctx.h, t, 60_000_000_000)
+        failed += st != 0
+    stats = ctx.stats()
+    out = {"frames": n_frames, "failed": int(failed), "rate_fps": rate, "p50_frame_ms": round(stats.p50_latency_ms, 3),
+           "p99_frame_ms": round(stats.p99_latency_ms, 3), "evals_per_s": round(stats.evals_per_s, 1),
+           "offered_evals_per_s": round(rate * float(np.mean([r[0] * r[1] for r in res])), 1),
+           "materials": n_mat, "budget_bytes": budget, "resident_bytes_materials": int(sum(m.info.resident_bytes for m in mats)),
+           "latency": "nam_now() finish - scheduled Poisson arrival; host->device copy, kernel and device->host copy included"}
+    for m in mats:
+        m.destroy()
+    ctx.close()
+    return out
+
+
+def cpu_baseline(w, gpu_out16, seconds):
+    """FP64 oracle (as it stands) on a bounded prefix of the same workload,
+    all host cores; also the GPU FP16 result's error on that sample."""
+    import oracle.oracle as O
+    O.build()
+    cores = os.cpu_count() or 1
+    m = w["model"]
+    om = O.Model.from_workload(w, params="fp16")
+    q = w["queries"]
+    n_total = int(q["u"].shape[0])
+    k = 65536
+    t0 = time.perf_counter()
+    import workloads as W
+    O.eval(om, W.slice_queries(q, 0, k), nthreads=cores)
+    dt = time.perf_counter() - t0
+    k2 = int(min(n_total, max(k, k * seconds / max(dt, 1e-6))))
+    sub = W.slice_queries(q, 0, k2)
+    t0 = time.perf_counter()
+    ref = O.eval(om, sub, nthreads=cores)
+    dt = time.perf_counter() - t0
+    emu = O.eval(O.Model.from_workload(w, params="fp16", act_round=O.ROUND_FP16), sub, nthreads=cores)
+    e_emu = O.relative_error(gpu_out16[:k2], emu)
+    e_exact = O.relative_error(gpu_out16[:k2], ref)
+    return {"value": round(k2 / dt, 1), "unit": "evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {k2} queries of the 1920x1080 workload, FP64, FP16-quantised parameters",
+            "seconds": round(dt, 2),
+            "gpu_fp16_error_on_sample": {"vs_fp16_operand_oracle_max": e_emu[0], "vs_unrounded_oracle_max": e_exact[0],
+                                         "vs_unrounded_oracle_mean": e_exact[1]}}
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 oracle timed on the host cores
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle.oracle as O
+    import workloads as W
+    O.build()
+    w = workload()
+    om = O.Model.from_workload(w, params="fp16")
+    cores = os.cpu_count() or 1
+    q = w["queries"]
+    n_total = int(q["u"].shape[0])
+    # each step: a bounded contiguous sample of the workload, cycling through it
+    k = 1 << 17
+    for i in range(args.warmup):
+        O.eval(om, W.slice_queries(q, (i * k) % (n_total - k), k), nthreads=cores)
+    times = []
+    for i in range(args.steps):
+        s = (i * k) % (n_total - k)
+        sub = W.slice_queries(q, s, k)
+        t0 = time.perf_counter()
+        O.eval(om, sub, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    ms = statistics.fmean(times) * 1e3
+    v = k / (ms * 1e-3)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "queries_per_step": k, "sample": "131072 consecutive queries per step"},
+        "cpu_baseline": {"value": round(v, 1), "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": "131072-query slices of the 1920x1080 workload, FP64 oracle, all host cores"},
+        "e2e": {"value": round(v, 1), "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -218,7 +218,8 @@ nam_status nam_eval_multi(nam_ctx* ctx, const nam_material* materials, int32_t n
 /* Reverse mode of nam_eval for a trainable (F32) material: given grad_rgb
  * (device [n][3]) accumulates (adds, does not zero) the gradient of
  * sum <grad_rgb, rgb> into grad_params (device [n_params], layout of the
- * masters) and grad_pyramid (device [texels][8]; may be NULL).  Weight
+ * masters) and grad_pyramid (device [texels][8], 16-byte aligned; may be
+ * NULL; a misaligned pointer is refused with NAM_ERR_INVALID_ARG).  Weight
  * gradients are reduced per CTA then added with one atomic per parameter and
  * CTA; pyramid gradients are scattered with atomics (tap weight x dL/dz).
  * ReLU'(0) = 0.  No gradient flows through the degenerate-frame fallbacks. */

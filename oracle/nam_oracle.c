@@ -322,6 +322,42 @@ typedef struct {
   double cosf;            /* output factor: 1 or max(0, wi.z) */
 } trace;
 
+/* ------------------------------------------------------------------------- */
+/* valid alternative roundings                                                */
+/* ------------------------------------------------------------------------- */
+/* A reduced-precision evaluation rounds FP32 values that are themselves
+ * rounded sums; when the exact value lies within that FP32 error of the
+ * midpoint between two representable neighbours, either neighbour is a
+ * correct result.  The rounding context records such ambiguous sites
+ * (decoder layer input `layer`, element j) and, on request, rounds chosen
+ * sites to the other neighbour, so that the oracle can list every valid
+ * result of a query. */
+#define ORC_MAX_SITES 32
+typedef struct {
+  int record;                       /* record ambiguous sites */
+  int nsites;
+  int site[ORC_MAX_SITES];
+  double dist[ORC_MAX_SITES];       /* |x - midpoint| / (gamma A) */
+  int nflip;
+  int flip[ORC_MAX_SITES];          /* sites rounded to the other neighbour */
+  double gamma;                     /* ambiguity band, relative to the sum's magnitude */
+} round_ctx;
+
+static uint16_t f16_step(uint16_t b, int up) {
+  int neg = (b >> 15) & 1;
+  uint16_t mag = b & 0x7fff;
+  if (mag == 0) return up ? 0x0001 : 0x8001;
+  if (up != neg) return b + 1;   /* away from zero */
+  return b - 1;                  /* towards zero */
+}
+static uint8_t e4m3_step(uint8_t b, int up) {
+  int neg = (b >> 7) & 1;
+  uint8_t mag = b & 0x7f;
+  if (mag == 0) return up ? 0x01 : 0x81;
+  if (up != neg) return (uint8_t)(mag >= 0x7e ? b : b + 1);
+  return b - 1;
+}
+
 /* Rounding of the decoder's MMA operands, emulated in FP64 so that the oracle
  * can evaluate the reduced-precision forms of the method step by step:
  * act_round 1 rounds every decoder-layer input to binary16 (FP16 inference,
@@ -340,7 +376,53 @@ static double round_act(const orc_model* m, double x, int dec_layer) {
   return x;
 }
 
-static void forward(const orc_model* m, const orc_queries* q, int64_t i, trace* tr) {
+/* round_act with ambiguity bookkeeping: A is the magnitude (sum of |terms|)
+ * of the sum that produced x; `site` identifies the rounding point. */
+static double round_act_ctx(const orc_model* m, double x, double A, int dec_layer, int site, round_ctx* rc) {
+  if (!rc || m->act_round == 0) return round_act(m, x, dec_layer);
+  double lo, hi, scale = 1.0, xs = x, nominal;
+  if (m->act_round == 1) {
+    uint16_t b = orc_f64_to_f16(x);
+    nominal = orc_f16_to_f64(b);
+    if (nominal == x) return nominal;
+    if (nominal > x) { hi = nominal; lo = orc_f16_to_f64(f16_step(b, 0)); }
+    else { lo = nominal; hi = orc_f16_to_f64(f16_step(b, 1)); }
+  } else {
+    float sc = (float)m->act_scale[dec_layer];
+    float inv = 1.0f / sc;
+    scale = sc;
+    xs = (double)((float)x * inv);
+    A = A * (double)inv;
+    uint8_t b = orc_f64_to_e4m3(xs);
+    nominal = orc_e4m3_to_f64(b);
+    if (nominal == xs || fabs(xs) >= 448.0) return nominal * scale;
+    if (nominal > xs) { hi = nominal; lo = orc_e4m3_to_f64(e4m3_step(b, 0)); }
+    else { lo = nominal; hi = orc_e4m3_to_f64(e4m3_step(b, 1)); }
+  }
+  double mid = 0.5 * (lo + hi);
+  double d = fabs(xs - mid) / (rc->gamma * A);
+  if (d <= 1.0) {
+    if (rc->record) {
+      if (rc->nsites < ORC_MAX_SITES) {
+        rc->site[rc->nsites] = site;
+        rc->dist[rc->nsites] = d;
+        rc->nsites++;
+      } else {
+        /* keep the closest ones */
+        int worst = 0;
+        for (int k = 1; k < ORC_MAX_SITES; ++k)
+          if (rc->dist[k] > rc->dist[worst]) worst = k;
+        if (d < rc->dist[worst]) { rc->site[worst] = site; rc->dist[worst] = d; }
+      }
+    }
+    for (int k = 0; k < rc->nflip; ++k)
+      if (rc->flip[k] == site) return (nominal == lo ? hi : lo) * scale;
+  }
+  return nominal * scale;
+}
+
+static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trace* tr, round_ctx* rc,
+                       double kappa) {
   double u = q->u[i], v = q->v[i], lod = q->lod[i];
   double xi = q->xi ? q->xi[i] : 0.0;
   tr->ntaps = latent_taps(m, u, v, lod, xi, tr->idx, tr->w);
@@ -376,10 +458,17 @@ static void forward(const orc_model* m, const orc_queries* q, int64_t i, trace* 
   }
   /* decoder input order: z0..z7, wi', wo' */
   double* x = tr->act[0];
-  for (int c = 0; c < ORC_C; ++c) x[c] = round_act(m, tr->z[c], 0);
+  for (int c = 0; c < ORC_C; ++c) {
+    double A = 0.0;
+    for (int k = 0; k < tr->ntaps; ++k) A += fabs(tr->w[k] * texel(m, tr->idx[k], c));
+    x[c] = round_act_ctx(m, tr->z[c], A, 0, c, rc);
+  }
+  /* directions: FP32 transform by an FP32 frame whose error grows with the
+   * frame's condition number */
+  const double Ad = 3.0 + 8.0 * kappa;
   for (int k = 0; k < 3; ++k) {
-    x[ORC_C + k] = round_act(m, wi_l[k], 0);
-    x[ORC_C + 3 + k] = round_act(m, wo_l[k], 0);
+    x[ORC_C + k] = round_act_ctx(m, wi_l[k], Ad, 0, ORC_C + k, rc);
+    x[ORC_C + 3 + k] = round_act_ctx(m, wo_l[k], Ad, 0, ORC_C + 3 + k, rc);
   }
 
   const double* p = m->dec_params;
@@ -390,11 +479,14 @@ static void forward(const orc_model* m, const orc_queries* q, int64_t i, trace* 
     p = b + out;
     int last = (l == m->n_layers - 1);
     for (int j = 0; j < out; ++j) {
-      double s = b[j];
-      for (int k = 0; k < in; ++k) s += W[j * in + k] * tr->act[l][k];
+      double s = b[j], A = fabs(b[j]);
+      for (int k = 0; k < in; ++k) {
+        s += W[j * in + k] * tr->act[l][k];
+        A += fabs(W[j * in + k] * tr->act[l][k]);
+      }
       tr->pre[l][j] = s;
       if (!last) {
-        tr->act[l + 1][j] = round_act(m, s > 0.0 ? s : 0.0, l + 1);
+        tr->act[l + 1][j] = round_act_ctx(m, s > 0.0 ? s : 0.0, A, l + 1, (l + 1) * 1024 + j, rc);
       }
     }
   }
@@ -402,6 +494,10 @@ static void forward(const orc_model* m, const orc_queries* q, int64_t i, trace* 
   tr->cosf = 1.0;
   if (m->out_cosine) tr->cosf = tr->wi[2] > 0.0 ? tr->wi[2] : 0.0;
   for (int c = 0; c < 3; ++c) tr->y[c] = tr->pre[lastl][c] * tr->cosf;
+}
+
+static void forward(const orc_model* m, const orc_queries* q, int64_t i, trace* tr) {
+  forward_rc(m, q, i, tr, NULL, 0.0);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -659,4 +755,139 @@ void orc_relu_pattern(const orc_model* m, const orc_queries* q, int64_t n, uint6
     out[i] = h;
   }
   free(tr);
+}
+
+/* Condition number of the frame step at each query: how much relative
+ * rounding in r = (n_raw, t_raw) is amplified in T.  Each raw vector's
+ * relative rounding is bounded by (sum of the magnitudes of the terms that
+ * form it) / (its norm); Gram-Schmidt multiplies the tangent's by
+ * 1 / sin(angle(n_raw, t_raw)).  kappa = max of the two ratios / sin.  1 when
+ * there is no frame MLP.  Used by the parity tests to separate
+ * ill-conditioned queries (where any finite-precision evaluation of the
+ * method departs from the exact result) from the rest. */
+static double frame_kappa(const orc_model* m, const trace* tr) {
+  if (m->frame_hidden <= 0) return 1.0;
+  int H = m->frame_hidden;
+  const double* Wf1 = m->frame_params;
+  const double* Wf2 = Wf1 + H * ORC_C + H;
+  const double* bf2 = Wf2 + 6 * H;
+  double a[6];
+  for (int j = 0; j < 6; ++j) {
+    double s = fabs(bf2[j]);
+    for (int k = 0; k < H; ++k) s += fabs(Wf2[j * H + k] * tr->hf[k]);
+    a[j] = s;
+  }
+  double An = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  double At = sqrt(a[3] * a[3] + a[4] * a[4] + a[5] * a[5]);
+  const double* nr = tr->r;
+  const double* trr = tr->r + 3;
+  double nl = sqrt(dot3(nr, nr)), tl = sqrt(dot3(trr, trr)), c[3];
+  cross3(nr, trr, c);
+  double sn = sqrt(dot3(c, c)) / (nl * tl);
+  double rn = An / nl, rt = At / tl;
+  double k = (rn > rt ? rn : rt) / sn;
+  return isfinite(k) ? k : 1e300;
+}
+
+void orc_frame_condition(const orc_model* m, const orc_queries* q, int64_t n, double* kappa_out) {
+  trace* tr = (trace*)malloc(sizeof(trace));
+  orc_model mm = *m;
+  mm.act_round = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (m->frame_hidden <= 0) { kappa_out[i] = 1.0; continue; }
+    forward(&mm, q, i, tr);
+    kappa_out[i] = frame_kappa(m, tr);
+  }
+  free(tr);
+}
+
+/* Every valid result of each query under the model's rounding emulation:
+ * the nominal result first, then the results with each subset of the three
+ * ambiguous rounding decisions closest to their midpoints taken the other
+ * way.  out is
+ * [n][ORC_MAX_ALT][3], unused slots NaN; nalt[i] results, nsites[i]
+ * ambiguous sites found.  gamma is the FP32 error band relative to each
+ * sum's magnitude. */
+#define ORC_MAX_ALT 8
+typedef struct {
+  const orc_model* m;
+  const orc_queries* q;
+  int64_t begin, end;
+  double gamma;
+  double* out;
+  int32_t* nalt;
+  int32_t* nsites;
+} alt_job;
+
+static void* alt_worker(void* arg) {
+  alt_job* j = (alt_job*)arg;
+  const orc_model* m = j->m;
+  trace* tr = (trace*)malloc(sizeof(trace));
+  orc_model plain = *m;
+  plain.act_round = 0;
+  for (int64_t i = j->begin; i < j->end; ++i) {
+    double* o = j->out + i * ORC_MAX_ALT * 3;
+    for (int k = 0; k < ORC_MAX_ALT * 3; ++k) o[k] = NAN;
+    double kappa = 1.0;
+    if (m->frame_hidden > 0) {
+      forward(&plain, j->q, i, tr);
+      kappa = frame_kappa(m, tr);
+    }
+    round_ctx rc;
+    memset(&rc, 0, sizeof rc);
+    rc.record = 1;
+    rc.gamma = j->gamma;
+    forward_rc(m, j->q, i, tr, &rc, kappa);
+    for (int c = 0; c < 3; ++c) o[c] = tr->y[c];
+    int ns = rc.nsites, na = 1;
+    j->nsites[i] = ns;
+    /* the three sites closest to their rounding midpoints, all subsets */
+    int sites[3], nk = 0;
+    for (int pick = 0; pick < 3 && pick < ns; ++pick) {
+      int best = -1;
+      for (int k = 0; k < ns; ++k) {
+        int used = 0;
+        for (int u2 = 0; u2 < nk; ++u2) used |= sites[u2] == rc.site[k];
+        if (!used && (best < 0 || rc.dist[k] < rc.dist[best])) best = k;
+      }
+      sites[nk++] = rc.site[best];
+    }
+    if (nk > 0) {
+      int nsub = (1 << nk) - 1;
+      for (int t = 0; t < nsub && na < ORC_MAX_ALT; ++t) {
+        round_ctx fc;
+        memset(&fc, 0, sizeof fc);
+        fc.gamma = j->gamma;
+        int mask = t + 1;
+        for (int k = 0; k < nk; ++k)
+          if (mask & (1 << k)) fc.flip[fc.nflip++] = sites[k];
+        forward_rc(m, j->q, i, tr, &fc, kappa);
+        for (int c = 0; c < 3; ++c) o[na * 3 + c] = tr->y[c];
+        ++na;
+      }
+    }
+    j->nalt[i] = na;
+  }
+  free(tr);
+  return NULL;
+}
+
+void orc_eval_alternatives(const orc_model* m, const orc_queries* q, int64_t n, double gamma, double* out,
+                           int32_t* nalt, int32_t* nsites, int nthreads) {
+  if (nthreads < 1) nthreads = 1;
+  if (nthreads > 256) nthreads = 256;
+  if (n < 4096) nthreads = 1;
+  pthread_t th[256];
+  alt_job jobs[256];
+  int64_t chunk = (n + nthreads - 1) / nthreads;
+  for (int t = 0; t < nthreads; ++t) {
+    jobs[t].m = m; jobs[t].q = q; jobs[t].gamma = gamma;
+    jobs[t].out = out; jobs[t].nalt = nalt; jobs[t].nsites = nsites;
+    jobs[t].begin = (int64_t)t * chunk;
+    if (jobs[t].begin > n) jobs[t].begin = n;
+    jobs[t].end = jobs[t].begin + chunk < n ? jobs[t].begin + chunk : n;
+  }
+  if (nthreads == 1) { alt_worker(&jobs[0]); return; }
+  for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, alt_worker, &jobs[t]);
+  for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
 }

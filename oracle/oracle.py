@@ -68,6 +68,8 @@ def lib():
         _lib.orc_loss.restype = d; _lib.orc_loss.argtypes = [p, p, i64, p]
         _lib.orc_grad.argtypes = [p, p, i64, p, p, p, p]
         _lib.orc_relu_pattern.argtypes = [p, p, i64, p]
+        _lib.orc_frame_condition.argtypes = [p, p, i64, p]
+        _lib.orc_eval_alternatives.argtypes = [p, p, i64, d, p, p, p, C.c_int]
     return _lib
 
 
@@ -271,6 +273,75 @@ def relu_pattern(model: Model, q) -> np.ndarray:
     qv = _QueryView(q, n)
     lib().orc_relu_pattern(C.byref(model._s), C.byref(qv.s), n, _ptr(out))
     return out
+
+
+def frame_condition(model: Model, q) -> np.ndarray:
+    """Per-query condition number of the frame step (1 without a frame MLP)."""
+    n = _nq(q)
+    out = np.ones(n, dtype=np.float64)
+    if n:
+        qv = _QueryView(q, n)
+        lib().orc_frame_condition(C.byref(model._s), C.byref(qv.s), n, _ptr(out))
+    return out
+
+
+MAX_ALT = 8
+
+
+def eval_alternatives(model: Model, q, gamma=2.0 ** -19, nthreads=None):
+    """Every valid result of each query under the model's rounding emulation
+    (see orc_eval_alternatives): alts [n, 8, 3] (NaN-padded, nominal first),
+    nalt [n], nsites [n]."""
+    n = _nq(q)
+    alts = np.full((n, MAX_ALT, 3), np.nan)
+    nalt = np.zeros(n, dtype=np.int32)
+    nsites = np.zeros(n, dtype=np.int32)
+    if n:
+        qv = _QueryView(q, n)
+        lib().orc_eval_alternatives(C.byref(model._s), C.byref(qv.s), n, gamma, _ptr(alts), _ptr(nalt),
+                                    _ptr(nsites), nthreads or os.cpu_count() or 1)
+    return alts, nalt, nsites
+
+
+def parity(g, o, kappa, tol, kappa_well=50.0, c=64.0, unit=2.0 ** -24):
+    """Element-wise parity with a conditioning-aware bound.
+
+    rel_i = max_c |g - o| / max(|o|, tau), tau = RMS of o.  Queries whose
+    frame condition number is at most kappa_well must meet `tol`; beyond it
+    the bound is max(tol, c * kappa * unit), the growth of a
+    finite-precision evaluation's rounding (unit roundoff `unit` of the
+    frame arithmetic) through an ill-conditioned frame.  Returns
+    (ok, stats)."""
+    g = np.asarray(g, dtype=np.float64).reshape(-1, 3)
+    alts = None
+    if np.ndim(o) == 3:   # [n, k, 3] valid alternatives, nominal first
+        alts = np.asarray(o, dtype=np.float64)
+        o = alts[:, 0, :]
+    o = np.asarray(o, dtype=np.float64).reshape(-1, 3)
+    kappa = np.asarray(kappa, dtype=np.float64)
+    if o.size == 0:
+        return True, {"max_rel": 0.0, "mean_rel": 0.0, "ill_conditioned": 0, "n": 0}
+    tau = max(float(np.sqrt(np.mean(o * o))), 1e-30)
+    den = np.maximum(np.abs(o), tau)
+    if alts is None:
+        rel = (np.abs(g - o) / den).max(axis=1)
+    else:
+        r = (np.abs(g[:, None, :] - alts) / den[:, None, :]).max(axis=2)
+        rel = np.nanmin(r, axis=1)
+    well = kappa <= kappa_well
+    bound = np.where(well, tol, np.maximum(tol, c * kappa * unit))
+    ok = bool(np.all(rel <= bound)) and bool(np.all(np.isfinite(g)))
+    bins = {}
+    for lo, hi in ((0, 10), (10, 50), (50, 300), (300, 3000), (3000, np.inf)):
+        sel = (kappa > lo) & (kappa <= hi)
+        if sel.any():
+            bins[f"({lo},{hi}]"] = {"n": int(sel.sum()), "max_rel": float(rel[sel].max()),
+                                   "max_rel_over_kappa_u": float((rel[sel] / (kappa[sel] * unit)).max())}
+    st = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
+          "max_rel_well_conditioned": float(rel[well].max()) if well.any() else 0.0,
+          "ill_conditioned": int((~well).sum()), "n": int(len(rel)),
+          "worst_over_bound": float((rel / bound).max()), "by_kappa": bins}
+    return ok, st
 
 
 def loss(g, y):

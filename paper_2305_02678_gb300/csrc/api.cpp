@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -91,6 +92,30 @@ bool nam::budget_reserve(nam_ctx* ctx, uint64_t bytes) {
   }
 }
 void nam::budget_release(nam_ctx* ctx, uint64_t bytes) { ctx->resident.fetch_sub(bytes); }
+
+int nam::blocks_per_sm(const void* func, int threads, int dyn_smem, int cap, bool resources_only) {
+  int o = 0;
+  cudaError_t e = cudaSuccess;
+  if (!resources_only) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, func, threads, dyn_smem);
+  cudaFuncAttributes a{};
+  cudaError_t ea = cudaFuncGetAttributes(&a, func);
+  if (resources_only || e != cudaSuccess || o < 1) {
+    cudaGetLastError();
+    int regs = ea == cudaSuccess ? a.numRegs : 64;
+    int smem = dyn_smem + (ea == cudaSuccess ? (int)a.sharedSizeBytes : 0) + 1024;
+    int by_smem = (227 * 1024) / (smem > 0 ? smem : 1);
+    int by_regs = 65536 / (((regs + 7) / 8 * 8) * threads);
+    int by_thr = 2048 / threads;
+    o = std::min(std::min(by_smem, by_regs), std::min(by_thr, 32));
+  }
+  if (o > cap) o = cap;
+  if (o < 1) o = 1;
+  if (getenv("NAM_VERBOSE"))
+    fprintf(stderr, "[nam] occupancy: api=%d (%s) regs=%d static_smem=%zu dyn_smem=%d -> %d blocks/SM\n", o,
+            cudaGetErrorString(e), ea == cudaSuccess ? a.numRegs : -1, ea == cudaSuccess ? a.sharedSizeBytes : 0,
+            dyn_smem, o);
+  return o;
+}
 
 // ---------------------------------------------------------------------------
 // context
@@ -268,10 +293,11 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
     }
   }
   uint64_t resident = pyr_bytes + blob_bytes + (uint64_t)np * 4;
+  m->pyr_off = (np + 3) / 4 * 4;
   if (d->trainable) {
-    // FP32 pyramid masters are the pyramid itself; Adam moments + grads for
-    // params and pyramid, plus per-step scratch (grad_rgb, loss)
-    resident += 3ull * np * 4 + 3ull * pyr_bytes;
+    // FP32 pyramid masters are the pyramid itself; Adam moments and gradients
+    // for params and pyramid
+    resident += 3ull * (m->pyr_off + pd.texels * 8) * 4;
   }
   if (!budget_reserve(ctx, resident)) {
     delete m;
@@ -283,9 +309,10 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   if (!e) e = dev_alloc(ctx, (void**)&m->params, np * 4);
   if (!e && blob_bytes) e = dev_alloc(ctx, &m->blob, blob_bytes);
   if (!e && d->trainable) {
-    e = dev_alloc(ctx, (void**)&m->adam_m, (np + pd.texels * 8) * 4);
-    if (!e) e = dev_alloc(ctx, (void**)&m->adam_v, (np + pd.texels * 8) * 4);
-    if (!e) e = dev_alloc(ctx, (void**)&m->grad, (np + pd.texels * 8) * 4);
+    const size_t nb = (m->pyr_off + pd.texels * 8) * 4;
+    e = dev_alloc(ctx, (void**)&m->adam_m, nb);
+    if (!e) e = dev_alloc(ctx, (void**)&m->adam_v, nb);
+    if (!e) e = dev_alloc(ctx, (void**)&m->grad, nb);
   }
   if (e) {
     free_material(ctx, m);
@@ -304,7 +331,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
     e = (int)cudaMemcpy(m->blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice);
   }
   if (!e && d->trainable) {
-    size_t nb = (np + pd.texels * 8) * 4;
+    size_t nb = (m->pyr_off + pd.texels * 8) * 4;
     cudaMemset(m->adam_m, 0, nb);
     cudaMemset(m->adam_v, 0, nb);
     e = (int)cudaMemset(m->grad, 0, nb);

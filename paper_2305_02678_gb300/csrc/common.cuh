@@ -28,32 +28,39 @@ __device__ __forceinline__ LevelPick pick_levels(const PyrDesc& P, float lod) {
 
 // Integer texel coordinate of the lower bilinear tap and its fraction, plus
 // the upper tap, under the material's addressing.  Texel centres sit at
-// (i + 1/2) / W, so the continuous coordinate is x = u W - 1/2.  For wrap the
-// integer part of u is removed first (exact in FP32), which for power-of-two
-// W gives the same x as u W - 1/2 modulo W, bit for bit.
+// (i + 1/2) / W, so the continuous coordinate is x = u W - 1/2.  X = u W is
+// exact for power-of-two W; the 1/2 is then applied to X's fractional part
+// (which cannot lose bits, unlike X - 1/2 itself when |X - 1/2| crosses a
+// power of two), so tap index and fraction are exact while |X| < 2^23.
+// Larger |X| (no fraction left in FP32) is reduced with the exact fmodf for
+// wrap; non-finite coordinates read texel 0.
 __device__ __forceinline__ void tap_axis(const PyrDesc& P, float u, int W, int& i0, int& i1, float& f) {
-  if (P.address == NAM_ADDRESS_CLAMP) {
-    float x = fmaf(u, (float)W, -0.5f);
-    float x0 = floorf(x);
-    f = x - x0;
-    // clamp in float first so that huge |u| cannot overflow the int conversion
-    float c0 = fminf(fmaxf(x0, 0.0f), (float)(W - 1));
-    float c1 = fminf(fmaxf(x0 + 1.0f, 0.0f), (float)(W - 1));
-    i0 = (int)c0;
-    i1 = (int)c1;
+  float X = u * (float)W;
+  if (!(fabsf(X) < 8388608.0f)) X = isfinite(X) ? (P.address == NAM_ADDRESS_CLAMP ? X : fmodf(X, (float)W)) : 0.0f;
+  const float Xf = floorf(X);
+  const float r = X - Xf;  // [0, 1]
+  float x0;
+  if (r >= 0.5f) {
+    x0 = Xf;
+    f = r - 0.5f;
   } else {
-    float uf = u - floorf(u);  // [0, 1]
-    float x = fmaf(uf, (float)W, -0.5f);
-    float x0 = floorf(x);
-    f = x - x0;
-    int k = (int)x0;  // in [-1, W]
+    x0 = Xf - 1.0f;
+    f = r + 0.5f;
+  }
+  if (P.address == NAM_ADDRESS_CLAMP) {
+    // clamp in float first so that huge |u| cannot overflow the int conversion
+    i0 = (int)fminf(fmaxf(x0, 0.0f), (float)(W - 1));
+    i1 = (int)fminf(fmaxf(x0 + 1.0f, 0.0f), (float)(W - 1));
+  } else {
+    int k = (int)x0;  // |k| <= 2^23
     if (P.pow2) {
       i0 = k & (W - 1);
       i1 = (k + 1) & (W - 1);
     } else {
-      i0 = k < 0 ? k + W : (k >= W ? k - W : k);
-      int k1 = k + 1;
-      i1 = k1 >= W ? k1 - W : k1;
+      k %= W;
+      if (k < 0) k += W;
+      i0 = k;
+      i1 = k + 1 == W ? 0 : k + 1;
     }
   }
 }

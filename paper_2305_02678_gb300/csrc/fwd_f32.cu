@@ -160,9 +160,7 @@ static int launch_one(const LaunchCommon& L, cudaStream_t s) {
   static int occ = -1;  // per instantiation
   if (occ < 0) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 128, smem);
-    occ = o > 0 ? o : 1;
+    occ = blocks_per_sm((const void*)k, 128, smem, 16);
   }
   int64_t blocks = (L.n + 127) / 128;
   int64_t cap = (int64_t)occ * L.num_sms;

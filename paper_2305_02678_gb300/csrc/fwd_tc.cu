@@ -423,11 +423,8 @@ static int launch_tc_one(const LaunchCommon& L, cudaStream_t s) {
   static int occ = -1;
   if (occ < 0) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM);
-    int o = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k, 128, Lay::SMEM);
-    // TMEM: 512 columns per SM, 64 per CTA
-    if (o > 8) o = 8;
-    occ = o > 0 ? o : 1;
+    // TMEM: 512 columns per SM, 64 per CTA -> at most 8 resident CTAs
+    occ = blocks_per_sm((const void*)k, 128, Lay::SMEM, 8, true);
   }
   const int64_t nchunks = L.chunks ? (int64_t)L.n_chunks : (L.n + 127) / 128;
   if (nchunks == 0) return 0;

@@ -20,7 +20,10 @@ struct nam_material_s {
   void* pyramid = nullptr;    // device pyramid (FP16 or FP32 texels)
   void* blob = nullptr;       // tensor-core weight blob (F16 / FP8)
   float* params = nullptr;    // FP32 masters (frame then decoder)
-  float* adam_m = nullptr;    // trainable: [n_params + texels*8]
+  int64_t pyr_off = 0;        // trainable: offset of the pyramid block in
+                              // adam_m / adam_v / grad (n_params rounded up
+                              // to 16 bytes, for the 16-byte vector atomics)
+  float* adam_m = nullptr;    // trainable: [pyr_off + texels*8]
   float* adam_v = nullptr;
   float* grad = nullptr;      // trainable: gradient buffer, same layout
   void* train_scratch = nullptr;  // trainable: rgb, grad_rgb, loss for a batch

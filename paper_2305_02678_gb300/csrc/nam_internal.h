@@ -72,6 +72,12 @@ struct LaunchCommon {
   int num_sms;
 };
 
+// Resident blocks per SM of a kernel: the occupancy API, or (resources_only,
+// and as a fallback) the limit computed from the kernel's registers, shared
+// memory and threads.  The API answers 1 for kernels that use TMEM, whose
+// true limit (columns allocated per CTA) the caller passes as `cap`.
+int blocks_per_sm(const void* func, int threads, int dyn_smem, int cap, bool resources_only = false);
+
 int launch_eval_f32(const LaunchCommon& L, void* stream);
 int launch_eval_tc(const LaunchCommon& L, int precision, void* stream);
 

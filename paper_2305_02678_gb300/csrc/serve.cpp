@@ -112,7 +112,8 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
     if (e != cudaSuccess) return cuda_fail((int)e, "serving: H2D");
   }
   float* rgb = (float*)(base + (size_t)j->nf * n * 4);
-  uint8_t* tab = (uint8_t*)(rgb + 3 * n);
+  // chunk table (int64 fields) at the next 16-byte boundary after the RGB
+  uint8_t* tab = base + (((size_t)j->nf * n * 4 + (size_t)n * 12 + 15) / 16 * 16);
   const size_t cb = j->chunks.size() * sizeof(Chunk);
   const size_t pb = j->mats.size() * sizeof(void*);
   std::vector<uint8_t> host(cb + 2 * pb);
@@ -272,7 +273,7 @@ extern "C" nam_status nam_submit(nam_ctx* ctx, const nam_frame* f, nam_ticket* o
   build_chunks(f->items, f->n_items, &j->chunks);
   j->nf = f->materials[0]->desc.filter == NAM_FILTER_STOCHASTIC ? 10 : 9;
   const int64_t n = f->n_queries;
-  j->bytes = (uint64_t)n * 4 * j->nf + (uint64_t)n * 12 + j->chunks.size() * sizeof(Chunk) +
+  j->bytes = ((uint64_t)n * 4 * j->nf + (uint64_t)n * 12 + 15) / 16 * 16 + j->chunks.size() * sizeof(Chunk) +
              2 * j->mats.size() * sizeof(void*) + 256;
   j->st.arrival_s = f->arrival_s > 0 ? f->arrival_s : nam_now();
   j->st.n_queries = n;

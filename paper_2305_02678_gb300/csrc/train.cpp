@@ -1,6 +1,7 @@
 // C ABI: reverse mode and the training step (Sec. 5.2).
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <cstring>
 
 #include "nam_ctx.h"
@@ -42,6 +43,8 @@ extern "C" nam_status nam_backward(nam_ctx* ctx, nam_material m, const nam_queri
   if (n < 0) return fail(NAM_ERR_INVALID_ARG, "n < 0");
   if (n == 0) return NAM_OK;
   if (!grad_rgb || !grad_params) return fail(NAM_ERR_INVALID_ARG, "NULL gradient buffer");
+  if (((uintptr_t)grad_pyramid & 15u) != 0)
+    return fail(NAM_ERR_INVALID_ARG, "grad_pyramid must be 16-byte aligned (it takes 16-byte vector atomics)");
   st = check_queries(m, q);
   if (st) return st;
   DeviceGuard g(ctx->device);
@@ -92,14 +95,14 @@ extern "C" nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_que
   int e = launch_eval_f32(L, s);
   if (!e) e = launch_loss(rgb, target_rgb, n, grad_rgb, loss_acc, s);
   BackwardArgs a;
-  fill_bwd(ctx, m, q, n, grad_rgb, m->grad, m->grad + m->n_params, flags, &a);
+  const int64_t np = m->n_params, po = m->pyr_off, nt = m->pyr.texels * 8;
+  fill_bwd(ctx, m, q, n, grad_rgb, m->grad, m->grad + po, flags, &a);
   if (!e) e = launch_backward(a, s);
-  const int64_t np = m->n_params, nt = m->pyr.texels * 8;
   if (!e)
     e = launch_adam(m->params, m->grad, m->adam_m, m->adam_v, np, opt->lr_params, opt->beta1, opt->beta2, opt->eps,
                     opt->step, s);
   if (!e)
-    e = launch_adam((float*)m->pyramid, m->grad + np, m->adam_m + np, m->adam_v + np, nt, opt->lr_pyramid,
+    e = launch_adam((float*)m->pyramid, m->grad + po, m->adam_m + po, m->adam_v + po, nt, opt->lr_pyramid,
                     opt->beta1, opt->beta2, opt->eps, opt->step, s);
   if (e) return cuda_fail(e, "nam_train_step: launch");
   if (loss_out) {
