@@ -74,9 +74,10 @@ __device__ __forceinline__ void bilinear_acc(const PyrDesc& P, const void* pyr, 
   float fx, fy;
   tap_axis(P, u, W, x0, x1, fx);
   tap_axis(P, v, H, y0, y1, fy);
-  const int64_t base = P.off[l];
-  const int64_t r0 = base + (int64_t)y0 * W, r1 = base + (int64_t)y1 * W;
-  const int64_t idx[4] = {r0 + x0, r0 + x1, r1 + x0, r1 + x1};
+  // texel indices fit 32 bits (pyramids up to 2^32 texels, 64 GiB at FP16)
+  const uint32_t base = (uint32_t)P.off[l];
+  const uint32_t r0 = base + (uint32_t)y0 * (uint32_t)W, r1 = base + (uint32_t)y1 * (uint32_t)W;
+  const uint32_t idx[4] = {r0 + x0, r0 + x1, r1 + x0, r1 + x1};
   const float gx = 1.0f - fx, gy = 1.0f - fy;
   const float w4[4] = {gx * gy * wgt, fx * gy * wgt, gx * fy * wgt, fx * fy * wgt};
   if (F16) {
@@ -99,8 +100,8 @@ __device__ __forceinline__ void bilinear_acc(const PyrDesc& P, const void* pyr, 
     float4 a[4], b[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      a[k] = __ldg(p + 2 * idx[k]);
-      b[k] = __ldg(p + 2 * idx[k] + 1);
+      a[k] = __ldg(p + 2 * (size_t)idx[k]);
+      b[k] = __ldg(p + 2 * (size_t)idx[k] + 1);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -144,32 +145,32 @@ struct Frame {
 
 __device__ __forceinline__ Frame build_frame(const float r[6]) {
   Frame F;
-  float nl = sqrtf(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-  if (!(nl >= 1e-20f)) {
+  const float nl2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  if (!(nl2 >= 1e-40f)) {
     F.n[0] = 0.0f; F.n[1] = 0.0f; F.n[2] = 1.0f;
   } else {
-    float inv = 1.0f / nl;
+    const float inv = rsqrtf(nl2);
     F.n[0] = r[0] * inv; F.n[1] = r[1] * inv; F.n[2] = r[2] * inv;
   }
-  float s = r[3] * F.n[0] + r[4] * F.n[1] + r[5] * F.n[2];
-  float tp0 = r[3] - s * F.n[0], tp1 = r[4] - s * F.n[1], tp2 = r[5] - s * F.n[2];
-  float tpl = sqrtf(tp0 * tp0 + tp1 * tp1 + tp2 * tp2);
-  float trl = sqrtf(r[3] * r[3] + r[4] * r[4] + r[5] * r[5]);
-  if (!(tpl > 1e-6f * trl)) {
-    float sg = copysignf(1.0f, F.n[2]);
-    float a = -1.0f / (sg + F.n[2]);
-    float bb = F.n[0] * F.n[1] * a;
+  const float s = r[3] * F.n[0] + r[4] * F.n[1] + r[5] * F.n[2];
+  const float tp0 = r[3] - s * F.n[0], tp1 = r[4] - s * F.n[1], tp2 = r[5] - s * F.n[2];
+  const float tpl2 = tp0 * tp0 + tp1 * tp1 + tp2 * tp2;
+  const float trl2 = r[3] * r[3] + r[4] * r[4] + r[5] * r[5];
+  if (!(tpl2 > 1e-12f * trl2)) {
+    const float sg = copysignf(1.0f, F.n[2]);
+    const float a = -1.0f / (sg + F.n[2]);
+    const float bb = F.n[0] * F.n[1] * a;
     F.t[0] = 1.0f + sg * F.n[0] * F.n[0] * a;
     F.t[1] = sg * bb;
     F.t[2] = -sg * F.n[0];
   } else {
-    float inv = 1.0f / tpl;
+    const float inv = rsqrtf(tpl2);
     F.t[0] = tp0 * inv; F.t[1] = tp1 * inv; F.t[2] = tp2 * inv;
   }
-  float c0 = F.n[1] * F.t[2] - F.n[2] * F.t[1];
-  float c1 = F.n[2] * F.t[0] - F.n[0] * F.t[2];
-  float c2 = F.n[0] * F.t[1] - F.n[1] * F.t[0];
-  float inv = 1.0f / sqrtf(c0 * c0 + c1 * c1 + c2 * c2);
+  const float c0 = F.n[1] * F.t[2] - F.n[2] * F.t[1];
+  const float c1 = F.n[2] * F.t[0] - F.n[0] * F.t[2];
+  const float c2 = F.n[0] * F.t[1] - F.n[1] * F.t[0];
+  const float inv = rsqrtf(c0 * c0 + c1 * c1 + c2 * c2);
   F.b[0] = c0 * inv; F.b[1] = c1 * inv; F.b[2] = c2 * inv;
   return F;
 }

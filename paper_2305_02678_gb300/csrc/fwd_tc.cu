@@ -44,15 +44,14 @@ struct TcLayout {
   // block whose first column is 1.0 (bias input) and an all-zero block.
   static constexpr int KB = (H / 8) > 4 ? (H / 8) : 4;
   static constexpr int A_BYTES = (KB + 2) * 2048;
-  // weight blob
-  static constexpr int B_F1 = 0;                          // 16 x 16
-  static constexpr int B_F2 = FRAME ? 512 : 0;            // 16 x 32
-  static constexpr int B_L1 = FRAME ? 1536 : 0;           // H x 16
+  // weight blob: every bias rides in the MMA as the weight of the constant-1
+  // input column (one extra K step of 16)
+  static constexpr int B_F1 = 0;                          // 16 x 32: [Wf1 | Wf1 | bf1 0..]
+  static constexpr int B_F2 = FRAME ? 1024 : 0;           // 16 x 48: [Wf2 | Wf2 | bf2 0..]
+  static constexpr int B_L1 = FRAME ? 2560 : 0;           // H x 16: [W1 | b1 0]
   static constexpr int B_L2 = B_L1 + H * 16 * 2;          // H x (H + 16)
   static constexpr int B_LO = B_L2 + H * (H + 16) * 2;    // 16 x (H + 16)
-  static constexpr int BIAS_F1 = B_LO + 16 * (H + 16) * 2;
-  static constexpr int BIAS_F2 = BIAS_F1 + (FRAME ? 64 : 0);
-  static constexpr int BLOB = BIAS_F2 + (FRAME ? 32 : 0);
+  static constexpr int BLOB = B_LO + 16 * (H + 16) * 2;
   static constexpr int BLOB_ALIGNED = (BLOB + 127) / 128 * 128;
   static constexpr int SMEM = BLOB_ALIGNED + A_BYTES + 64;
 };
@@ -77,8 +76,10 @@ static void put_h(uint8_t* base, int R, int row, int k, float v) {
 }
 
 // Lay out the FP16-quantised weights as MMA B operands (N rows = outputs,
-// K = inputs, K-major), biases of the decoder in the extra input column K = in
-// (matching the constant-1 column of the A operand), frame biases as FP32.
+// K = inputs, K-major), each layer's bias in the extra input column that
+// meets the constant-1 column of the A operand.  The frame layers take their
+// FP16 operand in two halves (high part, residual), so their weights appear
+// twice along K.
 int pack_tc_blob(const Shape& s, int precision, const float* frame, const float* dec, const float* /*act_scale*/,
                  uint8_t* out, float* /*weight_scales_out*/) {
   if (precision != NAM_PREC_F16) return -1;
@@ -86,28 +87,22 @@ int pack_tc_blob(const Shape& s, int precision, const float* frame, const float*
   if (!bytes) return -1;
   std::memset(out, 0, bytes);
   const int H = s.H;
-  int B_L1 = s.frame ? 1536 : 0;
-  int B_L2 = B_L1 + H * 16 * 2;
-  int B_LO = B_L2 + H * (H + 16) * 2;
-  int BIAS_F1 = B_LO + 16 * (H + 16) * 2;
-  int BIAS_F2 = BIAS_F1 + 64;
+  const int B_L1 = s.frame ? 2560 : 0;
+  const int B_L2 = B_L1 + H * 16 * 2;
+  const int B_LO = B_L2 + H * (H + 16) * 2;
   if (s.frame) {
     const float* Wf1 = frame;            // [16][8]
     const float* bf1 = Wf1 + 128;        // [16]
     const float* Wf2 = bf1 + 16;         // [6][16]
     const float* bf2 = Wf2 + 96;         // [6]
-    // F1: 16 x 16, both K halves carry Wf1 (operand = z_hi | z_lo)
-    for (int n = 0; n < 16; ++n)
+    for (int n = 0; n < 16; ++n) {
       for (int k = 0; k < 16; ++k) put_h(out + 0, 16, n, k, Wf1[n * 8 + (k & 7)]);
-    // F2: 16 x 32, rows 0..5 = Wf2 in both halves (operand = h_hi | h_lo)
-    for (int n = 0; n < 6; ++n)
-      for (int k = 0; k < 32; ++k) put_h(out + 512, 16, n, k, Wf2[n * 16 + (k & 15)]);
-    // frame biases: FP16-quantised values, added in FP32
-    float b1q[16], b2q[8] = {0};
-    for (int j = 0; j < 16; ++j) b1q[j] = __half2float(__float2half_rn(bf1[j]));
-    for (int j = 0; j < 6; ++j) b2q[j] = __half2float(__float2half_rn(bf2[j]));
-    std::memcpy(out + BIAS_F1, b1q, 64);
-    std::memcpy(out + BIAS_F2, b2q, 32);
+      put_h(out + 0, 16, n, 16, bf1[n]);
+    }
+    for (int n = 0; n < 6; ++n) {
+      for (int k = 0; k < 32; ++k) put_h(out + 1024, 16, n, k, Wf2[n * 16 + (k & 15)]);
+      put_h(out + 1024, 16, n, 32, bf2[n]);
+    }
   }
   const float* W1 = dec;                 // [H][14]
   const float* b1 = W1 + 14 * H;
@@ -143,6 +138,45 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
   lo = ptx::pack_h2(a - f.x, b - f.y);
 }
 
+// One query's inputs, loaded a tile ahead of its use.
+struct QueryIn {
+  float u, v, lod, xi, wix, wiy, wiz, wox, woy, woz;
+};
+struct ChunkIn {
+  int64_t start;
+  int count, mat;
+};
+
+__device__ __forceinline__ ChunkIn chunk_at(const LaunchCommon& L, int64_t c) {
+  ChunkIn ci;
+  if (L.chunks) {
+    const Chunk ch = L.chunks[c];
+    ci.start = ch.start;
+    ci.count = ch.count;
+    ci.mat = ch.material;
+  } else {
+    ci.start = c * 128;
+    ci.count = (int)((L.n - ci.start) < 128 ? (L.n - ci.start) : 128);
+    ci.mat = 0;
+  }
+  return ci;
+}
+
+__device__ __forceinline__ QueryIn load_query(const QueryPtrs& q, int64_t i) {
+  QueryIn x;
+  x.u = __ldg(q.u + i);
+  x.v = __ldg(q.v + i);
+  x.lod = __ldg(q.lod + i);
+  x.xi = q.xi ? __ldg(q.xi + i) : 0.0f;
+  x.wix = __ldg(q.wix + i);
+  x.wiy = __ldg(q.wiy + i);
+  x.wiz = __ldg(q.wiz + i);
+  x.wox = __ldg(q.wox + i);
+  x.woy = __ldg(q.woy + i);
+  x.woz = __ldg(q.woz + i);
+  return x;
+}
+
 template <int H, bool FRAME, bool F16P>
 __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
   using Lay = TcLayout<H, FRAME>;
@@ -157,6 +191,7 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
   const uint32_t bar_m = ptx::smem_u32(&bars[1]);
   const uint32_t aW = ptx::smem_u32(sW);
   const uint32_t aA = ptx::smem_u32(sA);
+  const uint32_t aConst = aA + Lay::KB * 2048;  // (1, 0, ...) | 0 blocks
 
   if (tid == 0) {
     ptx::mbar_init(bar_w, 1);
@@ -167,9 +202,8 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
     ptx::tmem_alloc(ptx::smem_u32(tslot), 64);
     ptx::tmem_relinquish();
   }
-  // constant A blocks: 1.0 in the first column of block KB, zeros in KB+1
-  ptx::st_shared_v4(aA + Lay::KB * 2048 + tid * 16, 0x3C00u, 0u, 0u, 0u);
-  ptx::st_shared_v4(aA + (Lay::KB + 1) * 2048 + tid * 16, 0u, 0u, 0u, 0u);
+  ptx::st_shared_v4(aConst + tid * 16, 0x3C00u, 0u, 0u, 0u);
+  ptx::st_shared_v4(aConst + 2048 + tid * 16, 0u, 0u, 0u, 0u);
   ptx::fence_proxy_async();
   ptx::tc_fence_before();
   __syncthreads();
@@ -187,30 +221,50 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
   int cur_mat = -1;
   const void* pyr = L.pyr0;
   const bool cosine = (L.flags & NAM_OUT_COSINE) != 0;
-  const QueryPtrs& q = L.q;
+  const int r = tid;
 
   constexpr uint32_t ID_16 = ptx::idesc_f16(128, 16);
   constexpr uint32_t ID_H = ptx::idesc_f16(128, H);
 
-  for (int64_t c = c_begin; c < c_end; ++c) {
-    int64_t start;
-    int count, mat;
-    if (L.chunks) {
-      const Chunk ch = L.chunks[c];
-      start = ch.start;
-      count = ch.count;
-      mat = ch.material;
-    } else {
-      start = c * 128;
-      count = (int)((L.n - start) < 128 ? (L.n - start) : 128);
-      mat = 0;
+  // make this thread's A-operand writes visible to the tensor core, sync the
+  // CTA, let one thread issue `issue`, wait for completion.  Returns false
+  // (for every thread) if any thread's wait ran out.
+  auto mma_stage = [&](auto issue) -> bool {
+    ptx::fence_proxy_async();
+    ptx::tc_fence_before();
+    if (__syncthreads_or(bad)) return false;
+    if (tid == 0) {
+      ptx::tc_fence_after();
+      issue();
+      ptx::mma_commit(bar_m);
     }
-    if (mat != cur_mat) {
-      // (re)stage the material's weights; every reader of sW is past the
-      // previous barrier and no MMA is in flight
+    mma_pending = true;
+    bad |= !ptx::mbar_wait(bar_m, ph_m, L.timeout_ns);
+    ph_m ^= 1;
+    if (!bad) mma_pending = false;
+    ptx::tc_fence_after();
+    return true;
+  };
+
+  ChunkIn ci{};
+  QueryIn qc{};
+  if (c_begin < c_end) {
+    ci = chunk_at(L, c_begin);
+    qc = load_query(L.q, ci.start + (r < ci.count ? r : 0));
+  }
+  for (int64_t c = c_begin; c < c_end; ++c) {
+    // prefetch the next tile's inputs; consumed one iteration later
+    ChunkIn cn = ci;
+    QueryIn qn = qc;
+    if (c + 1 < c_end) {
+      cn = chunk_at(L, c + 1);
+      qn = load_query(L.q, cn.start + (r < cn.count ? r : 0));
+    }
+    if (ci.mat != cur_mat) {
+      // (re)stage the material's weights; no MMA is in flight here
       if (__syncthreads_or(bad)) break;
-      const void* wsrc = L.chunks ? L.mats.weights[mat] : L.w0;
-      pyr = L.chunks ? L.mats.pyramid[mat] : L.pyr0;
+      const void* wsrc = L.chunks ? L.mats.weights[ci.mat] : L.w0;
+      pyr = L.chunks ? L.mats.pyramid[ci.mat] : L.pyr0;
       if (tid == 0) {
         ptx::fence_proxy_async();
         ptx::mbar_arrive_expect_tx(bar_w, Lay::BLOB);
@@ -220,18 +274,14 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
       bad |= !ptx::mbar_wait(bar_w, ph_w, L.timeout_ns);
       ph_w ^= 1;
       if (!bad) w_pending = false;
-      cur_mat = mat;
+      cur_mat = ci.mat;
     }
-    const int r = tid;
-    const bool valid = r < count;
-    const int64_t i = start + (valid ? r : 0);
+    const bool valid = r < ci.count;
+    const int64_t i = ci.start + (valid ? r : 0);
 
     // ---- 1. latent fetch ------------------------------------------------
     float z[8];
-    const float xi = q.xi ? q.xi[i] : 0.0f;
-    fetch_latent<F16P>(L.pyr, pyr, q.u[i], q.v[i], q.lod[i], xi, z);
-    const float wix = q.wix[i], wiy = q.wiy[i], wiz = q.wiz[i];
-    const float wox = q.wox[i], woy = q.woy[i], woz = q.woz[i];
+    fetch_latent<F16P>(L.pyr, pyr, qc.u, qc.v, qc.lod, qc.xi, z);
     const uint32_t z01 = ptx::pack_h2(z[0], z[1]), z23 = ptx::pack_h2(z[2], z[3]);
     const uint32_t z45 = ptx::pack_h2(z[4], z[5]), z67 = ptx::pack_h2(z[6], z[7]);
 
@@ -247,67 +297,46 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
         ptx::st_shared_v4(aA + 0 * 2048 + r * 16, h0, h1, h2, h3);
         ptx::st_shared_v4(aA + 1 * 2048 + r * 16, lo0, lo1, lo2, lo3);
       }
-      ptx::fence_proxy_async();
-      ptx::tc_fence_before();
-      if (__syncthreads_or(bad)) break;
-      if (tid == 0) {
-        ptx::tc_fence_after();
-        ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_F1, 16 * 16, 128), ID_16, 0);
-        ptx::mma_commit(bar_m);
-      }
-      mma_pending = true;
-      bad |= !ptx::mbar_wait(bar_m, ph_m, L.timeout_ns);
-      ph_m ^= 1;
-      if (!bad) mma_pending = false;
-      ptx::tc_fence_after();
+      if (!mma_stage([&] {
+            ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_F1, 256, 128), ID_16, 0);
+            ptx::mma_f16(tmem, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + Lay::B_F1 + 512, 256, 128), ID_16, 1);
+          }))
+        break;
       {
         uint32_t acc[16];
         ptx::tmem_ld16(tlane, acc);
         ptx::tmem_ld_wait();
-        const float* bf1 = reinterpret_cast<const float*>(sW + Lay::BIAS_F1);
         uint32_t hi[8], lo[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float a = fmaxf(u2f(acc[2 * j]) + bf1[2 * j], 0.0f);
-          float b = fmaxf(u2f(acc[2 * j + 1]) + bf1[2 * j + 1], 0.0f);
-          split2(a, b, hi[j], lo[j]);
-        }
+        for (int j = 0; j < 8; ++j)
+          split2(fmaxf(u2f(acc[2 * j]), 0.0f), fmaxf(u2f(acc[2 * j + 1]), 0.0f), hi[j], lo[j]);
         ptx::st_shared_v4(aA + 0 * 2048 + r * 16, hi[0], hi[1], hi[2], hi[3]);
         ptx::st_shared_v4(aA + 1 * 2048 + r * 16, hi[4], hi[5], hi[6], hi[7]);
         ptx::st_shared_v4(aA + 2 * 2048 + r * 16, lo[0], lo[1], lo[2], lo[3]);
         ptx::st_shared_v4(aA + 3 * 2048 + r * 16, lo[4], lo[5], lo[6], lo[7]);
       }
-      ptx::fence_proxy_async();
-      ptx::tc_fence_before();
-      if (__syncthreads_or(bad)) break;
-      if (tid == 0) {
-        ptx::tc_fence_after();
-        ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_F2, 16 * 16, 128), ID_16, 0);
-        ptx::mma_f16(tmem, ptx::sdesc(aA + 2 * 2048, 2048, 128),
-                     ptx::sdesc(aW + Lay::B_F2 + 2 * 256, 16 * 16, 128), ID_16, 1);
-        ptx::mma_commit(bar_m);
-      }
-      mma_pending = true;
-      bad |= !ptx::mbar_wait(bar_m, ph_m, L.timeout_ns);
-      ph_m ^= 1;
-      if (!bad) mma_pending = false;
-      ptx::tc_fence_after();
+      if (!mma_stage([&] {
+            ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_F2, 256, 128), ID_16, 0);
+            ptx::mma_f16(tmem, ptx::sdesc(aA + 2 * 2048, 2048, 128), ptx::sdesc(aW + Lay::B_F2 + 512, 256, 128),
+                         ID_16, 1);
+            ptx::mma_f16(tmem, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + Lay::B_F2 + 1024, 256, 128), ID_16, 1);
+          }))
+        break;
       {
         uint32_t acc[8];
         ptx::tmem_ld8(tlane, acc);
         ptx::tmem_ld_wait();
-        const float* bf2 = reinterpret_cast<const float*>(sW + Lay::BIAS_F2);
         float rr[6];
 #pragma unroll
-        for (int j = 0; j < 6; ++j) rr[j] = u2f(acc[j]) + bf2[j];
+        for (int j = 0; j < 6; ++j) rr[j] = u2f(acc[j]);
         // ---- 3. frame + transform ---------------------------------------
         Frame F = build_frame(rr);
-        to_local(F, wix, wiy, wiz, xl);
-        to_local(F, wox, woy, woz, xl + 3);
+        to_local(F, qc.wix, qc.wiy, qc.wiz, xl);
+        to_local(F, qc.wox, qc.woy, qc.woz, xl + 3);
       }
     } else {
-      xl[0] = wix; xl[1] = wiy; xl[2] = wiz;
-      xl[3] = wox; xl[4] = woy; xl[5] = woz;
+      xl[0] = qc.wix; xl[1] = qc.wiy; xl[2] = qc.wiz;
+      xl[3] = qc.wox; xl[4] = qc.woy; xl[5] = qc.woz;
     }
 
     // ---- 4. decoder ---------------------------------------------------------
@@ -315,22 +344,14 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
     ptx::st_shared_v4(aA + 0 * 2048 + r * 16, z01, z23, z45, z67);
     ptx::st_shared_v4(aA + 1 * 2048 + r * 16, ptx::pack_h2(xl[0], xl[1]), ptx::pack_h2(xl[2], xl[3]),
                       ptx::pack_h2(xl[4], xl[5]), 0x00003C00u);
-    ptx::fence_proxy_async();
-    ptx::tc_fence_before();
-    if (__syncthreads_or(bad)) break;
-    if (tid == 0) {
-      ptx::tc_fence_after();
-      ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_L1, H * 16, 128), ID_H, 0);
-      ptx::mma_commit(bar_m);
-    }
-    mma_pending = true;
-    bad |= !ptx::mbar_wait(bar_m, ph_m, L.timeout_ns);
-    ph_m ^= 1;
-    if (!bad) mma_pending = false;
-    ptx::tc_fence_after();
+    if (!mma_stage([&] {
+          ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_L1, H * 16, 128), ID_H, 0);
+        }))
+      break;
 
     // hidden -> hidden and hidden -> out share the epilogue: TMEM row ->
     // ReLU -> FP16 -> A blocks [0, H/8)
+    bool ok = true;
 #pragma unroll
     for (int layer = 0; layer < 2; ++layer) {
 #pragma unroll
@@ -355,30 +376,23 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
           ptx::st_shared_v4(aA + (c0 / 8 + b) * 2048 + r * 16, pk[4 * b], pk[4 * b + 1], pk[4 * b + 2],
                             pk[4 * b + 3]);
       }
-      ptx::fence_proxy_async();
-      ptx::tc_fence_before();
-      if (__syncthreads_or(bad)) break;
-      if (tid == 0) {
-        ptx::tc_fence_after();
-        const int boff = layer == 0 ? Lay::B_L2 : Lay::B_LO;
-        const int nrows = layer == 0 ? H : 16;
-        const uint32_t id = layer == 0 ? ID_H : ID_16;
+      const int boff = layer == 0 ? Lay::B_L2 : Lay::B_LO;
+      const int nrows = layer == 0 ? H : 16;
+      const uint32_t id = layer == 0 ? ID_H : ID_16;
+      if (!mma_stage([&] {
 #pragma unroll
-        for (int s = 0; s < H / 16; ++s)
-          ptx::mma_f16(tmem, ptx::sdesc(aA + s * 4096, 2048, 128),
-                       ptx::sdesc(aW + boff + s * 2 * nrows * 16, nrows * 16, 128), id, s > 0 ? 1u : 0u);
-        // bias step: A constant blocks (KB, KB+1) x B blocks (H/8, H/8+1)
-        ptx::mma_f16(tmem, ptx::sdesc(aA + Lay::KB * 2048, 2048, 128),
-                     ptx::sdesc(aW + boff + (H / 8) * nrows * 16, nrows * 16, 128), id, 1u);
-        ptx::mma_commit(bar_m);
+            for (int s2 = 0; s2 < H / 16; ++s2)
+              ptx::mma_f16(tmem, ptx::sdesc(aA + s2 * 4096, 2048, 128),
+                           ptx::sdesc(aW + boff + s2 * 2 * nrows * 16, nrows * 16, 128), id, s2 > 0 ? 1u : 0u);
+            // bias step: A constant blocks x B blocks (H/8, H/8+1)
+            ptx::mma_f16(tmem, ptx::sdesc(aConst, 2048, 128),
+                         ptx::sdesc(aW + boff + (H / 8) * nrows * 16, nrows * 16, 128), id, 1u);
+          })) {
+        ok = false;
+        break;
       }
-      mma_pending = true;
-      bad |= !ptx::mbar_wait(bar_m, ph_m, L.timeout_ns);
-      ph_m ^= 1;
-      if (!bad) mma_pending = false;
-      ptx::tc_fence_after();
     }
-    if (bad) break;
+    if (!ok) break;
 
     // ---- 5. output ----------------------------------------------------------
     {
@@ -387,7 +401,7 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
       ptx::tmem_ld_wait();
       float y0 = u2f(acc[0]), y1 = u2f(acc[1]), y2 = u2f(acc[2]);
       if (cosine) {
-        const float cz = fmaxf(wiz, 0.0f);
+        const float cz = fmaxf(qc.wiz, 0.0f);
         y0 *= cz; y1 *= cz; y2 *= cz;
       }
       if (valid) {
@@ -397,6 +411,8 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
       }
     }
     ptx::tc_fence_before();
+    ci = cn;
+    qc = qn;
   }
 
   // ---- teardown: wait (bounded) for copies / MMAs still in flight ----------
