@@ -314,6 +314,11 @@ nam_status nam_inject_fault(nam_ctx* ctx, int32_t fault);
  * FP32 result (host, row-major).  Checks the descriptor and TMEM conventions
  * the evaluation kernels rely on.  Synchronous. */
 nam_status nam_debug_mma_selftest(nam_ctx* ctx, const uint16_t* A_host, const uint16_t* B_host, float* D_host);
+/* The same product with the A operand read from tensor memory: A_rows_host
+ * is A row-major ([128][32] binary16), stored two elements per 32-bit TMEM
+ * column by the kernel; B as above. */
+nam_status nam_debug_mma_selftest_ts(nam_ctx* ctx, const uint16_t* A_rows_host, const uint16_t* B_host,
+                                     float* D_host);
 
 #ifdef __cplusplus
 }

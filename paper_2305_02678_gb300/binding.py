@@ -86,7 +86,7 @@ EXPORTS = ("nam_status_string", "nam_last_error_message", "nam_init", "nam_shutd
            "nam_create_material", "nam_destroy_material", "nam_material_get_info", "nam_material_params",
            "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_backward", "nam_train_step", "nam_now",
            "nam_submit", "nam_poll", "nam_wait", "nam_cancel", "nam_get_stats", "nam_inject_fault",
-           "nam_debug_mma_selftest")
+           "nam_debug_mma_selftest", "nam_debug_mma_selftest_ts")
 
 
 class NamError(RuntimeError):
@@ -123,6 +123,7 @@ def _load():
         "nam_get_stats": (i32, [p, p]),
         "nam_inject_fault": (i32, [p, i32]),
         "nam_debug_mma_selftest": (i32, [p, p, p, p]),
+        "nam_debug_mma_selftest_ts": (i32, [p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -301,4 +302,13 @@ def nam_debug_mma_selftest(ctx, A_bits: np.ndarray, B_bits: np.ndarray) -> np.nd
     assert A.nbytes == 8192 and B.nbytes == 4096
     D = np.zeros((128, 64), dtype=np.float32)
     _check(_lib.nam_debug_mma_selftest(ctx, ptr(A), ptr(B), ptr(D)), "nam_debug_mma_selftest")
+    return D
+
+
+def nam_debug_mma_selftest_ts(ctx, A_rows_bits: np.ndarray, B_bits: np.ndarray) -> np.ndarray:
+    A = np.ascontiguousarray(A_rows_bits, dtype=np.uint16)
+    B = np.ascontiguousarray(B_bits, dtype=np.uint16)
+    assert A.nbytes == 8192 and B.nbytes == 4096
+    D = np.zeros((128, 64), dtype=np.float32)
+    _check(_lib.nam_debug_mma_selftest_ts(ctx, ptr(A), ptr(B), ptr(D)), "nam_debug_mma_selftest_ts")
     return D

@@ -20,6 +20,8 @@
 
 namespace nam {
 int launch_mma_selftest(const uint8_t* A, const uint8_t* B, float* D, uint64_t timeout_ns, int* err, void* stream);
+int launch_mma_selftest_ts(const uint16_t* A, const uint8_t* B, float* D, uint64_t timeout_ns, int* err,
+                           void* stream);
 }
 
 using namespace nam;
@@ -574,6 +576,28 @@ extern "C" nam_status nam_eval_multi(nam_ctx* ctx, const nam_material* mats, int
 // ---------------------------------------------------------------------------
 // diagnostics
 // ---------------------------------------------------------------------------
+extern "C" nam_status nam_debug_mma_selftest_ts(nam_ctx* ctx, const uint16_t* A_rows_host,
+                                                const uint16_t* B_host, float* D_host) {
+  if (!ctx || !A_rows_host || !B_host || !D_host) return fail(NAM_ERR_INVALID_ARG, "NULL argument");
+  DeviceGuard g(ctx->device);
+  void *A = nullptr, *B = nullptr, *D = nullptr;
+  cudaMalloc(&A, 8192);
+  cudaMalloc(&B, 4096);
+  cudaMalloc(&D, 128 * 64 * 4);
+  cudaMemcpy(A, A_rows_host, 8192, cudaMemcpyHostToDevice);
+  cudaMemcpy(B, B_host, 4096, cudaMemcpyHostToDevice);
+  cudaMemset(D, 0, 128 * 64 * 4);
+  int e = launch_mma_selftest_ts((const uint16_t*)A, (const uint8_t*)B, (float*)D, ctx->timeout_ns, ctx->err_word,
+                                 nullptr);
+  if (!e) e = (int)cudaDeviceSynchronize();
+  if (!e) e = (int)cudaMemcpy(D_host, D, 128 * 64 * 4, cudaMemcpyDeviceToHost);
+  cudaFree(A);
+  cudaFree(B);
+  cudaFree(D);
+  if (e) return cuda_fail(e, "nam_debug_mma_selftest_ts");
+  return nam_check_device_error(ctx);
+}
+
 extern "C" nam_status nam_debug_mma_selftest(nam_ctx* ctx, const uint16_t* A_host, const uint16_t* B_host,
                                              float* D_host) {
   if (!ctx || !A_host || !B_host || !D_host) return fail(NAM_ERR_INVALID_ARG, "NULL argument");

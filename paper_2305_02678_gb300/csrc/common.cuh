@@ -134,6 +134,83 @@ __device__ __forceinline__ void fetch_latent(const PyrDesc& P, const void* pyr, 
   }
 }
 
+// The same fetch split in two so that the texel loads can be issued a tile
+// ahead of their use (FP16 pyramids): issue_taps computes the (up to) eight
+// tap indices and weights and starts the 16-byte loads; finish_taps filters.
+// Taps of a level with zero weight are not loaded.
+struct Taps8 {
+  uint4 t[8];
+  float w[8];
+};
+
+__device__ __forceinline__ void level_taps_f16(const PyrDesc& P, const uint4* __restrict__ p, int l, float u, float v,
+                                               float wgt, uint4* t, float* w) {
+  const int W = P.w[l], H = P.h[l];
+  int x0, x1, y0, y1;
+  float fx, fy;
+  tap_axis(P, u, W, x0, x1, fx);
+  tap_axis(P, v, H, y0, y1, fy);
+  const uint32_t base = (uint32_t)P.off[l];
+  const uint32_t r0 = base + (uint32_t)y0 * (uint32_t)W, r1 = base + (uint32_t)y1 * (uint32_t)W;
+  const float gx = 1.0f - fx, gy = 1.0f - fy;
+  w[0] = gx * gy * wgt;
+  w[1] = fx * gy * wgt;
+  w[2] = gx * fy * wgt;
+  w[3] = fx * fy * wgt;
+  t[0] = __ldg(p + r0 + x0);
+  t[1] = __ldg(p + r0 + x1);
+  t[2] = __ldg(p + r1 + x0);
+  t[3] = __ldg(p + r1 + x1);
+}
+
+__device__ __forceinline__ void issue_taps(const PyrDesc& P, const void* pyr, float u, float v, float lod, float xi,
+                                           Taps8& T) {
+  const uint4* p = reinterpret_cast<const uint4*>(pyr);
+  LevelPick lp = pick_levels(P, lod);
+  if (P.filter == NAM_FILTER_STOCHASTIC) {
+    level_taps_f16(P, p, xi < lp.t ? lp.l1 : lp.l0, u, v, 1.0f, T.t, T.w);
+  } else {
+    level_taps_f16(P, p, lp.l0, u, v, 1.0f - lp.t, T.t, T.w);
+    if (lp.t != 0.0f) {
+      level_taps_f16(P, p, lp.l1, u, v, lp.t, T.t + 4, T.w + 4);
+      return;
+    }
+  }
+#pragma unroll
+  for (int k = 4; k < 8; ++k) {
+    T.t[k] = make_uint4(0u, 0u, 0u, 0u);
+    T.w[k] = 0.0f;
+  }
+}
+
+// Packed FP32x2 FMA (sm_100 family); defined with the tensor-core helpers.
+__device__ __forceinline__ float2 fma2_f32(float2 a, float2 b, float2 c) {
+  unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
+  unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
+  unsigned long long rc = *reinterpret_cast<unsigned long long*>(&c);
+  unsigned long long rd;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+  return *reinterpret_cast<float2*>(&rd);
+}
+
+__device__ __forceinline__ void finish_taps(const Taps8& T, float z[8]) {
+  float2 acc[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc[c] = make_float2(0.0f, 0.0f);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const __half2* h = reinterpret_cast<const __half2*>(&T.t[k]);
+    const float2 wk = make_float2(T.w[k], T.w[k]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[c] = fma2_f32(wk, __half22float2(h[c]), acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    z[2 * c] = acc[c].x;
+    z[2 * c + 1] = acc[c].y;
+  }
+}
+
 // Shading frame from r = (n_raw, t_raw) (Sec. 4.2, Eq. 4; b = n x t / |n x t|,
 // Sec. 9): n = n_raw / |n_raw|, t = Gram-Schmidt of t_raw against n,
 // normalised.  Degenerate inputs: |n_raw| < 1e-20 -> n = (0,0,1);

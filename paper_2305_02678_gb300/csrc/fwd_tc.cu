@@ -178,7 +178,7 @@ __device__ __forceinline__ QueryIn load_query(const QueryPtrs& q, int64_t i) {
 }
 
 template <int H, bool FRAME, bool F16P>
-__global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
+__global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
   using Lay = TcLayout<H, FRAME>;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sW = smem;
@@ -248,10 +248,12 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
 
   ChunkIn ci{};
   QueryIn qc{};
+  Taps8 tc{};  // texels of the current tile (FP16 pyramids), loaded a tile ahead
   if (c_begin < c_end) {
     ci = chunk_at(L, c_begin);
     qc = load_query(L.q, ci.start + (r < ci.count ? r : 0));
   }
+  bool taps_ready = false;
   for (int64_t c = c_begin; c < c_end; ++c) {
     // prefetch the next tile's inputs; consumed one iteration later
     ChunkIn cn = ci;
@@ -281,7 +283,13 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
 
     // ---- 1. latent fetch ------------------------------------------------
     float z[8];
-    fetch_latent<F16P>(L.pyr, pyr, qc.u, qc.v, qc.lod, qc.xi, z);
+    if (F16P) {
+      if (!taps_ready) issue_taps(L.pyr, pyr, qc.u, qc.v, qc.lod, qc.xi, tc);
+      finish_taps(tc, z);
+    } else {
+      fetch_latent<F16P>(L.pyr, pyr, qc.u, qc.v, qc.lod, qc.xi, z);
+    }
+    taps_ready = false;
     const uint32_t z01 = ptx::pack_h2(z[0], z[1]), z23 = ptx::pack_h2(z[2], z[3]);
     const uint32_t z45 = ptx::pack_h2(z[4], z[5]), z67 = ptx::pack_h2(z[6], z[7]);
 
@@ -348,6 +356,12 @@ __global__ void __launch_bounds__(128) eval_tc_kernel(const LaunchCommon L) {
           ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_L1, H * 16, 128), ID_H, 0);
         }))
       break;
+
+    // texels of the next tile start loading now, under the hidden layers
+    if (F16P && c + 1 < c_end && cn.mat == ci.mat) {
+      issue_taps(L.pyr, pyr, qn.u, qn.v, qn.lod, qn.xi, tc);
+      taps_ready = true;
+    }
 
     // hidden -> hidden and hidden -> out share the epilogue: TMEM row ->
     // ReLU -> FP16 -> A blocks [0, H/8)
@@ -521,6 +535,72 @@ __global__ void __launch_bounds__(128) mma_selftest_kernel(const uint8_t* A, con
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, 64);
   }
+}
+
+// Same product with A taken from TMEM: thread r stores row r of A (two fp16
+// per 32-bit column, element 2j in the low half of column j) with
+// tcgen05.st, and two K=16 MMAs read it at columns +0 and +8.
+__global__ void __launch_bounds__(128) mma_selftest_ts_kernel(const uint16_t* A, const uint8_t* B, float* D,
+                                                              uint64_t timeout_ns, int* err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* sB = smem;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 16384);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int k = tid; k < 4096 / 16; k += 128) reinterpret_cast<uint4*>(sB)[k] = reinterpret_cast<const uint4*>(B)[k];
+  const uint32_t b = ptx::smem_u32(bar);
+  if (tid == 0) {
+    ptx::mbar_init(b, 1);
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0) {
+    ptx::tmem_alloc(ptx::smem_u32(tslot), 128);
+    ptx::tmem_relinquish();
+  }
+  ptx::fence_proxy_async();
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t lane = (uint32_t)(warp * 32) << 16;
+  uint32_t row[16];
+  for (int j = 0; j < 16; ++j) row[j] = (uint32_t)A[tid * 32 + 2 * j] | ((uint32_t)A[tid * 32 + 2 * j + 1] << 16);
+  ptx::tmem_st16(tmem + lane + 64, row);
+  ptx::tmem_st_wait();
+  ptx::tc_fence_before();
+  __syncthreads();
+  const uint32_t aB = ptx::smem_u32(sB);
+  if (tid == 0) {
+    ptx::tc_fence_after();
+    constexpr uint32_t id = ptx::idesc_f16(128, 64);
+    ptx::mma_f16_ts(tmem, tmem + 64, ptx::sdesc(aB, 64 * 16, 128), id, 0);
+    ptx::mma_f16_ts(tmem, tmem + 64 + 8, ptx::sdesc(aB + 2 * 64 * 16, 64 * 16, 128), id, 1);
+    ptx::mma_commit(b);
+  }
+  bool ok = ptx::mbar_wait(b, 0, timeout_ns);
+  if (!ok && tid == 0) record_error(err, DEVERR_WAIT_TIMEOUT);
+  ptx::tc_fence_after();
+  if (ok) {
+    uint32_t acc[32];
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      ptx::tmem_ld32(tmem + lane + c0, acc);
+      ptx::tmem_ld_wait();
+      for (int j = 0; j < 32; ++j) D[tid * 64 + c0 + j] = u2f(acc[j]);
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 128);
+  }
+}
+
+int launch_mma_selftest_ts(const uint16_t* A, const uint8_t* B, float* D, uint64_t timeout_ns, int* err,
+                           void* stream) {
+  const int smem = 16384 + 64;
+  mma_selftest_ts_kernel<<<1, 128, smem, (cudaStream_t)stream>>>(A, B, D, timeout_ns, err);
+  return (int)cudaGetLastError();
 }
 
 int launch_mma_selftest(const uint8_t* A, const uint8_t* B, float* D, uint64_t timeout_ns, int* err,

@@ -18,3 +18,13 @@ def test_single_mma_matches_numpy(gctx):
     D = B.nam_debug_mma_selftest(gctx.h, kmajor_pack(A), kmajor_pack(Bm))
     ref = A @ Bm.T
     assert np.array_equal(D, ref.astype(np.float32)), f"max diff {np.abs(D - ref).max()}"
+
+
+def test_single_mma_with_a_from_tensor_memory(gctx):
+    from paper_2305_02678_gb300 import binding as B
+    rng = np.random.default_rng(1)
+    A = rng.integers(-4, 5, size=(128, 32)) / 4.0
+    Bm = rng.integers(-4, 5, size=(64, 32)) / 4.0
+    D = B.nam_debug_mma_selftest_ts(gctx.h, A.astype(np.float16).view(np.uint16), kmajor_pack(Bm))
+    ref = A @ Bm.T
+    assert np.array_equal(D, ref.astype(np.float32)), f"max diff {np.abs(D - ref).max()}"
