@@ -242,6 +242,30 @@ typedef struct {
 nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
                           int64_t n, const nam_adam* opt, float* loss_out, void* stream, uint32_t flags);
 
+/* A training step that allocates no device memory.  The paper has no
+ * counterpart: this is a library facility.  nam_train_step allocates its
+ * per-batch buffers (forward RGB, dL/dRGB, loss accumulator) on first use and
+ * again when the batch grows; callers that may not call cudaMalloc while they
+ * run -- a fixed memory plan, an embedding host that owns all allocation, a
+ * loop that must not synchronise the device the way cudaMalloc/cudaFree can --
+ * call this instead.  It does exactly what nam_train_step does, with those
+ * buffers in one static device array of the library
+ * (NAM_NOALLOC_TRAIN_MAX_QUERIES * 24 + 256 bytes, held by every GPU that
+ * loads libnam until the process exits).
+ *  - n must be at most NAM_NOALLOC_TRAIN_MAX_QUERIES; larger batches are
+ *    refused with NAM_ERR_INVALID_ARG before anything is enqueued.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) for that device; make that first call before any
+ *    stream capture.
+ *  - All calls share the array, which keeps the last call's contents (the
+ *    loss accumulator is cleared by each call).  Calls whose work overlaps on
+ *    the GPU (different streams, no ordering between them) race on it: order
+ *    them on one stream.
+ *  - Arguments, results and errors as nam_train_step. */
+#define NAM_NOALLOC_TRAIN_MAX_QUERIES 65536
+nam_status nam_train_step_noalloc(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
+                                  int64_t n, const nam_adam* opt, float* loss_out, void* stream, uint32_t flags);
+
 /* ------------------------------------------------------------------------ */
 /* serving: continuous batching of frames (Sec. 7.3 coherency analogue)      */
 /* ------------------------------------------------------------------------ */

@@ -84,7 +84,8 @@ class nam_stats(C.Structure):
 #: every symbol include/nam.h declares
 EXPORTS = ("nam_status_string", "nam_last_error_message", "nam_init", "nam_shutdown", "nam_check_device_error",
            "nam_create_material", "nam_destroy_material", "nam_material_get_info", "nam_material_params",
-           "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_backward", "nam_train_step", "nam_now",
+           "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_backward", "nam_train_step",
+           "nam_train_step_noalloc", "nam_now",
            "nam_submit", "nam_poll", "nam_wait", "nam_cancel", "nam_get_stats", "nam_inject_fault",
            "nam_debug_mma_selftest", "nam_debug_mma_selftest_ts")
 
@@ -115,6 +116,7 @@ def _load():
         "nam_eval_multi": (i32, [p, p, i32, p, p, i32, p, p, u32]),
         "nam_backward": (i32, [p, p, p, i64, p, p, p, p, u32]),
         "nam_train_step": (i32, [p, p, p, p, i64, p, p, p, u32]),
+        "nam_train_step_noalloc": (i32, [p, p, p, p, i64, p, p, p, u32]),
         "nam_now": (C.c_double, []),
         "nam_submit": (i32, [p, p, p]),
         "nam_poll": (i32, [p, u64, p, p]),
@@ -256,6 +258,21 @@ def nam_train_step(ctx, mat, q, target_rgb, n, lr_params=1e-3, lr_pyramid=1e-2, 
     qs = make_queries(q)
     _check(_lib.nam_train_step(ctx, mat, C.byref(qs), ptr(target_rgb), int(n), C.byref(opt), C.byref(loss),
                                _stream(stream), flags), "nam_train_step")
+    return loss.value
+
+
+NAM_NOALLOC_TRAIN_MAX_QUERIES = 65536
+
+
+def nam_train_step_noalloc(ctx, mat, q, target_rgb, n, lr_params=1e-3, lr_pyramid=1e-2, beta1=0.9, beta2=0.999,
+                           eps=1e-8, step=1, stream=None, flags=0):
+    """nam_train_step with its per-batch buffers in the library's static
+    device array (no device allocation; n <= NAM_NOALLOC_TRAIN_MAX_QUERIES)."""
+    opt = nam_adam(lr_params, lr_pyramid, beta1, beta2, eps, step)
+    loss = C.c_float(0.0)
+    qs = make_queries(q)
+    _check(_lib.nam_train_step_noalloc(ctx, mat, C.byref(qs), ptr(target_rgb), int(n), C.byref(opt), C.byref(loss),
+                                       _stream(stream), flags), "nam_train_step_noalloc")
     return loss.value
 
 
