@@ -371,6 +371,7 @@ def run_ours(args):
 
     # ---- precision sweep on the same workload ----------------------------
     sweep = {}
+    out8 = None
     if not args.no_sweep:
         mat32 = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"],
                              precision=B.NAM_PREC_F32)
@@ -378,11 +379,25 @@ def run_ours(args):
         t32 = time_launches(lambda: B.nam_eval(ctx.h, mat32.h, dq, n, out32, stream, 0),
                             max(3, args.steps // 4), 2, flush, stream)
         ms32 = statistics.fmean(t32)
-        sweep["fp32_evals_per_s"] = n / (ms32 * 1e-3)
+        sweep["fp32_evals_per_s"] = round(n / (ms32 * 1e-3), 1)
         sweep["fp32_ms"] = round(ms32, 4)
         sweep["fp16_speedup_vs_fp32"] = round(ms32 / ms, 2)
         mat32.destroy()
-        sweep["fp8"] = "not built"
+        # FP8: static activation scales from a 65,536-query calibration batch
+        cq = W.calibration_queries(2)
+        dcq = {k: torch.from_numpy(v).to(dev) for k, v in cq.items() if k != "xi"}
+        scales = B.nam_fp8_calibrate(ctx.h, mat16.h, dcq, len(cq["u"]), stream)[:3]
+        mat8 = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"],
+                            precision=B.NAM_PREC_FP8, act_scale=scales)
+        out8 = torch.empty((n, 3), device=dev)
+        t8 = time_launches(lambda: B.nam_eval(ctx.h, mat8.h, dq, n, out8, stream, 0), max(3, args.steps // 2), 2,
+                           flush, stream)
+        ms8 = statistics.fmean(t8)
+        sweep["fp8_evals_per_s"] = round(n / (ms8 * 1e-3), 1)
+        sweep["fp8_ms"] = round(ms8, 4)
+        sweep["fp8_speedup_vs_fp32"] = round(ms32 / ms8, 2)
+        sweep["fp8_act_scales"] = [float(x) for x in scales]
+        mat8.destroy()
     # ---- serving stream ---------------------------------------------------
     serving = None
     if not args.no_serve and rank == 0:
@@ -391,7 +406,8 @@ def run_ours(args):
     # ---- CPU baseline: the FP64 oracle on the host cores -------------------
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
-        cpu = cpu_baseline(w, out16.cpu().numpy(), args.cpu_seconds)
+        cpu = cpu_baseline(w, out16.cpu().numpy(), args.cpu_seconds,
+                           None if out8 is None else out8.cpu().numpy())
 
     mat16.destroy()
     ctx.close()
@@ -491,7 +507,7 @@ def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30):
     return out
 
 
-def cpu_baseline(w, gpu_out16, seconds):
+def cpu_baseline(w, gpu_out16, seconds, gpu_out8=None):
     """FP64 oracle (as it stands) on all host cores over a bounded sample of
     the same workload: consecutive queries of the 1080p frame, wrapping
     around, about `seconds` of work; also the GPU FP16 result's error on the
@@ -522,13 +538,25 @@ def cpu_baseline(w, gpu_out16, seconds):
     emu = O.eval(O.Model.from_workload(w, params="fp16", act_round=O.ROUND_FP16), sub, nthreads=cores)
     e_emu = O.relative_error(gpu_out16[:c], emu)
     e_exact = O.relative_error(gpu_out16[:c], ref)
+    master = O.eval(O.Model.from_workload(w), sub, nthreads=cores)
+    e_master = O.relative_error(gpu_out16[:c], master)
+    fp8 = None
+    if gpu_out8 is not None:
+        ref8 = O.eval(O.Model.from_workload(w, params="fp8"), sub, nthreads=cores)
+        e8 = O.relative_error(gpu_out8[:c], ref8)
+        e8m = O.relative_error(gpu_out8[:c], master)
+        fp8 = {"vs_e4m3_weight_oracle_max": e8[0], "vs_e4m3_weight_oracle_mean": e8[1],
+               "vs_fp32_master_oracle_max": e8m[0], "vs_fp32_master_oracle_mean": e8m[1]}
     return {"value": round(done / dt, 1), "unit": "evals/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} queries: the 1920x1080 workload's queries in order, wrapping around "
                       f"(FP64, FP16-quantised parameters, {cores} threads)",
             "seconds": round(dt, 2),
             "gpu_fp16_error_on_sample": {"queries": c, "vs_fp16_operand_oracle_max": e_emu[0],
                                          "vs_unrounded_oracle_max": e_exact[0],
-                                         "vs_unrounded_oracle_mean": e_exact[1]}}
+                                         "vs_unrounded_oracle_mean": e_exact[1],
+                                         "vs_fp32_master_oracle_max": e_master[0],
+                                         "vs_fp32_master_oracle_mean": e_master[1]},
+            "gpu_fp8_error_on_sample": fp8}
 
 
 # ----------------------------------------------------------------------------

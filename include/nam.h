@@ -195,6 +195,19 @@ nam_status nam_eval(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t 
 nam_status nam_eval_host(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
                          float* rgb_out, void* stream, uint32_t flags);
 
+/* Static activation scales for NAM_PREC_FP8 from a calibration batch (FP8
+ * inference is beyond the paper, which stops at FP16 parameters, Sec. 5.2):
+ * evaluates material m's FP32 master parameters with the FP32 kernel on n
+ * device queries and writes act_scale_out[l] = (max over the batch of
+ * |input of decoder layer l|) / 448 for each of the n_layers decoder layers
+ * (1 where that maximum is 0), so that the largest input seen maps to the
+ * largest E4M3 magnitude.  Layer 0's input is (z, wi', wo'); later layers'
+ * inputs are the previous layer's ReLU outputs.  act_scale_out: host array
+ * of n_layers floats, ready for nam_material_desc.fp8_act_scale.  m may have
+ * any precision.  Synchronises `stream`. */
+nam_status nam_fp8_calibrate(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
+                             float* act_scale_out, void* stream);
+
 /* A contiguous run of queries [start, start+count) evaluated with
  * materials[material]. */
 typedef struct {
@@ -203,13 +216,13 @@ typedef struct {
   int32_t material;
 } nam_work_item;
 
-/* Evaluate work items (device array `items`, n_items entries) that each use
- * one of nmat materials (device queries and output, as nam_eval).  All
- * materials must share precision and decoder widths.  Each item's queries
- * run on the path a single-material launch would use, so a query's result
- * does not depend on the other items. */
+/* Evaluate work items (HOST array `items`, n_items entries, read before the
+ * call returns) that each use one of nmat materials (device queries and
+ * output, as nam_eval).  All materials must share precision and decoder
+ * widths.  Each item's queries run on the path a single-material launch
+ * would use, so a query's result does not depend on the other items. */
 nam_status nam_eval_multi(nam_ctx* ctx, const nam_material* materials, int32_t nmat,
-                          const nam_queries* q, const nam_work_item* items_dev, int32_t n_items,
+                          const nam_queries* q, const nam_work_item* items, int32_t n_items,
                           float* rgb_out, void* stream, uint32_t flags);
 
 /* ------------------------------------------------------------------------ */

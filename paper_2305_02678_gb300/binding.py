@@ -84,7 +84,7 @@ class nam_stats(C.Structure):
 #: every symbol include/nam.h declares
 EXPORTS = ("nam_status_string", "nam_last_error_message", "nam_init", "nam_shutdown", "nam_check_device_error",
            "nam_create_material", "nam_destroy_material", "nam_material_get_info", "nam_material_params",
-           "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_backward", "nam_train_step",
+           "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_fp8_calibrate", "nam_backward", "nam_train_step",
            "nam_train_step_noalloc", "nam_now",
            "nam_submit", "nam_poll", "nam_wait", "nam_cancel", "nam_get_stats", "nam_inject_fault",
            "nam_debug_mma_selftest", "nam_debug_mma_selftest_ts")
@@ -117,6 +117,7 @@ def _load():
         "nam_backward": (i32, [p, p, p, i64, p, p, p, p, u32]),
         "nam_train_step": (i32, [p, p, p, p, i64, p, p, p, u32]),
         "nam_train_step_noalloc": (i32, [p, p, p, p, i64, p, p, p, u32]),
+        "nam_fp8_calibrate": (i32, [p, p, p, i64, p, p]),
         "nam_now": (C.c_double, []),
         "nam_submit": (i32, [p, p, p]),
         "nam_poll": (i32, [p, u64, p, p]),
@@ -228,6 +229,16 @@ def nam_material_params(ctx, mat):
 def nam_eval(ctx, mat, q, n, rgb_out, stream=None, flags=0):
     qs = make_queries(q)
     _check(_lib.nam_eval(ctx, mat, C.byref(qs), int(n), ptr(rgb_out), _stream(stream), flags), "nam_eval")
+
+
+def nam_fp8_calibrate(ctx, mat, q, n, stream=None):
+    """Static per-layer FP8 activation scales (max |layer input| / 448) of
+    material `mat` over n device queries; returns a float32 numpy array."""
+    qs = make_queries(q)
+    out = np.zeros(NAM_MAX_LAYERS, dtype=np.float32)
+    _check(_lib.nam_fp8_calibrate(ctx, mat, C.byref(qs), int(n), out.ctypes.data, _stream(stream)),
+           "nam_fp8_calibrate")
+    return out
 
 
 def nam_eval_host(ctx, mat, q, n, rgb_out, stream=None, flags=0):

@@ -440,6 +440,34 @@ extern "C" nam_status nam_eval(nam_ctx* ctx, nam_material m, const nam_queries* 
   return NAM_OK;
 }
 
+extern "C" nam_status nam_fp8_calibrate(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
+                                        float* act_scale_out, void* stream) {
+  if (!ctx || !m || !act_scale_out) return fail(NAM_ERR_INVALID_ARG, "nam_fp8_calibrate: NULL argument");
+  if (n <= 0) return fail(NAM_ERR_INVALID_ARG, "nam_fp8_calibrate: n must be > 0");
+  if (!owns(ctx, m)) return fail(NAM_ERR_NOT_FOUND, "nam_fp8_calibrate: unknown material");
+  nam_status st = check_queries(m, q);
+  if (st) return st;
+  const int nl = m->desc.n_layers;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  float* amax = nullptr;
+  cudaError_t ce = cudaMallocAsync((void**)&amax, 4 * sizeof(float), s);
+  if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_fp8_calibrate: allocation");
+  ce = cudaMemsetAsync(amax, 0, 4 * sizeof(float), s);
+  LaunchCommon L;
+  fill_launch(ctx, m, q, n, nullptr, 0, &L);
+  L.w0 = m->params;  // FP32 masters, whatever the material's precision
+  L.amax = amax;
+  int e = ce == cudaSuccess ? launch_eval_f32(L, stream) : (int)ce;
+  float h[4] = {0, 0, 0, 0};
+  if (!e) e = (int)cudaMemcpyAsync(h, amax, sizeof h, cudaMemcpyDeviceToHost, s);
+  cudaFreeAsync(amax, s);
+  if (!e) e = (int)cudaStreamSynchronize(s);
+  if (e) return cuda_fail(e, "nam_fp8_calibrate");
+  for (int l = 0; l < nl; ++l) act_scale_out[l] = h[l] > 0.0f ? h[l] / 448.0f : 1.0f;
+  return NAM_OK;
+}
+
 extern "C" nam_status nam_eval_host(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n, float* rgb_out,
                                     void* stream, uint32_t flags) {
   if (!ctx || !m) return fail(NAM_ERR_INVALID_ARG, "nam_eval_host: NULL context or material");

@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(128) eval_f32_kernel(LaunchCommon L) {
   __syncthreads();
   const QueryPtrs& q = L.q;
   const bool cosine = (L.flags & NAM_OUT_COSINE) != 0;
+  const bool calib = L.amax != nullptr;
+  float am0 = 0.0f, am1 = 0.0f, am2 = 0.0f;  // calibration: max |layer input|
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < L.n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float z[8];
@@ -120,11 +122,18 @@ __global__ void __launch_bounds__(128) eval_f32_kernel(LaunchCommon L) {
     float h1[H];
 #pragma unroll
     for (int j = 0; j < H; ++j) h1[j] = fmaxf(S.b1[j] + dot_row<16>(&S.W1[j * 16], x), 0.0f);
+    if (calib) {
+#pragma unroll
+      for (int c = 0; c < 14; ++c) am0 = fmaxf(am0, fabsf(x[c]));
+#pragma unroll
+      for (int j = 0; j < H; ++j) am1 = fmaxf(am1, h1[j]);
+    }
     float y0 = S.bo[0], y1 = S.bo[1], y2 = S.bo[2];
     if (NH == 2) {
 #pragma unroll 4
       for (int j = 0; j < H; ++j) {
         float s = fmaxf(S.bh[0][j] + dot_row<H>(&S.Wh[0][j * H], h1), 0.0f);
+        am2 = fmaxf(am2, s);
         float4 wo = reinterpret_cast<const float4*>(S.WoT)[j];
         y0 = fmaf(wo.x, s, y0);
         y1 = fmaf(wo.y, s, y1);
@@ -147,9 +156,24 @@ __global__ void __launch_bounds__(128) eval_f32_kernel(LaunchCommon L) {
       float c = fmaxf(wiz, 0.0f);
       y0 *= c; y1 *= c; y2 *= c;
     }
-    L.rgb[3 * i + 0] = y0;
-    L.rgb[3 * i + 1] = y1;
-    L.rgb[3 * i + 2] = y2;
+    if (L.rgb) {
+      L.rgb[3 * i + 0] = y0;
+      L.rgb[3 * i + 1] = y1;
+      L.rgb[3 * i + 2] = y2;
+    }
+  }
+  if (calib) {
+    // non-negative floats order like their bit patterns: integer atomic max
+    for (int o = 16; o > 0; o >>= 1) {
+      am0 = fmaxf(am0, __shfl_xor_sync(0xffffffffu, am0, o));
+      am1 = fmaxf(am1, __shfl_xor_sync(0xffffffffu, am1, o));
+      am2 = fmaxf(am2, __shfl_xor_sync(0xffffffffu, am2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(reinterpret_cast<int*>(L.amax) + 0, __float_as_int(am0));
+      atomicMax(reinterpret_cast<int*>(L.amax) + 1, __float_as_int(am1));
+      atomicMax(reinterpret_cast<int*>(L.amax) + 2, __float_as_int(am2));
+    }
   }
 }
 

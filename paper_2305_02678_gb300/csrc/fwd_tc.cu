@@ -20,6 +20,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstring>
 
 #include "common.cuh"
@@ -56,16 +57,45 @@ struct TcLayout {
   static constexpr int SMEM = BLOB_ALIGNED + A_BYTES + 64;
 };
 
+// FP8 (E4M3) decoder: the A region and the frame blocks are those of the FP16
+// layout; the decoder's B operands hold E4M3 codes in the canonical K-major
+// layout for 8-bit types (8-row x 16-byte core matrices = 16 codes along K),
+// K padded to the 32 of one kind::f8f6f4 MMA.  The biases stay FP32 and are
+// added in the epilogue together with the per-layer scales:
+//   next-layer code = E4M3(relu(D * c_l + b'_l)),  c_l = s_l sw_l / s_{l+1},
+//   b'_l = b_l / s_{l+1};  output = D * c_2 + b_2,  c_2 = s_2 sw_2,
+// where D = sum of code products (FP32, in TMEM), s_l the static input scale
+// of decoder layer l and sw_l its weight scale.
+template <int H, bool FRAME>
+struct TcLayout8 {
+  static constexpr int KP = H < 32 ? 32 : H;              // hidden K padded to one MMA step
+  static constexpr int B_L1 = FRAME ? 2560 : 0;           // H x 32 codes
+  static constexpr int B_L2 = B_L1 + H * 32;              // H x KP codes
+  static constexpr int B_LO = B_L2 + H * KP;              // 16 x KP codes
+  static constexpr int B_SC = (B_LO + 16 * KP + 15) / 16 * 16;  // FP32: inv_s0, c0, c1, c2
+  static constexpr int B_B1 = B_SC + 16;                  // FP32 b'_0 [H]
+  static constexpr int B_B2 = B_B1 + H * 4;               // FP32 b'_1 [H]
+  static constexpr int B_B3 = B_B2 + H * 4;               // FP32 b_2 [4]
+  static constexpr int BLOB = B_B3 + 16;
+  static constexpr int BLOB_ALIGNED = (BLOB + 127) / 128 * 128;
+  static constexpr int SMEM = BLOB_ALIGNED + TcLayout<H, FRAME>::A_BYTES + 64;
+};
+
+template <int H, bool FRAME>
+static size_t blob_bytes_of(int precision) {
+  return precision == NAM_PREC_FP8 ? (size_t)TcLayout8<H, FRAME>::BLOB : (size_t)TcLayout<H, FRAME>::BLOB;
+}
+
 size_t tc_blob_bytes(const Shape& s, int precision) {
-  if (precision != NAM_PREC_F16 || s.NH != 2) return 0;
+  if ((precision != NAM_PREC_F16 && precision != NAM_PREC_FP8) || s.NH != 2) return 0;
   if (s.frame) {
-    if (s.H == 16) return TcLayout<16, true>::BLOB;
-    if (s.H == 32) return TcLayout<32, true>::BLOB;
-    if (s.H == 64) return TcLayout<64, true>::BLOB;
+    if (s.H == 16) return blob_bytes_of<16, true>(precision);
+    if (s.H == 32) return blob_bytes_of<32, true>(precision);
+    if (s.H == 64) return blob_bytes_of<64, true>(precision);
   } else {
-    if (s.H == 16) return TcLayout<16, false>::BLOB;
-    if (s.H == 32) return TcLayout<32, false>::BLOB;
-    if (s.H == 64) return TcLayout<64, false>::BLOB;
+    if (s.H == 16) return blob_bytes_of<16, false>(precision);
+    if (s.H == 32) return blob_bytes_of<32, false>(precision);
+    if (s.H == 64) return blob_bytes_of<64, false>(precision);
   }
   return 0;
 }
@@ -75,14 +105,57 @@ static void put_h(uint8_t* base, int R, int row, int k, float v) {
   std::memcpy(base + kmajor_off(R, row, k), &h, 2);
 }
 
+// E4M3 (OCP 8-bit float, "FN" variant: bias 7, no infinities, S.1111.111 the
+// only NaN, largest finite 448) of an FP32 value, round to nearest even,
+// saturating to +-448.  Written from the format's definition.
+static uint8_t e4m3_of(float x) {
+  if (std::isnan(x)) return 0x7F;
+  const uint8_t sign = std::signbit(x) ? 0x80 : 0x00;
+  const double a = std::fabs((double)x);
+  if (a >= 448.0) return sign | 0x7E;
+  if (a < 0.015625) {  // below 2^-6: subnormal codes, spacing 2^-9
+    const int m = (int)std::nearbyint(a * 512.0);  // m = 8 is the smallest normal
+    return sign | (uint8_t)m;
+  }
+  int e2;
+  const double f = std::frexp(a, &e2);  // a = f 2^e2, f in [0.5, 1)
+  int E = e2 - 1;
+  int m = (int)std::nearbyint((f * 2.0 - 1.0) * 8.0);
+  if (m == 8) {
+    m = 0;
+    ++E;
+  }
+  if (E > 8 || (E == 8 && m == 7)) return sign | 0x7E;
+  return sign | (uint8_t)(((E + 7) << 3) | m);
+}
+
+// Canonical no-swizzle K-major 8-bit layout of an R x K operand: element
+// (row, k) at byte (k / 16) * (R * 16) + row * 16 + (k % 16).
+static inline int kmajor_off8(int R, int row, int k) { return (k / 16) * (R * 16) + row * 16 + (k % 16); }
+
+// Per-layer E4M3 weights: sw = absmax(W) / 448 in FP32, code = E4M3(W / sw)
+// with the division in FP32.
+static float quantize_layer_e4m3(const float* W, int rows, int cols, uint8_t* base, int R, float* sw_out) {
+  float amax = 0.0f;
+  for (int i = 0; i < rows * cols; ++i) amax = std::fmax(amax, std::fabs(W[i]));
+  const float sw = amax > 0.0f ? amax / 448.0f : 1.0f;
+  for (int n = 0; n < rows; ++n)
+    for (int k = 0; k < cols; ++k) base[kmajor_off8(R, n, k)] = e4m3_of(W[n * cols + k] / sw);
+  *sw_out = sw;
+  return sw;
+}
+
+static void put_f(uint8_t* base, int idx, float v) { std::memcpy(base + 4 * idx, &v, 4); }
+
 // Lay out the FP16-quantised weights as MMA B operands (N rows = outputs,
 // K = inputs, K-major), each layer's bias in the extra input column that
 // meets the constant-1 column of the A operand.  The frame layers take their
 // FP16 operand in two halves (high part, residual), so their weights appear
-// twice along K.
-int pack_tc_blob(const Shape& s, int precision, const float* frame, const float* dec, const float* /*act_scale*/,
-                 uint8_t* out, float* /*weight_scales_out*/) {
-  if (precision != NAM_PREC_F16) return -1;
+// twice along K.  FP8: the frame part is the same; the decoder part is laid
+// out as TcLayout8 describes.
+int pack_tc_blob(const Shape& s, int precision, const float* frame, const float* dec, const float* act_scale,
+                 uint8_t* out, float* weight_scales_out) {
+  if (precision != NAM_PREC_F16 && precision != NAM_PREC_FP8) return -1;
   const size_t bytes = tc_blob_bytes(s, precision);
   if (!bytes) return -1;
   std::memset(out, 0, bytes);
@@ -110,6 +183,29 @@ int pack_tc_blob(const Shape& s, int precision, const float* frame, const float*
   const float* b2 = W2 + H * H;
   const float* W3 = b2 + H;              // [3][H]
   const float* b3 = W3 + 3 * H;
+  if (precision == NAM_PREC_FP8) {
+    if (!act_scale) return -1;
+    const int KP = H < 32 ? 32 : H;
+    const int b_l1 = s.frame ? 2560 : 0, b_l2 = b_l1 + H * 32, b_lo = b_l2 + H * KP;
+    const int b_sc = (b_lo + 16 * KP + 15) / 16 * 16, b_b1 = b_sc + 16, b_b2 = b_b1 + H * 4, b_b3 = b_b2 + H * 4;
+    float sw[3];
+    quantize_layer_e4m3(W1, H, 14, out + b_l1, H, &sw[0]);
+    quantize_layer_e4m3(W2, H, H, out + b_l2, H, &sw[1]);
+    quantize_layer_e4m3(W3, 3, H, out + b_lo, 16, &sw[2]);
+    const float inv0 = 1.0f / act_scale[0], inv1 = 1.0f / act_scale[1], inv2 = 1.0f / act_scale[2];
+    put_f(out + b_sc, 0, inv0);
+    put_f(out + b_sc, 1, (act_scale[0] * sw[0]) * inv1);
+    put_f(out + b_sc, 2, (act_scale[1] * sw[1]) * inv2);
+    put_f(out + b_sc, 3, act_scale[2] * sw[2]);
+    for (int n = 0; n < H; ++n) {
+      put_f(out + b_b1, n, b1[n] * inv1);
+      put_f(out + b_b2, n, b2[n] * inv2);
+    }
+    for (int n = 0; n < 3; ++n) put_f(out + b_b3, n, b3[n]);
+    if (weight_scales_out)
+      for (int l = 0; l < 3; ++l) weight_scales_out[l] = sw[l];
+    return 0;
+  }
   for (int n = 0; n < H; ++n) {
     for (int k = 0; k < 14; ++k) put_h(out + B_L1, H, n, k, W1[n * 14 + k]);
     put_h(out + B_L1, H, n, 14, b1[n]);
@@ -177,12 +273,16 @@ __device__ __forceinline__ QueryIn load_query(const QueryPtrs& q, int64_t i) {
   return x;
 }
 
-template <int H, bool FRAME, bool F16P>
+// P8: the decoder in E4M3 (kind::f8f6f4) instead of FP16.
+template <int H, bool FRAME, bool F16P, bool P8>
 __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
   using Lay = TcLayout<H, FRAME>;
+  using Lay8 = TcLayout8<H, FRAME>;
+  constexpr int BLOB = P8 ? Lay8::BLOB : Lay::BLOB;
+  constexpr int BLOB_ALIGNED = P8 ? Lay8::BLOB_ALIGNED : Lay::BLOB_ALIGNED;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* sW = smem;
-  uint8_t* sA = smem + Lay::BLOB_ALIGNED;
+  uint8_t* sA = smem + BLOB_ALIGNED;
   uint64_t* bars = reinterpret_cast<uint64_t*>(sA + Lay::A_BYTES);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
 
@@ -192,6 +292,8 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
   const uint32_t aW = ptx::smem_u32(sW);
   const uint32_t aA = ptx::smem_u32(sA);
   const uint32_t aConst = aA + Lay::KB * 2048;  // (1, 0, ...) | 0 blocks
+  const uint32_t aZero = aConst + 2048;
+  const float* sc8 = reinterpret_cast<const float*>(sW + Lay8::B_SC);  // P8: inv_s0, c0, c1, c2
 
   if (tid == 0) {
     ptx::mbar_init(bar_w, 1);
@@ -225,6 +327,8 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
 
   constexpr uint32_t ID_16 = ptx::idesc_f16(128, 16);
   constexpr uint32_t ID_H = ptx::idesc_f16(128, H);
+  constexpr uint32_t ID8_16 = ptx::idesc_e4m3(128, 16);
+  constexpr uint32_t ID8_H = ptx::idesc_e4m3(128, H);
 
   // make this thread's A-operand writes visible to the tensor core, sync the
   // CTA, let one thread issue `issue`, wait for completion.  Returns false
@@ -269,8 +373,8 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
       pyr = L.chunks ? L.mats.pyramid[ci.mat] : L.pyr0;
       if (tid == 0) {
         ptx::fence_proxy_async();
-        ptx::mbar_arrive_expect_tx(bar_w, Lay::BLOB);
-        ptx::bulk_g2s(aW, wsrc, Lay::BLOB, bar_w);
+        ptx::mbar_arrive_expect_tx(bar_w, BLOB);
+        ptx::bulk_g2s(aW, wsrc, BLOB, bar_w);
       }
       w_pending = true;
       bad |= !ptx::mbar_wait(bar_w, ph_w, L.timeout_ns);
@@ -290,8 +394,20 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
       fetch_latent<F16P>(L.pyr, pyr, qc.u, qc.v, qc.lod, qc.xi, z);
     }
     taps_ready = false;
-    const uint32_t z01 = ptx::pack_h2(z[0], z[1]), z23 = ptx::pack_h2(z[2], z[3]);
-    const uint32_t z45 = ptx::pack_h2(z[4], z[5]), z67 = ptx::pack_h2(z[6], z[7]);
+    // the decoder's copy of z, packed now so that only 2 or 4 registers live
+    // through the frame stages: FP16 pairs, or E4M3(z / s_0) quadruples
+    uint32_t zp[4];
+    if (P8) {
+      const float inv0 = sc8[0];
+      zp[0] = ptx::pack_e4m3x2(z[0] * inv0, z[1] * inv0) | (ptx::pack_e4m3x2(z[2] * inv0, z[3] * inv0) << 16);
+      zp[1] = ptx::pack_e4m3x2(z[4] * inv0, z[5] * inv0) | (ptx::pack_e4m3x2(z[6] * inv0, z[7] * inv0) << 16);
+      zp[2] = zp[3] = 0;
+    } else {
+      zp[0] = ptx::pack_h2(z[0], z[1]);
+      zp[1] = ptx::pack_h2(z[2], z[3]);
+      zp[2] = ptx::pack_h2(z[4], z[5]);
+      zp[3] = ptx::pack_h2(z[6], z[7]);
+    }
 
     float xl[6];
     if (FRAME) {
@@ -348,14 +464,28 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
     }
 
     // ---- 4. decoder ---------------------------------------------------------
-    // L1 operand: block 0 = z (fp16), block 1 = (wi', wo', 1, 0)
-    ptx::st_shared_v4(aA + 0 * 2048 + r * 16, z01, z23, z45, z67);
-    ptx::st_shared_v4(aA + 1 * 2048 + r * 16, ptx::pack_h2(xl[0], xl[1]), ptx::pack_h2(xl[2], xl[3]),
-                      ptx::pack_h2(xl[4], xl[5]), 0x00003C00u);
-    if (!mma_stage([&] {
-          ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_L1, H * 16, 128), ID_H, 0);
-        }))
-      break;
+    if (P8) {
+      // L1 operand: block 0 = E4M3(x / s_0) for x = (z, wi', wo'), two zero
+      // codes; the second K block of the MMA is the constant zero block
+      const float inv0 = sc8[0];
+      const uint32_t w2 =
+          ptx::pack_e4m3x2(xl[0] * inv0, xl[1] * inv0) | (ptx::pack_e4m3x2(xl[2] * inv0, xl[3] * inv0) << 16);
+      const uint32_t w3 = ptx::pack_e4m3x2(xl[4] * inv0, xl[5] * inv0);
+      ptx::st_shared_v4(aA + r * 16, zp[0], zp[1], w2, w3);
+      if (!mma_stage([&] {
+            ptx::mma_f8(tmem, ptx::sdesc(aA, aZero - aA, 128), ptx::sdesc(aW + Lay8::B_L1, H * 16, 128), ID8_H, 0);
+          }))
+        break;
+    } else {
+      // L1 operand: block 0 = z (fp16), block 1 = (wi', wo', 1, 0)
+      ptx::st_shared_v4(aA + 0 * 2048 + r * 16, zp[0], zp[1], zp[2], zp[3]);
+      ptx::st_shared_v4(aA + 1 * 2048 + r * 16, ptx::pack_h2(xl[0], xl[1]), ptx::pack_h2(xl[2], xl[3]),
+                        ptx::pack_h2(xl[4], xl[5]), 0x00003C00u);
+      if (!mma_stage([&] {
+            ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_L1, H * 16, 128), ID_H, 0);
+          }))
+        break;
+    }
 
     // texels of the next tile start loading now, under the hidden layers
     if (F16P && c + 1 < c_end && cn.mat == ci.mat) {
@@ -364,44 +494,79 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
     }
 
     // hidden -> hidden and hidden -> out share the epilogue: TMEM row ->
-    // ReLU -> FP16 -> A blocks [0, H/8)
+    // ReLU -> FP16 (or scaled E4M3) -> A blocks
     bool ok = true;
 #pragma unroll
     for (int layer = 0; layer < 2; ++layer) {
+      constexpr int NC = H < 32 ? H : 32;
 #pragma unroll
-      for (int c0 = 0; c0 < H; c0 += (H < 32 ? H : 32)) {
-        constexpr int NC = H < 32 ? H : 32;
-        uint32_t pk[NC / 2];
-        if (NC == 32) {
-          uint32_t acc[32];
+      for (int c0 = 0; c0 < H; c0 += NC) {
+        uint32_t acc[NC];
+        if constexpr (NC == 32) {
           ptx::tmem_ld32(tlane + c0, acc);
-          ptx::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 16; ++j) pk[j] = ptx::pack_h2_relu(u2f(acc[2 * j]), u2f(acc[2 * j + 1]));
         } else {
-          uint32_t acc[16];
           ptx::tmem_ld16(tlane + c0, acc);
-          ptx::tmem_ld_wait();
-#pragma unroll
-          for (int j = 0; j < 8; ++j) pk[j] = ptx::pack_h2_relu(u2f(acc[2 * j]), u2f(acc[2 * j + 1]));
         }
+        ptx::tmem_ld_wait();
+        if (P8) {
+          // code = E4M3(relu(D c_l + b'_l)), four codes per 32-bit word
+          const float cl = sc8[1 + layer];
+          const float2 c2v = make_float2(cl, cl);
+          const float4* bq = reinterpret_cast<const float4*>(sW + (layer == 0 ? Lay8::B_B1 : Lay8::B_B2)) + c0 / 4;
+          uint32_t pk[NC / 4];
 #pragma unroll
-        for (int b = 0; b < NC / 8; ++b)
-          ptx::st_shared_v4(aA + (c0 / 8 + b) * 2048 + r * 16, pk[4 * b], pk[4 * b + 1], pk[4 * b + 2],
-                            pk[4 * b + 3]);
+          for (int j = 0; j < NC / 4; ++j) {
+            const float4 b = bq[j];
+            const float2 q01 = ptx::fma2(make_float2(u2f(acc[4 * j]), u2f(acc[4 * j + 1])), c2v, make_float2(b.x, b.y));
+            const float2 q23 =
+                ptx::fma2(make_float2(u2f(acc[4 * j + 2]), u2f(acc[4 * j + 3])), c2v, make_float2(b.z, b.w));
+            pk[j] = ptx::pack_e4m3x2_relu(q01.x, q01.y) | (ptx::pack_e4m3x2_relu(q23.x, q23.y) << 16);
+          }
+#pragma unroll
+          for (int b = 0; b < NC / 16; ++b)
+            ptx::st_shared_v4(aA + (c0 / 16 + b) * 2048 + r * 16, pk[4 * b], pk[4 * b + 1], pk[4 * b + 2],
+                              pk[4 * b + 3]);
+        } else {
+          uint32_t pk[NC / 2];
+#pragma unroll
+          for (int j = 0; j < NC / 2; ++j) pk[j] = ptx::pack_h2_relu(u2f(acc[2 * j]), u2f(acc[2 * j + 1]));
+#pragma unroll
+          for (int b = 0; b < NC / 8; ++b)
+            ptx::st_shared_v4(aA + (c0 / 8 + b) * 2048 + r * 16, pk[4 * b], pk[4 * b + 1], pk[4 * b + 2],
+                              pk[4 * b + 3]);
+        }
       }
-      const int boff = layer == 0 ? Lay::B_L2 : Lay::B_LO;
-      const int nrows = layer == 0 ? H : 16;
-      const uint32_t id = layer == 0 ? ID_H : ID_16;
-      if (!mma_stage([&] {
+      bool staged;
+      if (P8) {
+        const int boff = layer == 0 ? Lay8::B_L2 : Lay8::B_LO;
+        const int nrows = layer == 0 ? H : 16;
+        const uint32_t id = layer == 0 ? ID8_H : ID8_16;
+        staged = mma_stage([&] {
+          // K steps of 32 codes = two 16-code blocks; an odd last block pairs
+          // with the constant zero block
 #pragma unroll
-            for (int s2 = 0; s2 < H / 16; ++s2)
-              ptx::mma_f16(tmem, ptx::sdesc(aA + s2 * 4096, 2048, 128),
-                           ptx::sdesc(aW + boff + s2 * 2 * nrows * 16, nrows * 16, 128), id, s2 > 0 ? 1u : 0u);
-            // bias step: A constant blocks x B blocks (H/8, H/8+1)
-            ptx::mma_f16(tmem, ptx::sdesc(aConst, 2048, 128),
-                         ptx::sdesc(aW + boff + (H / 8) * nrows * 16, nrows * 16, 128), id, 1u);
-          })) {
+          for (int s2 = 0; s2 < (H + 31) / 32; ++s2) {
+            const uint32_t a0 = aA + s2 * 4096;
+            const uint32_t lbo = (2 * s2 + 1 < H / 16) ? 2048u : (aZero - a0);
+            ptx::mma_f8(tmem, ptx::sdesc(a0, lbo, 128), ptx::sdesc(aW + boff + s2 * 2 * nrows * 16, nrows * 16, 128),
+                        id, s2 > 0 ? 1u : 0u);
+          }
+        });
+      } else {
+        const int boff = layer == 0 ? Lay::B_L2 : Lay::B_LO;
+        const int nrows = layer == 0 ? H : 16;
+        const uint32_t id = layer == 0 ? ID_H : ID_16;
+        staged = mma_stage([&] {
+#pragma unroll
+          for (int s2 = 0; s2 < H / 16; ++s2)
+            ptx::mma_f16(tmem, ptx::sdesc(aA + s2 * 4096, 2048, 128),
+                         ptx::sdesc(aW + boff + s2 * 2 * nrows * 16, nrows * 16, 128), id, s2 > 0 ? 1u : 0u);
+          // bias step: A constant blocks x B blocks (H/8, H/8+1)
+          ptx::mma_f16(tmem, ptx::sdesc(aConst, 2048, 128),
+                       ptx::sdesc(aW + boff + (H / 8) * nrows * 16, nrows * 16, 128), id, 1u);
+        });
+      }
+      if (!staged) {
         ok = false;
         break;
       }
@@ -414,6 +579,13 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
       ptx::tmem_ld4(tlane, acc);
       ptx::tmem_ld_wait();
       float y0 = u2f(acc[0]), y1 = u2f(acc[1]), y2 = u2f(acc[2]);
+      if (P8) {
+        const float c2 = sc8[3];
+        const float* b3 = reinterpret_cast<const float*>(sW + Lay8::B_B3);
+        y0 = fmaf(y0, c2, b3[0]);
+        y1 = fmaf(y1, c2, b3[1]);
+        y2 = fmaf(y2, c2, b3[2]);
+      }
       if (cosine) {
         const float cz = fmaxf(qc.wiz, 0.0f);
         y0 *= cz; y1 *= cz; y2 *= cz;
@@ -446,37 +618,44 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
 // ---------------------------------------------------------------------------
 // host launch
 // ---------------------------------------------------------------------------
-template <int H, bool FRAME, bool F16P>
+template <int H, bool FRAME, bool F16P, bool P8>
 static int launch_tc_one(const LaunchCommon& L, cudaStream_t s) {
-  using Lay = TcLayout<H, FRAME>;
-  auto k = eval_tc_kernel<H, FRAME, F16P>;
+  constexpr int SMEM = P8 ? TcLayout8<H, FRAME>::SMEM : TcLayout<H, FRAME>::SMEM;
+  auto k = eval_tc_kernel<H, FRAME, F16P, P8>;
   static int occ = -1;
   if (occ < 0) {
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Lay::SMEM);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     // TMEM: 512 columns per SM, 64 per CTA -> at most 8 resident CTAs
-    occ = blocks_per_sm((const void*)k, 128, Lay::SMEM, 8, true);
+    occ = blocks_per_sm((const void*)k, 128, SMEM, 8, true);
   }
   const int64_t nchunks = L.chunks ? (int64_t)L.n_chunks : (L.n + 127) / 128;
   if (nchunks == 0) return 0;
   int64_t cap = (int64_t)occ * L.num_sms;
   int grid = (int)(nchunks < cap ? nchunks : cap);
-  k<<<grid, 128, Lay::SMEM, s>>>(L);
+  k<<<grid, 128, SMEM, s>>>(L);
   return (int)cudaGetLastError();
 }
 
-template <int H>
+template <int H, bool P8>
 static int tc_dispatch(const LaunchCommon& L, cudaStream_t s) {
   if (L.shape.frame)
-    return L.pyr.f16 ? launch_tc_one<H, true, true>(L, s) : launch_tc_one<H, true, false>(L, s);
-  return L.pyr.f16 ? launch_tc_one<H, false, true>(L, s) : launch_tc_one<H, false, false>(L, s);
+    return L.pyr.f16 ? launch_tc_one<H, true, true, P8>(L, s) : launch_tc_one<H, true, false, P8>(L, s);
+  return L.pyr.f16 ? launch_tc_one<H, false, true, P8>(L, s) : launch_tc_one<H, false, false, P8>(L, s);
+}
+
+template <bool P8>
+static int tc_dispatch_h(const LaunchCommon& L, cudaStream_t s) {
+  if (L.shape.H == 16) return tc_dispatch<16, P8>(L, s);
+  if (L.shape.H == 32) return tc_dispatch<32, P8>(L, s);
+  if (L.shape.H == 64) return tc_dispatch<64, P8>(L, s);
+  return (int)cudaErrorInvalidValue;
 }
 
 int launch_eval_tc(const LaunchCommon& L, int precision, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (precision != NAM_PREC_F16 || L.shape.NH != 2) return (int)cudaErrorInvalidValue;
-  if (L.shape.H == 16) return tc_dispatch<16>(L, s);
-  if (L.shape.H == 32) return tc_dispatch<32>(L, s);
-  if (L.shape.H == 64) return tc_dispatch<64>(L, s);
+  if (L.shape.NH != 2) return (int)cudaErrorInvalidValue;
+  if (precision == NAM_PREC_F16) return tc_dispatch_h<false>(L, s);
+  if (precision == NAM_PREC_FP8) return tc_dispatch_h<true>(L, s);
   return (int)cudaErrorInvalidValue;
 }
 

@@ -70,6 +70,9 @@ struct LaunchCommon {
   int* err;
   uint64_t timeout_ns;
   int num_sms;
+  float* amax;           // FP32 kernel only: if set, max |input| of each decoder
+                         // layer over the batch (atomic max, starts at 0);
+                         // rgb may then be null
 };
 
 // Resident blocks per SM of a kernel: the occupancy API, or (resources_only,

@@ -214,10 +214,16 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
 }
 // Two FP32 values -> packed E4M3 pair in the low 16 bits (first value in the
 // low byte), round to nearest even, saturating.
-__device__ __forceinline__ uint16_t pack_e4m3x2(float lo, float hi) {
+__device__ __forceinline__ uint32_t pack_e4m3x2(float lo, float hi) {
   uint16_t d;
   asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
-  return d;
+  return (uint32_t)d;
+}
+// Same with ReLU applied by the conversion.
+__device__ __forceinline__ uint32_t pack_e4m3x2_relu(float lo, float hi) {
+  uint16_t d;
+  asm("cvt.rn.satfinite.relu.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
+  return (uint32_t)d;
 }
 __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)

@@ -342,6 +342,16 @@ def workload(i: int, scale: float = 1.0):
     raise ValueError(f"workload {i}")
 
 
+def calibration_queries(i: int, n_side: int = 256):
+    """A calibration batch for static FP8 activation scales: n_side^2 (65,536)
+    queries of workload i's kind (warp frame for 2 and 3, uniform otherwise)
+    drawn from seed + 1000, so that it is disjoint from the evaluated batch."""
+    r = rng_streams(SEEDS[i] + 1000, 1)[0]
+    if i in (2, 3):
+        return warp_queries(r, n_side, n_side, 2048, 2048)
+    return uniform_queries(r, n_side * n_side, {1: 8.0, 4: 10.0}[i])
+
+
 def target_rgb(target: ProceduralBRDF, q) -> np.ndarray:
     """[n, 3] float32 procedural BRDF values at the queries' uv and directions."""
     wi = np.stack([q["wix"], q["wiy"], q["wiz"]]).astype(np.float64)
