@@ -1,22 +1,26 @@
 // Tensor-core evaluation of the neural BRDF on sm_103a (tcgen05 + TMEM).
 //
-// One CTA of 128 threads owns a tile of up to 128 queries at a time; thread r
-// is query r of the tile and TMEM lane r.  Per tile:
+// One CTA per SM with five warpgroups; each warpgroup owns a tile of up to
+// 128 queries at a time (thread r = query r = TMEM lane r) and runs it
+// through the whole path on its own TMEM columns, weight copy and mbarriers:
 //   1. coalesced planar query loads, latent fetch (16-byte texel gathers,
 //      FP32 filter) -> z                                     (Sec. 4.1)
 //   2. frame MLP 8 -> 16 -> 6 on the tensor core with each FP16 operand
 //      split into a high and a low half (z = z_hi + z_lo), so the frame has
-//      FP32 accuracy; FP32 bias + ReLU between the layers    (Sec. 4.2)
+//      FP32 accuracy; ReLU between the layers                 (Sec. 4.2)
 //   3. frame build (Gram-Schmidt, b = n x t) and the direction transform in
 //      FP32 registers: each thread holds its own query's TMEM row, so the
 //      six frame outputs need no cross-lane exchange          (Eq. 4)
-//   4. decoder layers 14 -> H -> H -> 3: FP16 operands, FP32 accumulation in
-//      TMEM; the bias rides in the MMA as a constant-1 input column; ReLU and
-//      the FP16 rounding of the next layer's operand are one cvt.relu.f16x2
+//   4. decoder layers 14 -> H -> H -> 3: FP16 operands (or E4M3 with
+//      per-layer scales), FP32 accumulation in TMEM; FP16 biases ride in the
+//      MMA as the weight of a constant-1 input
 //   5. RGB store (x max(0, wi.z) if requested)
-// MLP weights (and the frame biases) are staged once per CTA, or again when a
-// multi-material launch switches material, with one bulk TMA copy of a blob
-// that the host laid out in the MMA operand order at material creation.
+// The FP16 A operands are written to TMEM (tcgen05.st) and read by the MMA
+// from there, so shared memory holds little more than the weights, and most
+// of the SM's L1/shared storage caches the texel gathers.  MLP weights are
+// staged per warpgroup, again when a multi-material launch switches
+// material, with one bulk TMA copy of a blob that the host laid out in the
+// MMA operand order at material creation.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -41,10 +45,6 @@ __host__ __device__ constexpr int kmajor_off(int R, int row, int k) {
 
 template <int H, bool FRAME>
 struct TcLayout {
-  // A operand blocks (128 rows x 8 fp16 each): data blocks [0, KB), then a
-  // block whose first column is 1.0 (bias input) and an all-zero block.
-  static constexpr int KB = (H / 8) > 4 ? (H / 8) : 4;
-  static constexpr int A_BYTES = (KB + 2) * 2048;
   // weight blob: every bias rides in the MMA as the weight of the constant-1
   // input column (one extra K step of 16)
   static constexpr int B_F1 = 0;                          // 16 x 32: [Wf1 | Wf1 | bf1 0..]
@@ -53,8 +53,6 @@ struct TcLayout {
   static constexpr int B_L2 = B_L1 + H * 16 * 2;          // H x (H + 16)
   static constexpr int B_LO = B_L2 + H * (H + 16) * 2;    // 16 x (H + 16)
   static constexpr int BLOB = B_LO + 16 * (H + 16) * 2;
-  static constexpr int BLOB_ALIGNED = (BLOB + 127) / 128 * 128;
-  static constexpr int SMEM = BLOB_ALIGNED + A_BYTES + 64;
 };
 
 // FP8 (E4M3) decoder: the A region and the frame blocks are those of the FP16
@@ -77,8 +75,6 @@ struct TcLayout8 {
   static constexpr int B_B2 = B_B1 + H * 4;               // FP32 b'_1 [H]
   static constexpr int B_B3 = B_B2 + H * 4;               // FP32 b_2 [4]
   static constexpr int BLOB = B_B3 + 16;
-  static constexpr int BLOB_ALIGNED = (BLOB + 127) / 128 * 128;
-  static constexpr int SMEM = BLOB_ALIGNED + TcLayout<H, FRAME>::A_BYTES + 64;
 };
 
 template <int H, bool FRAME>
@@ -273,45 +269,84 @@ __device__ __forceinline__ QueryIn load_query(const QueryPtrs& q, int64_t i) {
   return x;
 }
 
-// P8: the decoder in E4M3 (kind::f8f6f4) instead of FP16.
-template <int H, bool FRAME, bool F16P, bool P8>
-__global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
+// Shared memory of one CTA: a constant block (1.0 in column 0 of every row)
+// and a zero block, shared by the warpgroups; then one slot per warpgroup:
+// its copy of the weight blob, for FP8 its A blocks (E4M3 codes, plus a zero
+// block), and its two mbarriers.  The FP16 operands of every MMA that is not
+// a bias step live in TMEM instead of shared memory, which leaves most of the
+// SM's 256 KB of L1/shared storage to the L1 cache that serves the texel
+// gathers.
+template <int H, bool FRAME, bool P8>
+struct WgSlot {
+  static constexpr int BLOB = P8 ? TcLayout8<H, FRAME>::BLOB : TcLayout<H, FRAME>::BLOB;
+  static constexpr int BLOB_AL = (BLOB + 127) / 128 * 128;
+  static constexpr int A8_BLOCKS = P8 ? ((H / 16) > 1 ? (H / 16) : 1) : 0;  // E4M3 A blocks
+  static constexpr int A8_BYTES = P8 ? (A8_BLOCKS + 1) * 2048 : 0;          // + zero block
+  static constexpr int BYTES = BLOB_AL + A8_BYTES + 128;                     // + mbarriers
+};
+template <int H, bool FRAME, bool P8, int NWG>
+__host__ __device__ constexpr int smem_bytes() {
+  return 4096 + NWG * WgSlot<H, FRAME, P8>::BYTES + 16;
+}
+
+// TMEM columns of one warpgroup: FP32 accumulator [0, 64), FP16 A operand
+// [64, 96) (two values per column, row = query).
+constexpr int kTmemPerWg = 96;
+
+// Warpgroups per CTA (one CTA per SM): 640 threads at <= 96 registers.  Five
+// warpgroups without register prefetch of the next tile's texels measured
+// faster than four with it (the gathers then hit a larger L1).
+constexpr int kNwg = 5;
+
+// One CTA per SM with NWG warpgroups; each warpgroup runs the whole path on
+// its own tiles of 128 queries (thread r = query r = TMEM lane r), with its
+// own TMEM columns, weight copy and mbarriers, so warpgroups never wait for
+// each other.  P8: the decoder in E4M3 (kind::f8f6f4) instead of FP16.
+template <int H, bool FRAME, bool F16P, bool P8, int NWG>
+__global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommon L) {
   using Lay = TcLayout<H, FRAME>;
   using Lay8 = TcLayout8<H, FRAME>;
-  constexpr int BLOB = P8 ? Lay8::BLOB : Lay::BLOB;
-  constexpr int BLOB_ALIGNED = P8 ? Lay8::BLOB_ALIGNED : Lay::BLOB_ALIGNED;
+  using S = WgSlot<H, FRAME, P8>;
+  constexpr int BLOB = S::BLOB;
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sW = smem;
-  uint8_t* sA = smem + BLOB_ALIGNED;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + Lay::A_BYTES);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
 
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, wg = tid >> 7, r = tid & 127, warp = tid >> 5;
+  const uint32_t aConst = ptx::smem_u32(smem);
+  const uint32_t aZero = aConst + 2048;
+  uint8_t* sW = smem + 4096 + wg * S::BYTES;
+  const uint32_t aW = ptx::smem_u32(sW);
+  const uint32_t aA8 = aW + S::BLOB_AL;                 // P8: E4M3 A blocks
+  const uint32_t aZ8 = aA8 + S::A8_BLOCKS * 2048;       // P8: this slot's zero block
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sW + S::BLOB_AL + S::A8_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + 4096 + NWG * S::BYTES);
   const uint32_t bar_w = ptx::smem_u32(&bars[0]);
   const uint32_t bar_m = ptx::smem_u32(&bars[1]);
-  const uint32_t aW = ptx::smem_u32(sW);
-  const uint32_t aA = ptx::smem_u32(sA);
-  const uint32_t aConst = aA + Lay::KB * 2048;  // (1, 0, ...) | 0 blocks
-  const uint32_t aZero = aConst + 2048;
   const float* sc8 = reinterpret_cast<const float*>(sW + Lay8::B_SC);  // P8: inv_s0, c0, c1, c2
+  const uint32_t bar_id = 1 + wg;                       // named barrier of this warpgroup
 
-  if (tid == 0) {
+  if (r == 0) {
     ptx::mbar_init(bar_w, 1);
     ptx::mbar_init(bar_m, 1);
     ptx::fence_mbar_init();
   }
   if (warp == 0) {
-    ptx::tmem_alloc(ptx::smem_u32(tslot), 64);
+    ptx::tmem_alloc(ptx::smem_u32(tslot), 512);
     ptx::tmem_relinquish();
   }
-  ptx::st_shared_v4(aConst + tid * 16, 0x3C00u, 0u, 0u, 0u);
-  ptx::st_shared_v4(aConst + 2048 + tid * 16, 0u, 0u, 0u, 0u);
+  if (tid < 128) {
+    ptx::st_shared_v4(aConst + tid * 16, 0x3C00u, 0u, 0u, 0u);
+    ptx::st_shared_v4(aZero + tid * 16, 0u, 0u, 0u, 0u);
+  }
+  if (P8) ptx::st_shared_v4(aZ8 + r * 16, 0u, 0u, 0u, 0u);
   ptx::fence_proxy_async();
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
   const uint32_t tmem = *tslot;
-  const uint32_t tlane = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t lane = (uint32_t)((warp & 3) * 32) << 16;
+  const uint32_t tD = tmem + wg * kTmemPerWg;           // accumulator (MMA address: lane 0)
+  const uint32_t tA = tD + 64;                          // FP16 A operand
+  const uint32_t tDl = tD + lane, tAl = tA + lane;      // this warp's rows
 
   const int64_t nchunks = L.chunks ? (int64_t)L.n_chunks : (L.n + 127) / 128;
   const int64_t per = (nchunks + gridDim.x - 1) / gridDim.x;
@@ -323,21 +358,21 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
   int cur_mat = -1;
   const void* pyr = L.pyr0;
   const bool cosine = (L.flags & NAM_OUT_COSINE) != 0;
-  const int r = tid;
 
   constexpr uint32_t ID_16 = ptx::idesc_f16(128, 16);
   constexpr uint32_t ID_H = ptx::idesc_f16(128, H);
   constexpr uint32_t ID8_16 = ptx::idesc_e4m3(128, 16);
   constexpr uint32_t ID8_H = ptx::idesc_e4m3(128, H);
 
-  // make this thread's A-operand writes visible to the tensor core, sync the
-  // CTA, let one thread issue `issue`, wait for completion.  Returns false
-  // (for every thread) if any thread's wait ran out.
+  // make this thread's operand writes (shared memory and TMEM) visible to the
+  // tensor core, sync the warpgroup, let one thread issue `issue`, wait for
+  // completion.  Returns false (for every thread of the warpgroup) if any
+  // thread's wait ran out.
   auto mma_stage = [&](auto issue) -> bool {
-    ptx::fence_proxy_async();
+    if (P8) ptx::fence_proxy_async();
     ptx::tc_fence_before();
-    if (__syncthreads_or(bad)) return false;
-    if (tid == 0) {
+    if (ptx::bar_red_or(bar_id, 128, bad)) return false;
+    if (r == 0) {
       ptx::tc_fence_after();
       issue();
       ptx::mma_commit(bar_m);
@@ -352,26 +387,26 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
 
   ChunkIn ci{};
   QueryIn qc{};
-  Taps8 tc{};  // texels of the current tile (FP16 pyramids), loaded a tile ahead
-  if (c_begin < c_end) {
-    ci = chunk_at(L, c_begin);
+  int64_t c = c_begin + wg;
+  if (c < c_end) {
+    ci = chunk_at(L, c);
     qc = load_query(L.q, ci.start + (r < ci.count ? r : 0));
   }
-  bool taps_ready = false;
-  for (int64_t c = c_begin; c < c_end; ++c) {
+  for (; c < c_end; c += NWG) {
     // prefetch the next tile's inputs; consumed one iteration later
     ChunkIn cn = ci;
     QueryIn qn = qc;
-    if (c + 1 < c_end) {
-      cn = chunk_at(L, c + 1);
+    const bool has_next = c + NWG < c_end;
+    if (has_next) {
+      cn = chunk_at(L, c + NWG);
       qn = load_query(L.q, cn.start + (r < cn.count ? r : 0));
     }
     if (ci.mat != cur_mat) {
-      // (re)stage the material's weights; no MMA is in flight here
-      if (__syncthreads_or(bad)) break;
+      // (re)stage the material's weights; no MMA of this warpgroup is in flight
+      if (ptx::bar_red_or(bar_id, 128, bad)) break;
       const void* wsrc = L.chunks ? L.mats.weights[ci.mat] : L.w0;
       pyr = L.chunks ? L.mats.pyramid[ci.mat] : L.pyr0;
-      if (tid == 0) {
+      if (r == 0) {
         ptx::fence_proxy_async();
         ptx::mbar_arrive_expect_tx(bar_w, BLOB);
         ptx::bulk_g2s(aW, wsrc, BLOB, bar_w);
@@ -388,12 +423,12 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
     // ---- 1. latent fetch ------------------------------------------------
     float z[8];
     if (F16P) {
-      if (!taps_ready) issue_taps(L.pyr, pyr, qc.u, qc.v, qc.lod, qc.xi, tc);
+      Taps8 tc;
+      issue_taps(L.pyr, pyr, qc.u, qc.v, qc.lod, qc.xi, tc);
       finish_taps(tc, z);
     } else {
       fetch_latent<F16P>(L.pyr, pyr, qc.u, qc.v, qc.lod, qc.xi, z);
     }
-    taps_ready = false;
     // the decoder's copy of z, packed now so that only 2 or 4 registers live
     // through the frame stages: FP16 pairs, or E4M3(z / s_0) quadruples
     uint32_t zp[4];
@@ -413,42 +448,39 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
     if (FRAME) {
       // ---- 2. frame MLP at FP32 accuracy (split FP16 operands) -----------
       {
-        uint32_t lo0, lo1, lo2, lo3, h0, h1, h2, h3;
-        split2(z[0], z[1], h0, lo0);
-        split2(z[2], z[3], h1, lo1);
-        split2(z[4], z[5], h2, lo2);
-        split2(z[6], z[7], h3, lo3);
-        ptx::st_shared_v4(aA + 0 * 2048 + r * 16, h0, h1, h2, h3);
-        ptx::st_shared_v4(aA + 1 * 2048 + r * 16, lo0, lo1, lo2, lo3);
+        uint32_t v[8];
+        split2(z[0], z[1], v[0], v[4]);
+        split2(z[2], z[3], v[1], v[5]);
+        split2(z[4], z[5], v[2], v[6]);
+        split2(z[6], z[7], v[3], v[7]);
+        ptx::tmem_st8(tAl, v);  // A = (z_hi, z_lo)
+        ptx::tmem_st_wait();
       }
       if (!mma_stage([&] {
-            ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_F1, 256, 128), ID_16, 0);
-            ptx::mma_f16(tmem, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + Lay::B_F1 + 512, 256, 128), ID_16, 1);
+            ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + Lay::B_F1, 256, 128), ID_16, 0);
+            ptx::mma_f16(tD, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + Lay::B_F1 + 512, 256, 128), ID_16, 1);
           }))
         break;
       {
         uint32_t acc[16];
-        ptx::tmem_ld16(tlane, acc);
+        ptx::tmem_ld16(tDl, acc);
         ptx::tmem_ld_wait();
-        uint32_t hi[8], lo[8];
+        uint32_t v[16];
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          split2(fmaxf(u2f(acc[2 * j]), 0.0f), fmaxf(u2f(acc[2 * j + 1]), 0.0f), hi[j], lo[j]);
-        ptx::st_shared_v4(aA + 0 * 2048 + r * 16, hi[0], hi[1], hi[2], hi[3]);
-        ptx::st_shared_v4(aA + 1 * 2048 + r * 16, hi[4], hi[5], hi[6], hi[7]);
-        ptx::st_shared_v4(aA + 2 * 2048 + r * 16, lo[0], lo[1], lo[2], lo[3]);
-        ptx::st_shared_v4(aA + 3 * 2048 + r * 16, lo[4], lo[5], lo[6], lo[7]);
+          split2(fmaxf(u2f(acc[2 * j]), 0.0f), fmaxf(u2f(acc[2 * j + 1]), 0.0f), v[j], v[8 + j]);
+        ptx::tmem_st16(tAl, v);  // A = (h_hi, h_lo)
+        ptx::tmem_st_wait();
       }
       if (!mma_stage([&] {
-            ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_F2, 256, 128), ID_16, 0);
-            ptx::mma_f16(tmem, ptx::sdesc(aA + 2 * 2048, 2048, 128), ptx::sdesc(aW + Lay::B_F2 + 512, 256, 128),
-                         ID_16, 1);
-            ptx::mma_f16(tmem, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + Lay::B_F2 + 1024, 256, 128), ID_16, 1);
+            ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + Lay::B_F2, 256, 128), ID_16, 0);
+            ptx::mma_f16_ts(tD, tA + 8, ptx::sdesc(aW + Lay::B_F2 + 512, 256, 128), ID_16, 1);
+            ptx::mma_f16(tD, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + Lay::B_F2 + 1024, 256, 128), ID_16, 1);
           }))
         break;
       {
         uint32_t acc[8];
-        ptx::tmem_ld8(tlane, acc);
+        ptx::tmem_ld8(tDl, acc);
         ptx::tmem_ld_wait();
         float rr[6];
 #pragma unroll
@@ -466,35 +498,28 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
     // ---- 4. decoder ---------------------------------------------------------
     if (P8) {
       // L1 operand: block 0 = E4M3(x / s_0) for x = (z, wi', wo'), two zero
-      // codes; the second K block of the MMA is the constant zero block
+      // codes; the second K block of the MMA is the slot's zero block
       const float inv0 = sc8[0];
       const uint32_t w2 =
           ptx::pack_e4m3x2(xl[0] * inv0, xl[1] * inv0) | (ptx::pack_e4m3x2(xl[2] * inv0, xl[3] * inv0) << 16);
       const uint32_t w3 = ptx::pack_e4m3x2(xl[4] * inv0, xl[5] * inv0);
-      ptx::st_shared_v4(aA + r * 16, zp[0], zp[1], w2, w3);
+      ptx::st_shared_v4(aA8 + r * 16, zp[0], zp[1], w2, w3);
       if (!mma_stage([&] {
-            ptx::mma_f8(tmem, ptx::sdesc(aA, aZero - aA, 128), ptx::sdesc(aW + Lay8::B_L1, H * 16, 128), ID8_H, 0);
+            ptx::mma_f8(tD, ptx::sdesc(aA8, aZ8 - aA8, 128), ptx::sdesc(aW + Lay8::B_L1, H * 16, 128), ID8_H, 0);
           }))
         break;
     } else {
-      // L1 operand: block 0 = z (fp16), block 1 = (wi', wo', 1, 0)
-      ptx::st_shared_v4(aA + 0 * 2048 + r * 16, zp[0], zp[1], zp[2], zp[3]);
-      ptx::st_shared_v4(aA + 1 * 2048 + r * 16, ptx::pack_h2(xl[0], xl[1]), ptx::pack_h2(xl[2], xl[3]),
-                        ptx::pack_h2(xl[4], xl[5]), 0x00003C00u);
-      if (!mma_stage([&] {
-            ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aW + Lay::B_L1, H * 16, 128), ID_H, 0);
-          }))
+      // L1 operand: (z, wi', wo', 1, 0); the 1 meets the bias column of W1
+      uint32_t v[8] = {zp[0], zp[1], zp[2], zp[3], ptx::pack_h2(xl[0], xl[1]), ptx::pack_h2(xl[2], xl[3]),
+                       ptx::pack_h2(xl[4], xl[5]), 0x00003C00u};
+      ptx::tmem_st8(tAl, v);
+      ptx::tmem_st_wait();
+      if (!mma_stage([&] { ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + Lay::B_L1, H * 16, 128), ID_H, 0); }))
         break;
     }
 
-    // texels of the next tile start loading now, under the hidden layers
-    if (F16P && c + 1 < c_end && cn.mat == ci.mat) {
-      issue_taps(L.pyr, pyr, qn.u, qn.v, qn.lod, qn.xi, tc);
-      taps_ready = true;
-    }
-
     // hidden -> hidden and hidden -> out share the epilogue: TMEM row ->
-    // ReLU -> FP16 (or scaled E4M3) -> A blocks
+    // ReLU -> FP16 (or scaled E4M3) -> A operand
     bool ok = true;
 #pragma unroll
     for (int layer = 0; layer < 2; ++layer) {
@@ -503,9 +528,9 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
       for (int c0 = 0; c0 < H; c0 += NC) {
         uint32_t acc[NC];
         if constexpr (NC == 32) {
-          ptx::tmem_ld32(tlane + c0, acc);
+          ptx::tmem_ld32(tDl + c0, acc);
         } else {
-          ptx::tmem_ld16(tlane + c0, acc);
+          ptx::tmem_ld16(tDl + c0, acc);
         }
         ptx::tmem_ld_wait();
         if (P8) {
@@ -524,18 +549,20 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
           }
 #pragma unroll
           for (int b = 0; b < NC / 16; ++b)
-            ptx::st_shared_v4(aA + (c0 / 16 + b) * 2048 + r * 16, pk[4 * b], pk[4 * b + 1], pk[4 * b + 2],
+            ptx::st_shared_v4(aA8 + (c0 / 16 + b) * 2048 + r * 16, pk[4 * b], pk[4 * b + 1], pk[4 * b + 2],
                               pk[4 * b + 3]);
         } else {
           uint32_t pk[NC / 2];
 #pragma unroll
           for (int j = 0; j < NC / 2; ++j) pk[j] = ptx::pack_h2_relu(u2f(acc[2 * j]), u2f(acc[2 * j + 1]));
-#pragma unroll
-          for (int b = 0; b < NC / 8; ++b)
-            ptx::st_shared_v4(aA + (c0 / 8 + b) * 2048 + r * 16, pk[4 * b], pk[4 * b + 1], pk[4 * b + 2],
-                              pk[4 * b + 3]);
+          if constexpr (NC == 32) {
+            ptx::tmem_st16(tAl + c0 / 2, pk);
+          } else {
+            ptx::tmem_st8(tAl + c0 / 2, pk);
+          }
         }
       }
+      if (!P8) ptx::tmem_st_wait();
       bool staged;
       if (P8) {
         const int boff = layer == 0 ? Lay8::B_L2 : Lay8::B_LO;
@@ -543,12 +570,12 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
         const uint32_t id = layer == 0 ? ID8_H : ID8_16;
         staged = mma_stage([&] {
           // K steps of 32 codes = two 16-code blocks; an odd last block pairs
-          // with the constant zero block
+          // with the zero block
 #pragma unroll
           for (int s2 = 0; s2 < (H + 31) / 32; ++s2) {
-            const uint32_t a0 = aA + s2 * 4096;
-            const uint32_t lbo = (2 * s2 + 1 < H / 16) ? 2048u : (aZero - a0);
-            ptx::mma_f8(tmem, ptx::sdesc(a0, lbo, 128), ptx::sdesc(aW + boff + s2 * 2 * nrows * 16, nrows * 16, 128),
+            const uint32_t a0 = aA8 + s2 * 4096;
+            const uint32_t lbo = (2 * s2 + 1 < H / 16) ? 2048u : (aZ8 - a0);
+            ptx::mma_f8(tD, ptx::sdesc(a0, lbo, 128), ptx::sdesc(aW + boff + s2 * 2 * nrows * 16, nrows * 16, 128),
                         id, s2 > 0 ? 1u : 0u);
           }
         });
@@ -559,10 +586,10 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
         staged = mma_stage([&] {
 #pragma unroll
           for (int s2 = 0; s2 < H / 16; ++s2)
-            ptx::mma_f16(tmem, ptx::sdesc(aA + s2 * 4096, 2048, 128),
-                         ptx::sdesc(aW + boff + s2 * 2 * nrows * 16, nrows * 16, 128), id, s2 > 0 ? 1u : 0u);
-          // bias step: A constant blocks x B blocks (H/8, H/8+1)
-          ptx::mma_f16(tmem, ptx::sdesc(aConst, 2048, 128),
+            ptx::mma_f16_ts(tD, tA + 8 * s2, ptx::sdesc(aW + boff + s2 * 2 * nrows * 16, nrows * 16, 128), id,
+                            s2 > 0 ? 1u : 0u);
+          // bias step: (constant block, zero block) x B blocks (H/8, H/8+1)
+          ptx::mma_f16(tD, ptx::sdesc(aConst, 2048, 128),
                        ptx::sdesc(aW + boff + (H / 8) * nrows * 16, nrows * 16, 128), id, 1u);
         });
       }
@@ -576,7 +603,7 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
     // ---- 5. output ----------------------------------------------------------
     {
       uint32_t acc[4];
-      ptx::tmem_ld4(tlane, acc);
+      ptx::tmem_ld4(tDl, acc);
       ptx::tmem_ld_wait();
       float y0 = u2f(acc[0]), y1 = u2f(acc[1]), y2 = u2f(acc[2]);
       if (P8) {
@@ -602,7 +629,7 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
   }
 
   // ---- teardown: wait (bounded) for copies / MMAs still in flight ----------
-  if (tid == 0) {
+  if (r == 0) {
     if (mma_pending) ptx::mbar_wait(bar_m, ph_m ^ 1, L.timeout_ns);
     if (w_pending) ptx::mbar_wait(bar_w, ph_w ^ 1, L.timeout_ns);
     if (bad) record_error(L.err, DEVERR_WAIT_TIMEOUT);
@@ -611,7 +638,7 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
   __syncthreads();
   if (warp == 0) {
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, 64);
+    ptx::tmem_dealloc(tmem, 512);
   }
 }
 
@@ -620,19 +647,23 @@ __global__ void __launch_bounds__(128, 4) eval_tc_kernel(const LaunchCommon L) {
 // ---------------------------------------------------------------------------
 template <int H, bool FRAME, bool F16P, bool P8>
 static int launch_tc_one(const LaunchCommon& L, cudaStream_t s) {
-  constexpr int SMEM = P8 ? TcLayout8<H, FRAME>::SMEM : TcLayout<H, FRAME>::SMEM;
-  auto k = eval_tc_kernel<H, FRAME, F16P, P8>;
-  static int occ = -1;
-  if (occ < 0) {
+  constexpr int SMEM = smem_bytes<H, FRAME, P8, kNwg>();
+  auto k = eval_tc_kernel<H, FRAME, F16P, P8, kNwg>;
+  static bool configured = false;
+  if (!configured) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    // TMEM: 512 columns per SM, 64 per CTA -> at most 8 resident CTAs
-    occ = blocks_per_sm((const void*)k, 128, SMEM, 8, true);
+    // ask for the smallest shared-memory carveout that holds the CTA: the
+    // rest of the SM's L1/shared storage caches the texel gathers
+    const int pct = (SMEM + 1024) * 100 / (228 * 1024) + 1;
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    configured = true;
   }
   const int64_t nchunks = L.chunks ? (int64_t)L.n_chunks : (L.n + 127) / 128;
   if (nchunks == 0) return 0;
-  int64_t cap = (int64_t)occ * L.num_sms;
-  int grid = (int)(nchunks < cap ? nchunks : cap);
-  k<<<grid, 128, SMEM, s>>>(L);
+  // one CTA per SM (TMEM: kNwg x 96 of 512 columns)
+  const int64_t want = (nchunks + kNwg - 1) / kNwg;
+  const int grid = (int)(want < L.num_sms ? want : L.num_sms);
+  k<<<grid, kNwg * 128, SMEM, s>>>(L);
   return (int)cudaGetLastError();
 }
 
