@@ -51,21 +51,27 @@ def parse():
     ap.add_argument("--serve-frames", type=int, default=720)
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-sweep4k", action="store_true")
+    ap.add_argument("--train-steps", type=int, default=2000)
     return ap.parse_args()
 
 
 # ----------------------------------------------------------------------------
 # distributed plumbing (replicas: no data-path collective)
 # ----------------------------------------------------------------------------
-def dist_setup(args):
+def dist_setup(args, backend=None):
+    """Rank, world size and local GPU from the torchrun environment; one
+    process group per job (NCCL for the GPU arm; gloo where no GPU is used)."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+        backend = backend or ("nccl" if args.impl == "ours" else "gloo")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -398,6 +404,14 @@ def run_ours(args):
         sweep["fp8_speedup_vs_fp32"] = round(ms32 / ms8, 2)
         sweep["fp8_act_scales"] = [float(x) for x in scales]
         mat8.destroy()
+    # ---- precision sweep at 3840x2160 ---------------------------------------
+    sweep4k, outs4k = None, None
+    if not args.no_sweep4k:
+        sweep4k, outs4k = run_sweep_4k(ctx, dev, stream, flush, args)
+    # ---- training: 2,000 Adam steps on the procedural GGX target ------------
+    training = None
+    if args.train_steps > 0 and rank == 0:
+        training = run_training(ctx, dev, stream, args.train_steps)
     # ---- serving stream ---------------------------------------------------
     serving = None
     if not args.no_serve and rank == 0:
@@ -407,7 +421,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and args.cpu_seconds > 0:
         cpu = cpu_baseline(w, out16.cpu().numpy(), args.cpu_seconds,
-                           None if out8 is None else out8.cpu().numpy())
+                           None if out8 is None else out8.cpu().numpy(), outs4k)
 
     mat16.destroy()
     ctx.close()
@@ -425,6 +439,8 @@ def run_ours(args):
             "gpu_launches": args.steps,
             "roofline": roofline,
             "precision_sweep": sweep,
+            "precision_sweep_3840x2160": sweep4k,
+            "training": training,
             "serving": serving,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -434,6 +450,93 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def run_sweep_4k(ctx, dev, stream, flush, args):
+    """The 3840x2160 sweep: same pyramid and MLPs, FP32 / FP16 / FP8 kernels,
+    device-resident queries, L2 flushed before each timed launch.  Returns
+    timings and the three outputs for the error report of cpu_baseline."""
+    import torch
+
+    import workloads as W
+    from paper_2305_02678_gb300 import binding as B
+    w = W.workload(3)
+    q = w["queries"]
+    n = int(q["u"].shape[0])
+    m = w["model"]
+    dq = {k: torch.from_numpy(v).to(dev) for k, v in q.items() if k != "xi"}
+    mat16 = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"], precision=B.NAM_PREC_F16)
+    cq = W.calibration_queries(3)
+    dcq = {k: torch.from_numpy(v).to(dev) for k, v in cq.items() if k != "xi"}
+    scales = B.nam_fp8_calibrate(ctx.h, mat16.h, dcq, len(cq["u"]), stream)[:3]
+    mats = {"fp32": ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"],
+                                 precision=B.NAM_PREC_F32),
+            "fp16": mat16,
+            "fp8": ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"],
+                                precision=B.NAM_PREC_FP8, act_scale=scales)}
+    res, outs = {"workload": "fp16-2048sq-3840x2160", "queries": n, "fp8_act_scales": [float(x) for x in scales]}, {}
+    steps = max(3, args.steps // 2)
+    for name, mat in mats.items():
+        out = torch.empty((n, 3), device=dev)
+        t = time_launches(lambda: B.nam_eval(ctx.h, mat.h, dq, n, out, stream, 0), steps, 2, flush, stream)
+        ms = statistics.fmean(t)
+        res[f"{name}_ms"] = round(ms, 4)
+        res[f"{name}_evals_per_s"] = round(n / (ms * 1e-3), 1)
+        outs[name] = out
+    for name in ("fp16", "fp8"):
+        res[f"{name}_speedup_vs_fp32"] = round(res["fp32_ms"] / res[f"{name}_ms"], 2)
+    k = 1 << 20   # error sample: the first 1,048,576 queries
+    host = {name: o[:k].cpu().numpy() for name, o in outs.items()}
+    for mat in mats.values():
+        mat.destroy()
+    return res, {"w": w, "sample": k, "out": host}
+
+
+def run_training(ctx, dev, stream, steps, batch=262144, pool=8):
+    """Fit a 1024^2 x 8 FP32 latent pyramid (11 levels) with the frame MLP and
+    a 14-64-64-3 decoder to the procedural GGX-over-Lambert target: `steps`
+    fused steps (forward, log-L1 loss, reverse mode with atomic pyramid
+    scatter, Adam) on batches of 262,144 uniform queries, cycling through a
+    pool of `pool` pre-drawn batches resident on the device."""
+    import torch
+
+    import workloads as W
+    from paper_2305_02678_gb300 import binding as B
+    w = W.workload(4)
+    m = w["model"]
+    mat = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"], precision=B.NAM_PREC_F32,
+                       trainable=True)
+    rng = W.rng_streams(W.SEEDS[4] + 7, 1)[0]
+    batches = []
+    for _ in range(pool):
+        q = W.uniform_queries(rng, batch, 10.0)
+        y = torch.from_numpy(W.target_rgb(w["target"], q)).to(dev)
+        batches.append(({k: torch.from_numpy(v).to(dev) for k, v in q.items() if k != "xi"}, y))
+    losses = []
+    for s in range(1, 4):   # warm-up steps are real steps of the same run
+        dq, y = batches[s % pool]
+        losses.append(B.nam_train_step(ctx.h, mat.h, dq, y, batch, step=s, stream=stream))
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for s in range(4, steps + 1):
+        dq, y = batches[s % pool]
+        want = s % 100 == 0 or s == steps
+        l = B.nam_train_step(ctx.h, mat.h, dq, y, batch, step=s, stream=stream, want_loss=want)
+        if want:
+            losses.append(l)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / (steps - 3)
+    mat.destroy()
+    ctx.check()
+    return {"workload": "train-1024sq-262144", "steps": steps, "batch": batch, "ms_per_step": round(ms, 4),
+            "steps_per_s": round(1e3 / ms, 1), "samples_per_s": round(batch * 1e3 / ms, 1),
+            "loss_first": round(losses[0], 5), "loss_last": round(losses[-1], 5),
+            "loss_every_100": [round(x, 5) for x in losses[3:]],
+            "note": "each step: FP32 forward, log-L1 loss, hand-written reverse mode (atomic pyramid scatter), "
+                    "Adam over 11.18 M pyramid + MLP parameters; loss read back every 100 steps"}
 
 
 def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_frames=None):
@@ -473,18 +576,27 @@ def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_
     rng = rngs[2 * n_mat + 1]
     arrivals = np.cumsum(rng.exponential(1.0 / rate, total))
     which = rng.integers(0, len(res), total)
+    # every frame's tile -> material table, built before the stream starts so
+    # that submission keeps up with the arrival times
+    tables = []
+    for i in range(total):
+        tiles = frames[which[i]][3]
+        st = np.array(tiles, dtype=np.int64)
+        arr = np.zeros(len(tiles), dtype=[("start", "<i8"), ("count", "<i4"), ("material", "<i4")])
+        arr["start"], arr["count"], arr["material"] = st[:, 0], st[:, 1], rng.integers(0, n_mat, len(tiles))
+        tables.append(arr)
     keep = []
     tickets = []
+    submitted = []
     t0 = B.nam_now() + 0.05
     for i in range(total):
         n, pinned, out, tiles = frames[which[i]]
-        items = (B.nam_work_item * len(tiles))(*[B.nam_work_item(s, c, int(m)) for (s, c), m in
-                                                 zip(tiles, rng.integers(0, n_mat, len(tiles)))])
+        items = tables[i]
         f = B.nam_frame()
         f.n_queries = n
         f.q = B.make_queries(pinned)
-        f.items = C.addressof(items)
-        f.n_items = len(tiles)
+        f.items = items.ctypes.data
+        f.n_items = len(items)
         f.n_materials = n_mat
         f.materials = C.addressof(mat_arr)
         f.rgb_out = out.data_ptr()
@@ -495,13 +607,14 @@ def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_
         if f.arrival_s > now:
             time.sleep(f.arrival_s - now)
         tickets.append(B.nam_submit(ctx.h, f))
+        submitted.append(B.nam_now())
     failed = 0
     rows = []
     for i, t in enumerate(tickets):
         st, fs = B.nam_wait(ctx.h, t, 60_000_000_000)
         failed += st != 0
         if i >= warmup_frames and st == 0:
-            rows.append((which[i], fs.arrival_s, fs.admit_s, fs.start_s, fs.finish_s, fs.n_queries))
+            rows.append((which[i], fs.arrival_s, fs.admit_s, fs.start_s, fs.finish_s, fs.n_queries, submitted[i]))
     a = np.array(rows, dtype=np.float64)
     lat = (a[:, 4] - a[:, 1]) * 1e3
     span = a[:, 4].max() - a[:, 1].min()
@@ -516,6 +629,11 @@ def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_
     out = {"frames": n_frames, "warmup_frames": warmup_frames, "failed": int(failed), "rate_fps": rate,
            "p50_frame_ms": pct(lat, 50), "p99_frame_ms": pct(lat, 99),
            "queue_ms_p99": pct((a[:, 2] - a[:, 1]) * 1e3, 99), "run_ms_p50": pct((a[:, 4] - a[:, 3]) * 1e3, 50),
+           "run_ms_p99": pct((a[:, 4] - a[:, 3]) * 1e3, 99),
+           "submit_late_ms_p99": pct((a[:, 6] - a[:, 1]) * 1e3, 99),
+           "slowest_frames_ms": [[round(float(x), 3) for x in ((r[6] - r[1]) * 1e3, (r[2] - r[6]) * 1e3,
+                                                            (r[4] - r[3]) * 1e3, (r[4] - r[1]) * 1e3)]
+                                 for r in a[np.argsort(a[:, 4] - a[:, 1])[-5:]]],
            "evals_per_s": round(float(a[:, 5].sum() / span), 1),
            "offered_evals_per_s": round(rate * float(np.mean([r[0] * r[1] for r in res])), 1),
            "by_resolution": by_res, "materials": n_mat, "budget_bytes": budget,
@@ -528,7 +646,7 @@ def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_
     return out
 
 
-def cpu_baseline(w, gpu_out16, seconds, gpu_out8=None):
+def cpu_baseline(w, gpu_out16, seconds, gpu_out8=None, outs4k=None):
     """FP64 oracle (as it stands) on all host cores over a bounded sample of
     the same workload: consecutive queries of the 1080p frame, wrapping
     around, about `seconds` of work; also the GPU FP16 result's error on the
@@ -568,6 +686,20 @@ def cpu_baseline(w, gpu_out16, seconds, gpu_out8=None):
         e8m = O.relative_error(gpu_out8[:c], master)
         fp8 = {"vs_e4m3_weight_oracle_max": e8[0], "vs_e4m3_weight_oracle_mean": e8[1],
                "vs_fp32_master_oracle_max": e8m[0], "vs_fp32_master_oracle_mean": e8m[1]}
+    err4k = None
+    if outs4k is not None:
+        w4, k4 = outs4k["w"], outs4k["sample"]
+        sub4 = W.slice_queries(w4["queries"], 0, k4)
+        master4 = O.eval(O.Model.from_workload(w4), sub4, nthreads=cores)
+        ref = {"fp32": master4, "fp16": O.eval(O.Model.from_workload(w4, params="fp16"), sub4, nthreads=cores),
+               "fp8": O.eval(O.Model.from_workload(w4, params="fp8"), sub4, nthreads=cores)}
+        err4k = {"queries": k4}
+        for name, g in outs4k["out"].items():
+            e = O.relative_error(g, master4)
+            err4k[f"{name}_vs_fp32_master_oracle"] = {"max": e[0], "mean": e[1]}
+            if name != "fp32":
+                e2 = O.relative_error(g, ref[name])
+                err4k[f"{name}_vs_oracle_same_params_unrounded_activations"] = {"max": e2[0], "mean": e2[1]}
     return {"value": round(done / dt, 1), "unit": "evals/s", "cores": cores, "kind": "oracle",
             "sample": f"{done} queries: the 1920x1080 workload's queries in order, wrapping around "
                       f"(FP64, FP16-quantised parameters, {cores} threads)",
@@ -577,7 +709,8 @@ def cpu_baseline(w, gpu_out16, seconds, gpu_out8=None):
                                          "vs_unrounded_oracle_mean": e_exact[1],
                                          "vs_fp32_master_oracle_max": e_master[0],
                                          "vs_fp32_master_oracle_mean": e_master[1]},
-            "gpu_fp8_error_on_sample": fp8}
+            "gpu_fp8_error_on_sample": fp8,
+            "gpu_error_3840x2160_sample": err4k}
 
 
 # ----------------------------------------------------------------------------

@@ -263,13 +263,15 @@ def nam_backward(ctx, mat, q, n, grad_rgb, grad_params, grad_pyramid, stream=Non
 
 
 def nam_train_step(ctx, mat, q, target_rgb, n, lr_params=1e-3, lr_pyramid=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
-                   step=1, stream=None, flags=0):
+                   step=1, stream=None, flags=0, want_loss=True):
+    """One fused training step; returns the batch loss (which synchronises
+    the stream), or None without synchronising if want_loss is False."""
     opt = nam_adam(lr_params, lr_pyramid, beta1, beta2, eps, step)
     loss = C.c_float(0.0)
     qs = make_queries(q)
-    _check(_lib.nam_train_step(ctx, mat, C.byref(qs), ptr(target_rgb), int(n), C.byref(opt), C.byref(loss),
-                               _stream(stream), flags), "nam_train_step")
-    return loss.value
+    _check(_lib.nam_train_step(ctx, mat, C.byref(qs), ptr(target_rgb), int(n), C.byref(opt),
+                               C.byref(loss) if want_loss else None, _stream(stream), flags), "nam_train_step")
+    return loss.value if want_loss else None
 
 
 NAM_NOALLOC_TRAIN_MAX_QUERIES = 65536

@@ -149,6 +149,18 @@ extern "C" nam_status nam_init(nam_ctx** out, const nam_config* cfg) {
     return cuda_fail((int)e, "nam_init: error word");
   }
   cudaMemset(ctx->err_word, 0, sizeof(int));
+  cudaMemPoolProps pp{};
+  pp.allocType = cudaMemAllocationTypePinned;
+  pp.location.type = cudaMemLocationTypeDevice;
+  pp.location.id = c.device;
+  e = cudaMemPoolCreate(&ctx->pool, &pp);
+  if (e != cudaSuccess) {
+    cudaFree(ctx->err_word);
+    delete ctx;
+    return cuda_fail((int)e, "nam_init: memory pool");
+  }
+  uint64_t keep = UINT64_MAX;
+  cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep);
   cudaDeviceSynchronize();
   *out = ctx;
   return NAM_OK;
@@ -177,6 +189,7 @@ extern "C" nam_status nam_shutdown(nam_ctx* ctx) {
   cudaFree(ctx->err_word);
   cudaFree(ctx->stage_dev);
   if (ctx->stage_stream) cudaStreamDestroy((cudaStream_t)ctx->stage_stream);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
   return NAM_OK;
 }
@@ -451,7 +464,7 @@ extern "C" nam_status nam_fp8_calibrate(nam_ctx* ctx, nam_material m, const nam_
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   float* amax = nullptr;
-  cudaError_t ce = cudaMallocAsync((void**)&amax, 4 * sizeof(float), s);
+  cudaError_t ce = cudaMallocFromPoolAsync((void**)&amax, 4 * sizeof(float), ctx->pool, s);
   if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_fp8_calibrate: allocation");
   ce = cudaMemsetAsync(amax, 0, 4 * sizeof(float), s);
   LaunchCommon L;
@@ -581,7 +594,7 @@ extern "C" nam_status nam_eval_multi(nam_ctx* ctx, const nam_material* mats, int
     std::memcpy(host.data() + cb + pb + k * sizeof(void*), &w, sizeof w);
   }
   void* dev = nullptr;
-  cudaError_t e = cudaMallocAsync(&dev, host.size(), s);
+  cudaError_t e = cudaMallocFromPoolAsync(&dev, host.size(), ctx->pool, s);
   if (e != cudaSuccess) return cuda_fail((int)e, "nam_eval_multi: table allocation");
   e = cudaMemcpyAsync(dev, host.data(), host.size(), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {

@@ -5,6 +5,8 @@
 #include <cstdint>
 #include <deque>
 #include <map>
+#include <cuda_runtime.h>
+
 #include <mutex>
 #include <set>
 #include <thread>
@@ -55,6 +57,10 @@ struct nam_ctx {
   std::atomic<bool> fault_alloc{false};
   std::atomic<bool> fault_launch{false};
   std::atomic<bool> fault_stall{false};
+  // stream-ordered allocations (serving frame buffers, work tables): a pool
+  // of the context's own that keeps freed memory instead of returning it to
+  // the driver, so that steady-state frames do not pay for remapping
+  cudaMemPool_t pool = nullptr;
   // serving
   nam::ServeState* serve = nullptr;
   std::mutex serve_mu;                  // guards `serve` creation

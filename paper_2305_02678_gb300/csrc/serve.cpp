@@ -100,7 +100,7 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
   cudaStream_t s = slot.stream;
   const int64_t n = j->frame.n_queries;
   if (ctx->fault_alloc.exchange(false)) return fail(NAM_ERR_OOM, "injected allocation failure");
-  cudaError_t e = cudaMallocAsync(&j->dev, j->bytes, s);
+  cudaError_t e = cudaMallocFromPoolAsync(&j->dev, j->bytes, ctx->pool, s);
   if (e != cudaSuccess) return cuda_fail((int)e, "serving: frame buffers");
   uint8_t* base = (uint8_t*)j->dev;
   const float* src[10] = {j->frame.q.u, j->frame.q.v, j->frame.q.lod, j->frame.q.wix, j->frame.q.wiy,

@@ -201,11 +201,12 @@ __device__ __forceinline__ uint32_t pack_h2(float lo, float hi) {
   asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
   return d;
 }
-// Same with ReLU: the packed half2 max against zero after rounding equals
-// rounding max(x, 0) (round-to-nearest is monotonic and keeps 0).
+// Same with ReLU applied by the conversion (negative results become +0;
+// rounding commutes with max(x, 0) because round-to-nearest is monotonic and
+// keeps 0).
 __device__ __forceinline__ uint32_t pack_h2_relu(float lo, float hi) {
-  uint32_t d = pack_h2(lo, hi);
-  asm("max.f16x2 %0, %0, %1;" : "+r"(d) : "r"(0u));
+  uint32_t d;
+  asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
   return d;
 }
 // d = a * b + c on pairs of FP32 values (one packed instruction).
