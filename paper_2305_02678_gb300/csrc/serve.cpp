@@ -40,6 +40,10 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   Job* job = nullptr;
+  // pinned staging for the frame's work table: an upload from pageable
+  // memory could make the scheduler thread wait for the slot's stream
+  void* host_tab = nullptr;
+  size_t host_tab_bytes = 0;
 };
 
 struct ServeState {
@@ -103,6 +107,34 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
   cudaError_t e = cudaMallocFromPoolAsync(&j->dev, j->bytes, ctx->pool, s);
   if (e != cudaSuccess) return cuda_fail((int)e, "serving: frame buffers");
   uint8_t* base = (uint8_t*)j->dev;
+  const int64_t nfield = j->nf;
+  float* rgb = (float*)(base + (size_t)nfield * n * 4);
+  // work table (int64 fields) at the next 16-byte boundary after the RGB;
+  // uploaded first, from the slot's pinned buffer (free: the slot's previous
+  // frame has completed)
+  uint8_t* tab = base + (((size_t)nfield * n * 4 + (size_t)n * 12 + 15) / 16 * 16);
+  const size_t cb = j->chunks.size() * sizeof(Chunk);
+  const size_t pb = j->mats.size() * sizeof(void*);
+  const size_t tb = cb + 2 * pb;
+  if (tb > slot.host_tab_bytes) {
+    if (slot.host_tab) cudaFreeHost(slot.host_tab);
+    slot.host_tab = nullptr;
+    slot.host_tab_bytes = 0;
+    const size_t want = std::max<size_t>(tb * 2, 1 << 20);
+    e = cudaMallocHost(&slot.host_tab, want);
+    if (e != cudaSuccess) return cuda_fail((int)e, "serving: pinned table buffer");
+    slot.host_tab_bytes = want;
+  }
+  uint8_t* host = (uint8_t*)slot.host_tab;
+  std::memcpy(host, j->chunks.data(), cb);
+  for (size_t k = 0; k < j->mats.size(); ++k) {
+    const void* p = j->mats[k]->pyramid;
+    const void* w = j->mats[k]->blob;
+    std::memcpy(host + cb + k * sizeof(void*), &p, sizeof p);
+    std::memcpy(host + cb + pb + k * sizeof(void*), &w, sizeof w);
+  }
+  e = cudaMemcpyAsync(tab, host, tb, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "serving: table upload");
   const float* src[10] = {j->frame.q.u, j->frame.q.v, j->frame.q.lod, j->frame.q.wix, j->frame.q.wiy,
                           j->frame.q.wiz, j->frame.q.wox, j->frame.q.woy, j->frame.q.woz, j->frame.q.xi};
   float* dst[10] = {nullptr};
@@ -111,21 +143,6 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
     e = cudaMemcpyAsync(dst[f], src[f], (size_t)n * 4, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_fail((int)e, "serving: H2D");
   }
-  float* rgb = (float*)(base + (size_t)j->nf * n * 4);
-  // chunk table (int64 fields) at the next 16-byte boundary after the RGB
-  uint8_t* tab = base + (((size_t)j->nf * n * 4 + (size_t)n * 12 + 15) / 16 * 16);
-  const size_t cb = j->chunks.size() * sizeof(Chunk);
-  const size_t pb = j->mats.size() * sizeof(void*);
-  std::vector<uint8_t> host(cb + 2 * pb);
-  std::memcpy(host.data(), j->chunks.data(), cb);
-  for (size_t k = 0; k < j->mats.size(); ++k) {
-    const void* p = j->mats[k]->pyramid;
-    const void* w = j->mats[k]->blob;
-    std::memcpy(host.data() + cb + k * sizeof(void*), &p, sizeof p);
-    std::memcpy(host.data() + cb + pb + k * sizeof(void*), &w, sizeof w);
-  }
-  e = cudaMemcpyAsync(tab, host.data(), host.size(), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return cuda_fail((int)e, "serving: table upload");
   nam_queries dq{dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], dst[7], dst[8], dst[9]};
   LaunchCommon L;
   fill_launch(ctx, j->mats[0], &dq, 0, rgb, j->frame.flags, &L);
@@ -244,6 +261,7 @@ void nam::serve_stop(nam_ctx* ctx) {
     cudaStreamSynchronize(sl.stream);
     cudaStreamDestroy(sl.stream);
     cudaEventDestroy(sl.done);
+    if (sl.host_tab) cudaFreeHost(sl.host_tab);
   }
   for (auto& kv : S->jobs) delete kv.second;
   delete S;
