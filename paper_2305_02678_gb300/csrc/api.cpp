@@ -189,6 +189,9 @@ extern "C" nam_status nam_shutdown(nam_ctx* ctx) {
   cudaFree(ctx->err_word);
   cudaFree(ctx->stage_dev);
   if (ctx->stage_stream) cudaStreamDestroy((cudaStream_t)ctx->stage_stream);
+  if (ctx->h2d_stream) cudaStreamDestroy((cudaStream_t)ctx->h2d_stream);
+  if (ctx->d2h_stream) cudaStreamDestroy((cudaStream_t)ctx->d2h_stream);
+  for (void* ev : ctx->stage_events) cudaEventDestroy((cudaEvent_t)ev);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
   delete ctx;
   return NAM_OK;
@@ -510,24 +513,52 @@ extern "C" nam_status nam_eval_host(nam_ctx* ctx, nam_material m, const nam_quer
     }
     ctx->stage_bytes = need;
   }
+  // Pipelined over (at most four) chunks: host->device copies on one stream,
+  // kernels on the caller's stream, device->host copies on another, ordered
+  // by events, so that chunk k+1 arrives while chunk k runs and chunk k-1
+  // returns.  Chunks hold at least 2^19 queries (2 MB per field copy: smaller
+  // copies lose bandwidth to per-copy overhead).  Every chunk has its own
+  // region of the staging area, so nothing is overwritten while in use.
+  const int64_t kHostChunk = std::max<int64_t>(1 << 19, ((n + 3) / 4 + 127) / 128 * 128);
+  const int64_t nchunk = (n + kHostChunk - 1) / kHostChunk;
+  cudaError_t ce = cudaSuccess;
+  if (!ctx->h2d_stream) ce = cudaStreamCreateWithFlags((cudaStream_t*)&ctx->h2d_stream, cudaStreamNonBlocking);
+  if (ce == cudaSuccess && !ctx->d2h_stream)
+    ce = cudaStreamCreateWithFlags((cudaStream_t*)&ctx->d2h_stream, cudaStreamNonBlocking);
+  while (ce == cudaSuccess && (int64_t)ctx->stage_events.size() < 2 * nchunk) {
+    cudaEvent_t ev;
+    ce = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (ce == cudaSuccess) ctx->stage_events.push_back((void*)ev);
+  }
+  if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_eval_host: streams");
   cudaStream_t s = (cudaStream_t)stream;
+  cudaStream_t sin = (cudaStream_t)ctx->h2d_stream, sout = (cudaStream_t)ctx->d2h_stream;
   float* base = (float*)ctx->stage_dev;
   const float* src[10] = {q->u, q->v, q->lod, q->wix, q->wiy, q->wiz, q->wox, q->woy, q->woz, q->xi};
   float* dst[10];
-  for (int f = 0; f < nf; ++f) {
-    dst[f] = base + (size_t)f * n;
-    cudaError_t e = cudaMemcpyAsync(dst[f], src[f], (size_t)n * 4, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail((int)e, "nam_eval_host: H2D");
-  }
+  for (int f = 0; f < nf; ++f) dst[f] = base + (size_t)f * n;
   float* rgb_dev = base + (size_t)nf * n;
-  nam_queries dq{dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], dst[7], dst[8], has_xi ? dst[9] : nullptr};
-  LaunchCommon L;
-  fill_launch(ctx, m, &dq, n, rgb_dev, flags, &L);
-  int e = launch_material(L, m->desc.precision, stream);
-  if (e) return cuda_fail(e, "nam_eval_host: launch");
-  cudaError_t ce = cudaMemcpyAsync(rgb_out, rgb_dev, (size_t)n * 12, cudaMemcpyDeviceToHost, s);
-  if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_eval_host: D2H");
-  ce = cudaStreamSynchronize(s);
+  for (int64_t k = 0; k < nchunk; ++k) {
+    const int64_t off = k * kHostChunk, cnt = std::min<int64_t>(kHostChunk, n - off);
+    cudaEvent_t ev_in = (cudaEvent_t)ctx->stage_events[2 * k], ev_done = (cudaEvent_t)ctx->stage_events[2 * k + 1];
+    for (int f = 0; f < nf && ce == cudaSuccess; ++f)
+      ce = cudaMemcpyAsync(dst[f] + off, src[f] + off, (size_t)cnt * 4, cudaMemcpyHostToDevice, sin);
+    if (ce == cudaSuccess) ce = cudaEventRecord(ev_in, sin);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(s, ev_in, 0);
+    if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_eval_host: H2D");
+    nam_queries dq{dst[0] + off, dst[1] + off, dst[2] + off, dst[3] + off, dst[4] + off, dst[5] + off,
+                   dst[6] + off, dst[7] + off, dst[8] + off, has_xi ? dst[9] + off : nullptr};
+    LaunchCommon L;
+    fill_launch(ctx, m, &dq, cnt, rgb_dev + 3 * off, flags, &L);
+    int e = launch_material(L, m->desc.precision, stream);
+    if (e) return cuda_fail(e, "nam_eval_host: launch");
+    ce = cudaEventRecord(ev_done, s);
+    if (ce == cudaSuccess) ce = cudaStreamWaitEvent(sout, ev_done, 0);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(rgb_out + 3 * off, rgb_dev + 3 * off, (size_t)cnt * 12, cudaMemcpyDeviceToHost, sout);
+    if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_eval_host: D2H");
+  }
+  ce = cudaStreamSynchronize(sout);
   if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_eval_host: sync");
   return NAM_OK;
 }

@@ -53,6 +53,9 @@ struct nam_ctx {
   void* stage_dev = nullptr;
   size_t stage_bytes = 0;
   void* stage_stream = nullptr;
+  void* h2d_stream = nullptr;           // nam_eval_host: copies in / out, overlapping
+  void* d2h_stream = nullptr;           // the kernels on the caller's stream
+  std::vector<void*> stage_events;
   // fault injection
   std::atomic<bool> fault_alloc{false};
   std::atomic<bool> fault_launch{false};

@@ -242,6 +242,26 @@ def test_deterministic_and_host_path_identical(gctx, w2_small):
     mat.destroy()
 
 
+@pytest.mark.parametrize("precision,n", [(1, 2073600), (0, 1100001), (1, 524289)])
+def test_host_path_pipelined_chunks_identical(gctx, w2, precision, n):
+    """nam_eval_host splits large batches into chunks whose copies and
+    kernels overlap; every query must come out as the device path gives it,
+    also for ragged last chunks and the FP32 kernel."""
+    import torch
+    m = w2["model"]
+    q = W.slice_queries(w2["queries"], 0, n)
+    mat = gctx.material(w2["W0"], w2["H0"], w2["L"], w2["pyramid"], m["frame"], m["decoder"], precision=precision)
+    a = mat.eval(to_device(q)).cpu().numpy()
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in q.items()}
+    h = mat.eval_host(pinned)
+    assert np.array_equal(a, h)
+    # pageable numpy inputs take the same path
+    h2 = mat.eval_host(q)
+    assert np.array_equal(a, h2)
+    mat.destroy()
+    gctx.check()
+
+
 def test_multi_material_matches_single(gctx, oracle):
     """Work items over several materials give bit-identical results to
     evaluating each item's queries with its material alone."""
