@@ -891,3 +891,201 @@ void orc_eval_alternatives(const orc_model* m, const orc_queries* q, int64_t n, 
   for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, alt_worker, &jobs[t]);
   for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
 }
+
+/* ------------------------------------------------------------------------- */
+/* importance sampling (Sec. 4.3, Appendix A)                                 */
+/* ------------------------------------------------------------------------- */
+/* A second MLP maps (z(x), wi) to the nine parameters of an analytic proxy
+ * density: a blend of a tilted cosine lobe and a GGX half-vector density with
+ * elliptical anisotropy and non-centred mean slopes (Appendix A).
+ *
+ * Readings where the paper leaves the form open:
+ *  - network: input (z0..z7, wi_x, wi_y, wi_z), three ReLU hidden layers of
+ *    32, nine linear outputs in the paper's order
+ *    (w_d, mu_dx, mu_dy, w_s, alpha_x, alpha_y, rho, mu_sx, mu_sy);
+ *  - "quadratic approximations of tanh and sinh": qtanh(x) = x (1 - |x|/4)
+ *    for |x| < 2 and sign(x) beyond (odd, C1, onto [-1, 1]); qsinh(x) =
+ *    x (1 + |x|/2) (odd, monotonic, unbounded);
+ *  - alpha = 1e-3 + (1 - 1e-3) (qtanh + 1) / 2 in [1e-3, 1]; rho = 0.99 qtanh
+ *    (so that sqrt(1 - rho^2) > 0); mu = qsinh; (w_d, w_s) = softmax;
+ *  - D_std, the unit-roughness GGX density of the standard half-vector
+ *    sampling technique, is cos(theta) / pi on the upper hemisphere (at
+ *    alpha = 1 the GGX NDF is 1/pi, and the technique draws normals with
+ *    density D cos(theta));
+ *  - the half vector of the specular pdf is normalize(wi + wo) (zero density
+ *    when wi + wo = 0 or when it points below the surface);
+ *  - sampling takes three variates: u3 < w_d picks the diffuse lobe; (u1, u2)
+ *    drive Malley's cosine mapping (which is also the alpha = 1 GGX normal
+ *    sampling); the diffuse lobe is rotated to n_d with the Duff et al. basis;
+ *    the returned density is the full mixture density of the sampled wo. */
+#define ORC_SAMPLER_IN 11
+#define ORC_SAMPLER_H 32
+#define ORC_SAMPLER_OUT 9
+#define ORC_ALPHA_MIN 1e-3
+#define ORC_RHO_MAX 0.99
+#define ORC_PI 3.14159265358979323846
+
+double orc_qtanh(double x) {
+  double a = fabs(x);
+  if (a >= 2.0) return x > 0 ? 1.0 : -1.0;
+  return x * (1.0 - a / 4.0);
+}
+double orc_qsinh(double x) { return x * (1.0 + fabs(x) / 2.0); }
+
+/* Raw network outputs -> the nine proxy parameters. */
+void orc_proxy_activate(const double o[9], double p[9]) {
+  double mx = o[0] > o[3] ? o[0] : o[3];
+  double ed = exp(o[0] - mx), es = exp(o[3] - mx);
+  p[0] = ed / (ed + es);
+  p[3] = es / (ed + es);
+  p[1] = orc_qsinh(o[1]);
+  p[2] = orc_qsinh(o[2]);
+  p[4] = ORC_ALPHA_MIN + (1.0 - ORC_ALPHA_MIN) * 0.5 * (orc_qtanh(o[4]) + 1.0);
+  p[5] = ORC_ALPHA_MIN + (1.0 - ORC_ALPHA_MIN) * 0.5 * (orc_qtanh(o[5]) + 1.0);
+  p[6] = ORC_RHO_MAX * orc_qtanh(o[6]);
+  p[7] = orc_qsinh(o[7]);
+  p[8] = orc_qsinh(o[8]);
+}
+
+/* Sampler MLP: weights per layer W[out][in] then b[out], widths 11, 32, 32,
+ * 32, 9. */
+static void sampler_mlp(const double* sp, const double z[ORC_C], const double wi[3], double o[9]) {
+  double x[ORC_SAMPLER_H], y[ORC_SAMPLER_H];
+  double in[ORC_SAMPLER_IN];
+  for (int c = 0; c < ORC_C; ++c) in[c] = z[c];
+  for (int k = 0; k < 3; ++k) in[ORC_C + k] = wi[k];
+  const int widths[5] = {ORC_SAMPLER_IN, ORC_SAMPLER_H, ORC_SAMPLER_H, ORC_SAMPLER_H, ORC_SAMPLER_OUT};
+  const double* p = sp;
+  const double* cur = in;
+  for (int l = 0; l < 4; ++l) {
+    int ni = widths[l], no = widths[l + 1];
+    const double* W = p;
+    const double* b = p + ni * no;
+    p = b + no;
+    double* out = (l == 3) ? o : (l % 2 == 0 ? x : y);
+    for (int j = 0; j < no; ++j) {
+      double s = b[j];
+      for (int k = 0; k < ni; ++k) s += W[j * ni + k] * cur[k];
+      out[j] = (l == 3) ? s : (s > 0.0 ? s : 0.0);
+    }
+    cur = out;
+  }
+}
+
+static void normalize3(double v[3]) {
+  double l = sqrt(dot3(v, v));
+  for (int k = 0; k < 3; ++k) v[k] /= l;
+}
+
+/* Density of half vectors of the specular lobe (the LTC-style transform of
+ * D_std by M, with its Jacobian det(M^-1) / |M^-1 h|^3). */
+double orc_proxy_pdf_h(const double p[9], const double h[3]) {
+  double ax = p[4], ay = p[5], rho = p[6], msx = p[7], msy = p[8];
+  double s = sqrt(1.0 - rho * rho);
+  /* v = M^-1 h, M = [[ax, 0, -msx], [ay rho, ay s, -msy], [0, 0, 1]] */
+  double v[3];
+  v[2] = h[2];
+  v[0] = (h[0] + msx * h[2]) / ax;
+  v[1] = (h[1] + msy * h[2] - ay * rho * v[0]) / (ay * s);
+  double vl = sqrt(dot3(v, v));
+  double cz = v[2] / vl;
+  if (!(cz > 0.0)) return 0.0;
+  double dstd = cz / ORC_PI;
+  double detinv = 1.0 / (ax * ay * s);
+  return dstd * detinv / (vl * vl * vl);
+}
+
+/* Full proxy density of wo given wi (Appendix A, pdf_full / pdf_spec). */
+double orc_proxy_pdf(const double p[9], const double wi[3], const double wo[3]) {
+  double nd[3] = {-p[1], -p[2], 1.0};
+  normalize3(nd);
+  double c = dot3(wo, nd);
+  double pd = c > 0.0 ? c / ORC_PI : 0.0;
+  double h[3] = {wi[0] + wo[0], wi[1] + wo[1], wi[2] + wo[2]};
+  double hl = sqrt(dot3(h, h));
+  double ps = 0.0;
+  if (hl > 0.0) {
+    for (int k = 0; k < 3; ++k) h[k] /= hl;
+    double oh = fabs(dot3(wo, h));
+    if (oh > 0.0) ps = orc_proxy_pdf_h(p, h) / (4.0 * oh);
+  }
+  return p[0] * pd + p[3] * ps;
+}
+
+static void cosine_dir(double u1, double u2, double d[3]) {
+  double r = sqrt(u1), phi = 2.0 * ORC_PI * u2;
+  d[0] = r * cos(phi);
+  d[1] = r * sin(phi);
+  d[2] = sqrt(1.0 - u1 > 0.0 ? 1.0 - u1 : 0.0);
+}
+
+/* Sample transform W(u; wi) of the proxy (Appendix A, Sampling). */
+void orc_proxy_sample(const double p[9], const double wi[3], const double u[3], double wo[3], double* pdf) {
+  double l[3];
+  cosine_dir(u[0], u[1], l);
+  if (u[2] < p[0]) {
+    double nd[3] = {-p[1], -p[2], 1.0}, t[3], b[3];
+    normalize3(nd);
+    basis_tangent(nd, t);
+    cross3(nd, t, b);
+    for (int k = 0; k < 3; ++k) wo[k] = t[k] * l[0] + b[k] * l[1] + nd[k] * l[2];
+  } else {
+    double ax = p[4], ay = p[5], rho = p[6], msx = p[7], msy = p[8];
+    double s = sqrt(1.0 - rho * rho);
+    double h[3] = {ax * l[0] - msx * l[2], ay * rho * l[0] + ay * s * l[1] - msy * l[2], l[2]};
+    normalize3(h);
+    double d = dot3(wi, h);
+    for (int k = 0; k < 3; ++k) wo[k] = 2.0 * d * h[k] - wi[k];
+  }
+  *pdf = orc_proxy_pdf(p, wi, wo);
+}
+
+/* Per query: z from the latent pyramid as for the decoder, then the sampler
+ * network and its activations.  params_out [n][9]. */
+void orc_sampler_params(const orc_model* m, const double* sp, const orc_queries* q, int64_t n, double* params_out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double z[ORC_C], o[9];
+    double xi = q->xi ? q->xi[i] : 0.0;
+    latent(m, q->u[i], q->v[i], q->lod[i], xi, z);
+    double wi[3] = {q->wix[i], q->wiy[i], q->wiz[i]};
+    sampler_mlp(sp, z, wi, o);
+    orc_proxy_activate(o, params_out + i * 9);
+  }
+}
+
+/* Proxy density of each query's wo given its wi; pdf_out [n]. */
+void orc_sampler_pdf(const orc_model* m, const double* sp, const orc_queries* q, int64_t n, double* pdf_out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double p[9], z[ORC_C], o[9];
+    double xi = q->xi ? q->xi[i] : 0.0;
+    latent(m, q->u[i], q->v[i], q->lod[i], xi, z);
+    double wi[3] = {q->wix[i], q->wiy[i], q->wiz[i]};
+    double wo[3] = {q->wox[i], q->woy[i], q->woz[i]};
+    sampler_mlp(sp, z, wi, o);
+    orc_proxy_activate(o, p);
+    pdf_out[i] = orc_proxy_pdf(p, wi, wo);
+  }
+}
+
+/* One sample per query from variates u [n][3]: wo_out [n][3], pdf_out [n]. */
+void orc_sampler_sample(const orc_model* m, const double* sp, const orc_queries* q, int64_t n, const double* u,
+                        double* wo_out, double* pdf_out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double p[9], z[ORC_C], o[9];
+    double xi = q->xi ? q->xi[i] : 0.0;
+    latent(m, q->u[i], q->v[i], q->lod[i], xi, z);
+    double wi[3] = {q->wix[i], q->wiy[i], q->wiz[i]};
+    sampler_mlp(sp, z, wi, o);
+    orc_proxy_activate(o, p);
+    orc_proxy_sample(p, wi, u + i * 3, wo_out + i * 3, pdf_out + i);
+  }
+}
+
+/* Batch forms for quadrature: out[k] = pdf of wo[k] given wi, and the
+ * half-vector density at h[k]. */
+void orc_proxy_pdf_batch(const double p[9], const double wi[3], const double* wo, int64_t n, double* out) {
+  for (int64_t k = 0; k < n; ++k) out[k] = orc_proxy_pdf(p, wi, wo + 3 * k);
+}
+void orc_proxy_pdf_h_batch(const double p[9], const double* h, int64_t n, double* out) {
+  for (int64_t k = 0; k < n; ++k) out[k] = orc_proxy_pdf_h(p, h + 3 * k);
+}

@@ -57,6 +57,17 @@ def lib():
         _lib.orc_f64_to_f16.restype = u16; _lib.orc_f64_to_f16.argtypes = [d]
         _lib.orc_round_f16.restype = d; _lib.orc_round_f16.argtypes = [d]
         _lib.orc_e4m3_to_f64.restype = d; _lib.orc_e4m3_to_f64.argtypes = [u8]
+        _lib.orc_qtanh.restype = d; _lib.orc_qtanh.argtypes = [d]
+        _lib.orc_qsinh.restype = d; _lib.orc_qsinh.argtypes = [d]
+        _lib.orc_proxy_activate.argtypes = [p, p]
+        _lib.orc_proxy_pdf_h.restype = d; _lib.orc_proxy_pdf_h.argtypes = [p, p]
+        _lib.orc_proxy_pdf.restype = d; _lib.orc_proxy_pdf.argtypes = [p, p, p]
+        _lib.orc_proxy_sample.argtypes = [p, p, p, p, p]
+        _lib.orc_sampler_params.argtypes = [p, p, p, i64, p]
+        _lib.orc_sampler_pdf.argtypes = [p, p, p, i64, p]
+        _lib.orc_sampler_sample.argtypes = [p, p, p, i64, p, p, p]
+        _lib.orc_proxy_pdf_batch.argtypes = [p, p, p, i64, p]
+        _lib.orc_proxy_pdf_h_batch.argtypes = [p, p, i64, p]
         _lib.orc_f64_to_e4m3.restype = u8; _lib.orc_f64_to_e4m3.argtypes = [d]
         _lib.orc_round_e4m3.restype = d; _lib.orc_round_e4m3.argtypes = [d]
         _lib.orc_quantize_e4m3_layer.argtypes = [p, i64, p, p]
@@ -398,3 +409,91 @@ def relative_error(g, o):
     tau = max(tau, 1e-30)
     r = np.abs(g - o) / np.maximum(np.abs(o), tau)
     return float(r.max()), float(r.mean())
+
+
+# ----------------------------------------------------------------------------
+# importance sampling (Sec. 4.3, Appendix A)
+# ----------------------------------------------------------------------------
+PROXY_FIELDS = ("w_d", "mu_dx", "mu_dy", "w_s", "alpha_x", "alpha_y", "rho", "mu_sx", "mu_sy")
+
+
+def flat_sampler(layers):
+    """[(W [out][in], b), ...] for widths 11-32-32-32-9 -> FP64 flat array."""
+    return np.ascontiguousarray(np.concatenate([np.concatenate([W.ravel(), b]) for W, b in layers]),
+                                dtype=np.float64)
+
+
+def qtanh(x):
+    return np.array([lib().orc_qtanh(float(v)) for v in np.ravel(x)]).reshape(np.shape(x))
+
+
+def qsinh(x):
+    return np.array([lib().orc_qsinh(float(v)) for v in np.ravel(x)]).reshape(np.shape(x))
+
+
+def proxy_activate(raw):
+    raw = np.ascontiguousarray(raw, dtype=np.float64)
+    out = np.zeros(9)
+    lib().orc_proxy_activate(_ptr(raw), _ptr(out))
+    return out
+
+
+def proxy_pdf(params, wi, wo):
+    """Proxy density of each wo [n][3] given one wi [3]."""
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    wo = np.ascontiguousarray(np.atleast_2d(wo), dtype=np.float64)
+    wi = np.ascontiguousarray(wi, dtype=np.float64)
+    out = np.zeros(len(wo))
+    lib().orc_proxy_pdf_batch(_ptr(params), _ptr(wi), _ptr(wo), len(wo), _ptr(out))
+    return out
+
+
+def proxy_pdf_h(params, h):
+    """Density of specular half vectors at each h [n][3]."""
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    h = np.ascontiguousarray(np.atleast_2d(h), dtype=np.float64)
+    out = np.zeros(len(h))
+    lib().orc_proxy_pdf_h_batch(_ptr(params), _ptr(h), len(h), _ptr(out))
+    return out
+
+
+def proxy_sample(params, wi, u):
+    """Samples for variates u [n][3]: (wo [n][3], pdf [n])."""
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    wi = np.ascontiguousarray(wi, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    wo = np.zeros((len(u), 3))
+    pdf = np.zeros(len(u))
+    L = lib()
+    for k in range(len(u)):
+        L.orc_proxy_sample(_ptr(params), _ptr(wi), _ptr(u[k]), _ptr(wo[k]), _ptr(pdf[k:]))
+    return wo, pdf
+
+
+def sampler_params(model: Model, sampler, q) -> np.ndarray:
+    sp = flat_sampler(sampler)
+    n = _nq(q)
+    out = np.zeros((n, 9))
+    qv = _QueryView(q, n)
+    lib().orc_sampler_params(C.byref(model._s), _ptr(sp), C.byref(qv.s), n, _ptr(out))
+    return out
+
+
+def sampler_pdf(model: Model, sampler, q) -> np.ndarray:
+    sp = flat_sampler(sampler)
+    n = _nq(q)
+    out = np.zeros(n)
+    qv = _QueryView(q, n)
+    lib().orc_sampler_pdf(C.byref(model._s), _ptr(sp), C.byref(qv.s), n, _ptr(out))
+    return out
+
+
+def sampler_sample(model: Model, sampler, q, u):
+    sp = flat_sampler(sampler)
+    n = _nq(q)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    wo = np.zeros((n, 3))
+    pdf = np.zeros(n)
+    qv = _QueryView(q, n)
+    lib().orc_sampler_sample(C.byref(model._s), _ptr(sp), C.byref(qv.s), n, _ptr(u), _ptr(wo), _ptr(pdf))
+    return wo, pdf
