@@ -146,6 +146,13 @@ typedef struct {
                                  nam_backward / nam_train_step (F32 only) */
   const float* fp8_act_scale; /* NAM_PREC_FP8: host array, input scale of
                                  each decoder layer (n_layers values > 0) */
+  /* importance sampler (Sec. 4.3, Appendix A): an MLP from (z, wi) to the
+   * nine parameters of the analytic proxy density.  sampler_hidden = 0: no
+   * sampler; 32: widths 11 -> 32 -> 32 -> 32 -> 9 with ReLU hidden layers,
+   * FP32 weights per layer W (out x in) then b (out), layers in order (host
+   * or device memory as params_on_device says), copied at creation. */
+  int32_t sampler_hidden;
+  const float* sampler_weights;
 } nam_material_desc;
 
 typedef struct {
@@ -207,6 +214,32 @@ nam_status nam_eval_host(nam_ctx* ctx, nam_material m, const nam_queries* q, int
  * any precision.  Synchronises `stream`. */
 nam_status nam_fp8_calibrate(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
                              float* act_scale_out, void* stream);
+
+/* Importance sampling with the material's proxy density (Sec. 4.3,
+ * Appendix A).  The sampler network maps (z(x), wi) to (w_d, mu_d, w_s,
+ * alpha_x, alpha_y, rho, mu_s): w_d, w_s = softmax of two outputs; mu =
+ * qsinh(o) = o (1 + |o|/2); alpha = 1e-3 + (1 - 1e-3) (qtanh(o) + 1) / 2 and
+ * rho = 0.99 qtanh(o), qtanh(o) = o (1 - |o|/4) for |o| < 2 else sign(o).
+ * Density: p(wo) = w_d max(0, wo . n_d) / pi + w_s p_s(wo), n_d =
+ * normalize(-mu_dx, -mu_dy, 1); p_s(wo) = D_std(v/|v|) det(M^-1) / |v|^3 /
+ * (4 |wo . h|), h = normalize(wi + wo), v = M^-1 h, D_std(w) = max(0, w_z) /
+ * pi, M = [[alpha_x, 0, -mu_sx], [alpha_y rho, alpha_y sqrt(1 - rho^2),
+ * -mu_sy], [0, 0, 1]].  Directions are in the query's geometric frame (z up).
+ * All arrays are device memory; FP32 arithmetic; asynchronous on `stream`;
+ * NAM_ERR_UNSUPPORTED if the material has no sampler.
+ *
+ * nam_sample: one direction per query from the variates u ([n][3] in
+ * [0, 1)): u[2] < w_d picks the diffuse lobe, (u[0], u[1]) drive the cosine
+ * mapping (sqrt(u0) cos 2 pi u1, sqrt(u0) sin 2 pi u1, sqrt(1 - u0)), which is
+ * rotated to n_d (diffuse) or mapped to the half vector normalize(M d) and
+ * reflected about it (specular).  Writes wo_out [n][3] and, if pdf_out is not
+ * NULL, the mixture density of each sampled direction [n].  The queries' wo
+ * arrays are not read.
+ * nam_sample_pdf: the mixture density of each query's wo given its wi. */
+nam_status nam_sample(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n, const float* u,
+                      float* wo_out, float* pdf_out, void* stream);
+nam_status nam_sample_pdf(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n, float* pdf_out,
+                          void* stream);
 
 /* A contiguous run of queries [start, start+count) evaluated with
  * materials[material]. */

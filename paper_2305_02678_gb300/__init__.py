@@ -57,9 +57,11 @@ class Context:
         self.close()
 
     def material(self, W0, H0, L, pyramid, frame, decoder, precision=1, filter=0, address=0, trainable=False,
-                 act_scale=None):
-        """precision: NAM_PREC_F32/F16/FP8 (0/1/2); filter: trilinear/stochastic (0/1); address: wrap/clamp."""
-        return Material(self, W0, H0, L, pyramid, frame, decoder, precision, filter, address, trainable, act_scale)
+                 act_scale=None, sampler=None):
+        """precision: NAM_PREC_F32/F16/FP8 (0/1/2); filter: trilinear/stochastic (0/1); address: wrap/clamp;
+        sampler: None or [(W, b)] * 4 of the 11-32-32-32-9 importance-sampling MLP."""
+        return Material(self, W0, H0, L, pyramid, frame, decoder, precision, filter, address, trainable, act_scale,
+                        sampler)
 
     def stats(self):
         from . import binding as B
@@ -73,7 +75,8 @@ class Context:
 class Material:
     """A neural material resident on the device (pyramid + MLP weights)."""
 
-    def __init__(self, ctx, W0, H0, L, pyramid, frame, decoder, precision, filter, address, trainable, act_scale):
+    def __init__(self, ctx, W0, H0, L, pyramid, frame, decoder, precision, filter, address, trainable, act_scale,
+                 sampler=None):
         from . import binding as B
         self.ctx = ctx
         pyr = np.ascontiguousarray(pyramid)
@@ -99,7 +102,12 @@ class Material:
         if act_scale is not None:
             sc = np.ascontiguousarray(act_scale, dtype=np.float32)
             d.fp8_act_scale = sc.ctypes.data
-        self._keep = [pyr, fr, dec, sc]
+        smp = None
+        if sampler is not None:
+            smp = flatten_decoder(sampler)
+            d.sampler_hidden = sampler[0][0].shape[0]
+            d.sampler_weights = smp.ctypes.data
+        self._keep = [pyr, fr, dec, sc, smp]
         self.h = B.nam_create_material(ctx.h, d)
         self._keep = []
         self.precision, self.filter, self.address = precision, filter, address

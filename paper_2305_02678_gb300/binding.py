@@ -41,7 +41,7 @@ class nam_material_desc(C.Structure):
                 ("frame_hidden", C.c_int32), ("n_layers", C.c_int32), ("frame_weights", C.c_void_p),
                 ("widths", C.c_int32 * (NAM_MAX_LAYERS + 1)), ("decoder_weights", C.c_void_p),
                 ("precision", C.c_int32), ("filter", C.c_int32), ("address", C.c_int32), ("trainable", C.c_int32),
-                ("fp8_act_scale", C.c_void_p)]
+                ("fp8_act_scale", C.c_void_p), ("sampler_hidden", C.c_int32), ("sampler_weights", C.c_void_p)]
 
 
 class nam_material_info(C.Structure):
@@ -84,7 +84,7 @@ class nam_stats(C.Structure):
 #: every symbol include/nam.h declares
 EXPORTS = ("nam_status_string", "nam_last_error_message", "nam_init", "nam_shutdown", "nam_check_device_error",
            "nam_create_material", "nam_destroy_material", "nam_material_get_info", "nam_material_params",
-           "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_fp8_calibrate", "nam_backward", "nam_train_step",
+           "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_fp8_calibrate", "nam_sample", "nam_sample_pdf", "nam_backward", "nam_train_step",
            "nam_train_step_noalloc", "nam_now",
            "nam_submit", "nam_poll", "nam_wait", "nam_cancel", "nam_get_stats", "nam_inject_fault",
            "nam_debug_mma_selftest", "nam_debug_mma_selftest_ts")
@@ -118,6 +118,8 @@ def _load():
         "nam_train_step": (i32, [p, p, p, p, i64, p, p, p, u32]),
         "nam_train_step_noalloc": (i32, [p, p, p, p, i64, p, p, p, u32]),
         "nam_fp8_calibrate": (i32, [p, p, p, i64, p, p]),
+        "nam_sample": (i32, [p, p, p, i64, p, p, p, p]),
+        "nam_sample_pdf": (i32, [p, p, p, i64, p, p]),
         "nam_now": (C.c_double, []),
         "nam_submit": (i32, [p, p, p]),
         "nam_poll": (i32, [p, u64, p, p]),
@@ -239,6 +241,19 @@ def nam_fp8_calibrate(ctx, mat, q, n, stream=None):
     _check(_lib.nam_fp8_calibrate(ctx, mat, C.byref(qs), int(n), out.ctypes.data, _stream(stream)),
            "nam_fp8_calibrate")
     return out
+
+
+def nam_sample(ctx, mat, q, n, u, wo_out, pdf_out=None, stream=None):
+    """Importance-sample one outgoing direction per query (device arrays)."""
+    qs = make_queries(q)
+    _check(_lib.nam_sample(ctx, mat, C.byref(qs), int(n), ptr(u), ptr(wo_out), ptr(pdf_out), _stream(stream)),
+           "nam_sample")
+
+
+def nam_sample_pdf(ctx, mat, q, n, pdf_out, stream=None):
+    """Proxy density of each query's wo given its wi (device arrays)."""
+    qs = make_queries(q)
+    _check(_lib.nam_sample_pdf(ctx, mat, C.byref(qs), int(n), ptr(pdf_out), _stream(stream)), "nam_sample_pdf")
 
 
 def nam_eval_host(ctx, mat, q, n, rgb_out, stream=None, flags=0):

@@ -171,6 +171,7 @@ static void free_material(nam_ctx* ctx, nam_material m) {
   cudaFree(m->pyramid);
   cudaFree(m->blob);
   cudaFree(m->params);
+  cudaFree(m->sampler);
   cudaFree(m->adam_m);
   cudaFree(m->adam_v);
   cudaFree(m->grad);
@@ -253,6 +254,9 @@ nam_status nam::validate_desc(const nam_material_desc* d, Shape* shape, PyrDesc*
       if (!(d->fp8_act_scale[l] > 0.0f) || !std::isfinite(d->fp8_act_scale[l]))
         return fail(NAM_ERR_INVALID_ARG, "fp8_act_scale[%d] must be finite and > 0", l);
   }
+  if (d->sampler_hidden != 0 && d->sampler_hidden != 32)
+    return fail(NAM_ERR_UNSUPPORTED, "sampler_hidden must be 0 or 32");
+  if (d->sampler_hidden && !d->sampler_weights) return fail(NAM_ERR_INVALID_ARG, "sampler_weights is NULL");
   shape->H = H;
   shape->NH = d->n_layers - 1;
   shape->frame = d->frame_hidden ? 1 : 0;
@@ -294,6 +298,13 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   cudaMemcpy(master.data() + nframe, d->decoder_weights, (np - nframe) * 4, kind);
   for (float v : master)
     if (!std::isfinite(v)) return fail(NAM_ERR_INVALID_ARG, "non-finite weight");
+  std::vector<float> smp;
+  if (d->sampler_hidden) {
+    smp.resize(kSamplerFloats);
+    cudaMemcpy(smp.data(), d->sampler_weights, kSamplerFloats * 4, kind);
+    for (float v : smp)
+      if (!std::isfinite(v)) return fail(NAM_ERR_INVALID_ARG, "non-finite sampler weight");
+  }
 
   nam_material m = new nam_material_s();
   m->desc = *d;
@@ -310,7 +321,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
       return fail(NAM_ERR_UNSUPPORTED, "no tensor-core kernel for this shape/precision");
     }
   }
-  uint64_t resident = pyr_bytes + blob_bytes + (uint64_t)np * 4;
+  uint64_t resident = pyr_bytes + blob_bytes + (uint64_t)np * 4 + (uint64_t)smp.size() * 4;
   m->pyr_off = (np + 3) / 4 * 4;
   if (d->trainable) {
     // FP32 pyramid masters are the pyramid itself; Adam moments and gradients
@@ -326,6 +337,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   int e = dev_alloc(ctx, &m->pyramid, pyr_bytes);
   if (!e) e = dev_alloc(ctx, (void**)&m->params, np * 4);
   if (!e && blob_bytes) e = dev_alloc(ctx, &m->blob, blob_bytes);
+  if (!e && !smp.empty()) e = dev_alloc(ctx, (void**)&m->sampler, smp.size() * 4);
   if (!e && d->trainable) {
     const size_t nb = (m->pyr_off + pd.texels * 8) * 4;
     e = dev_alloc(ctx, (void**)&m->adam_m, nb);
@@ -339,6 +351,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   e = (int)cudaMemcpy(m->pyramid, d->pyramid, pyr_bytes,
                       d->params_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
   if (!e) e = (int)cudaMemcpy(m->params, master.data(), np * 4, cudaMemcpyHostToDevice);
+  if (!e && !smp.empty()) e = (int)cudaMemcpy(m->sampler, smp.data(), smp.size() * 4, cudaMemcpyHostToDevice);
   if (!e && blob_bytes) {
     std::vector<uint8_t> blob(blob_bytes);
     if (pack_tc_blob(sh, d->precision, nframe ? master.data() : nullptr, master.data() + nframe,
@@ -482,6 +495,37 @@ extern "C" nam_status nam_fp8_calibrate(nam_ctx* ctx, nam_material m, const nam_
   if (e) return cuda_fail(e, "nam_fp8_calibrate");
   for (int l = 0; l < nl; ++l) act_scale_out[l] = h[l] > 0.0f ? h[l] / 448.0f : 1.0f;
   return NAM_OK;
+}
+
+static nam_status sampler_call(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n, int mode,
+                               const float* u, float* wo_out, float* pdf_out, void* stream, const char* who) {
+  if (!ctx || !m || !q) return fail(NAM_ERR_INVALID_ARG, "%s: NULL argument", who);
+  if (n < 0) return fail(NAM_ERR_INVALID_ARG, "%s: n < 0", who);
+  if (!owns(ctx, m)) return fail(NAM_ERR_NOT_FOUND, "%s: unknown material", who);
+  if (!m->sampler) return fail(NAM_ERR_UNSUPPORTED, "%s: the material has no importance sampler", who);
+  if (n == 0) return NAM_OK;
+  if (!q->u || !q->v || !q->lod || !q->wix || !q->wiy || !q->wiz)
+    return fail(NAM_ERR_INVALID_ARG, "%s: NULL query array", who);
+  if (m->desc.filter == NAM_FILTER_STOCHASTIC && !q->xi) return fail(NAM_ERR_INVALID_ARG, "%s: xi is NULL", who);
+  if (mode == 0 && (!q->wox || !q->woy || !q->woz || !pdf_out))
+    return fail(NAM_ERR_INVALID_ARG, "%s: NULL wo or output", who);
+  if (mode == 1 && (!u || !wo_out)) return fail(NAM_ERR_INVALID_ARG, "%s: NULL variates or output", who);
+  DeviceGuard g(ctx->device);
+  LaunchCommon L;
+  fill_launch(ctx, m, q, n, nullptr, 0, &L);
+  int e = launch_sampler(L, m->sampler, mode, u, wo_out, pdf_out, stream);
+  if (e) return cuda_fail(e, who);
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_sample(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n, const float* u,
+                                 float* wo_out, float* pdf_out, void* stream) {
+  return sampler_call(ctx, m, q, n, 1, u, wo_out, pdf_out, stream, "nam_sample");
+}
+
+extern "C" nam_status nam_sample_pdf(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n, float* pdf_out,
+                                     void* stream) {
+  return sampler_call(ctx, m, q, n, 0, nullptr, nullptr, pdf_out, stream, "nam_sample_pdf");
 }
 
 extern "C" nam_status nam_eval_host(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n, float* rgb_out,

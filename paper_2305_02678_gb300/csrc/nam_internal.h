@@ -91,6 +91,12 @@ size_t tc_blob_bytes(const Shape& s, int precision);
 int pack_tc_blob(const Shape& s, int precision, const float* frame, const float* dec,
                  const float* act_scale, uint8_t* out, float* weight_scales_out);
 
+// Importance sampler (11 -> 32 -> 32 -> 32 -> 9 FP32 MLP + proxy density).
+constexpr int kSamplerFloats = (11 * 32 + 32) + 2 * (32 * 32 + 32) + (32 * 9 + 9);
+// mode 0: density of each query's wo; mode 1: sample from u [n][3].
+int launch_sampler(const LaunchCommon& L, const float* sampler, int mode, const float* u, float* wo_out,
+                   float* pdf_out, void* stream);
+
 // Backward / training.
 struct BackwardArgs {
   PyrDesc pyr;

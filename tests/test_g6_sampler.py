@@ -1,0 +1,153 @@
+"""Importance sampling on the GPU (nam_sample, nam_sample_pdf) against the
+oracle's proxy density and sample transform (Sec. 4.3, Appendix A).
+
+FP32 arithmetic on both sides of a well-conditioned comparison: densities
+agree to 1e-4 relative (against max(o, 1e-3 x median)) and sampled directions
+to 1e-4, except where the tie-breaks are decided by rounding: a lobe choice
+u3 within 1e-5 of w_d, a half vector within 1e-2 of grazing (|wo . h| or
+|wi + wo| small, where 1 / (4 |wo . h|) amplifies rounding)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from conftest import to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(seed, n, latent="f16", filt=0):
+    rng = W.rng_streams(seed, 5)
+    W0 = H0 = 256
+    L = 9
+    pyr = W.make_pyramid(rng[0], W0, H0, L, dtype=np.float16 if latent == "f16" else np.float32)
+    model = W.make_model(rng[1], (14, 64, 64, 3), (8, 16, 6))
+    sampler = W.make_mlp(rng[2], (11, 32, 32, 32, 9))
+    q = W.uniform_queries(rng[3], n, 8.0)
+    u = rng[4].random((n, 3)).astype(np.float32)
+    return W0, H0, L, pyr, model, sampler, q, u
+
+
+def _well(q, wo):
+    wi = np.stack([q["wix"], q["wiy"], q["wiz"]], 1).astype(np.float64)
+    s = wi + wo
+    sl = np.linalg.norm(s, axis=1)
+    h = s / np.maximum(sl, 1e-30)[:, None]
+    return (sl > 1e-2) & (np.abs((wo * h).sum(1)) > 1e-2)
+
+
+def _rel(g, o, floor):
+    return np.abs(g - o) / np.maximum(np.abs(o), floor)
+
+
+@pytest.mark.parametrize("latent,filt", [("f16", 0), ("f32", 0), ("f16", 1)])
+def test_pdf_matches_oracle(gctx, oracle, latent, filt):
+    import torch
+    W0, H0, L, pyr, model, sampler, q, _ = _setup(61, 20000, latent, filt)
+    mat = gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], filter=filt, sampler=sampler)
+    out = torch.empty(len(q["u"]), device="cuda")
+    from paper_2305_02678_gb300 import binding as B
+    B.nam_sample_pdf(gctx.h, mat.h, to_device(q), len(q["u"]), out)
+    g = out.cpu().numpy().astype(np.float64)
+    om = oracle.Model(W0, H0, L, pyr, model["frame"], model["decoder"], filter=filt)
+    o = oracle.sampler_pdf(om, sampler, q)
+    wo = np.stack([q["wox"], q["woy"], q["woz"]], 1).astype(np.float64)
+    ok = _well(q, wo)
+    r = _rel(g, o, 1e-3 * np.median(o))
+    print(f"pdf {latent} filt={filt}: max rel {r[ok].max():.2e} over {ok.sum()} of {len(ok)}; all {r.max():.2e}")
+    assert r[ok].max() <= 1e-4
+    assert np.all(np.isfinite(g))
+    mat.destroy()
+    gctx.check()
+
+
+@pytest.mark.parametrize("latent", ["f16", "f32"])
+def test_samples_match_oracle(gctx, oracle, latent):
+    import torch
+    from paper_2305_02678_gb300 import binding as B
+    W0, H0, L, pyr, model, sampler, q, u = _setup(62, 20000, latent)
+    mat = gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], sampler=sampler)
+    n = len(q["u"])
+    wo = torch.empty((n, 3), device="cuda")
+    pdf = torch.empty(n, device="cuda")
+    B.nam_sample(gctx.h, mat.h, to_device(q), n, torch.from_numpy(u).cuda(), wo, pdf)
+    g_wo = wo.cpu().numpy().astype(np.float64)
+    g_pdf = pdf.cpu().numpy().astype(np.float64)
+    om = oracle.Model(W0, H0, L, pyr, model["frame"], model["decoder"])
+    o_wo, o_pdf = oracle.sampler_sample(om, sampler, q, u.astype(np.float64))
+    params = oracle.sampler_params(om, sampler, q)
+    tie = np.abs(u[:, 2] - params[:, 0]) < 1e-5
+    ok = ~tie & _well(q, o_wo)
+    dw = np.abs(g_wo - o_wo).max(1)
+    # the density returned with each sample is the density at the direction
+    # the GPU sampled (a sharp lobe turns the ~1e-7 direction difference into
+    # a larger density difference, which is not an error of the density)
+    qg = dict(q)
+    qg["wox"], qg["woy"], qg["woz"] = (g_wo[:, k].astype(np.float32) for k in range(3))
+    o_pdf_g = oracle.sampler_pdf(om, sampler, qg)
+    r = _rel(g_pdf, o_pdf_g, 1e-3 * np.median(o_pdf_g))
+    print(f"samples {latent}: max |dwo| {dw[ok].max():.2e}, pdf max rel {r[ok].max():.2e}, "
+          f"compared {ok.sum()} of {n}, diffuse share {np.mean(u[:, 2] < params[:, 0]):.2f}")
+    assert dw[ok].max() <= 1e-4
+    assert r[ok].max() <= 1e-4
+    # unit directions everywhere
+    assert np.allclose(np.linalg.norm(g_wo, axis=1), 1.0, atol=1e-5)
+    mat.destroy()
+    gctx.check()
+
+
+def test_gpu_samples_follow_the_density(gctx, oracle):
+    """200,000 GPU samples at one shading point (same uv, lod and wi for all):
+    chi-square of their histogram against the oracle's density."""
+    import torch
+    from scipy import stats
+
+    from paper_2305_02678_gb300 import binding as B
+    W0, H0, L, pyr, model, sampler, q, _ = _setup(63, 1)
+    n = 200000
+    qq = {k: np.repeat(v, n) for k, v in q.items()}
+    u = np.random.default_rng(8).random((n, 3)).astype(np.float32)
+    mat = gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], sampler=sampler)
+    wo = torch.empty((n, 3), device="cuda")
+    B.nam_sample(gctx.h, mat.h, to_device(qq), n, torch.from_numpy(u).cuda(), wo, None)
+    wo = wo.cpu().numpy().astype(np.float64)
+    om = oracle.Model(W0, H0, L, pyr, model["frame"], model["decoder"])
+    p = oracle.sampler_params(om, sampler, q)[0]
+    wi = np.array([q["wix"][0], q["wiy"][0], q["wiz"][0]], np.float64)
+    keep = ((wo + wi)[:, 2] > 0) | (u[:, 2] < p[0])
+    wo = wo[keep]
+    nc, nphi, sub = 12, 24, 40
+    ci = np.clip(((wo[:, 2] + 1) / 2 * nc).astype(int), 0, nc - 1)
+    pi_ = np.clip(((np.arctan2(wo[:, 1], wo[:, 0]) % (2 * np.pi)) / (2 * np.pi) * nphi).astype(int), 0, nphi - 1)
+    obs = np.bincount(ci * nphi + pi_, minlength=nc * nphi).astype(float)
+    c = -1.0 + (np.arange(nc * sub) + 0.5) * 2.0 / (nc * sub)
+    ph = (np.arange(nphi * sub) + 0.5) * 2 * np.pi / (nphi * sub)
+    C, P = np.meshgrid(c, ph, indexing="ij")
+    s = np.sqrt(1 - C * C)
+    d = np.stack([s * np.cos(P), s * np.sin(P), C], -1).reshape(-1, 3)
+    dw = 2.0 / (nc * sub) * 2 * np.pi / (nphi * sub)
+    exp = oracle.proxy_pdf(p, wi, d).reshape(nc, sub, nphi, sub).sum(axis=(1, 3)).ravel() * dw * n
+    m = exp > 20
+    chi2 = ((obs[m] - exp[m]) ** 2 / exp[m]).sum()
+    pval = stats.chi2.sf(chi2, m.sum() - 1)
+    print(f"chi2 {chi2:.1f} over {m.sum()} bins, p = {pval:.3g}")
+    assert pval > 1e-4
+    mat.destroy()
+
+
+def test_sampler_errors(gctx):
+    import torch
+    from paper_2305_02678_gb300 import binding as B
+    W0, H0, L, pyr, model, sampler, q, u = _setup(64, 100)
+    mat = gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"])
+    out = torch.empty(100, device="cuda")
+    with pytest.raises(B.NamError) as e:
+        B.nam_sample_pdf(gctx.h, mat.h, to_device(q), 100, out)
+    assert e.value.status == B.NAM_ERR_UNSUPPORTED
+    mat.destroy()
+    bad = [(np.zeros((16, 11), np.float32), np.zeros(16, np.float32))] + sampler[1:]
+    with pytest.raises(B.NamError):
+        gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], sampler=bad)
+    # n = 0 is a no-op
+    mat2 = gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], sampler=sampler)
+    B.nam_sample(gctx.h, mat2.h, to_device(q), 0, torch.zeros((1, 3), device="cuda"), torch.zeros((1, 3), device="cuda"))
+    mat2.destroy()
