@@ -408,6 +408,10 @@ def run_ours(args):
     sweep4k, outs4k = None, None
     if not args.no_sweep4k:
         sweep4k, outs4k = run_sweep_4k(ctx, dev, stream, flush, args)
+    # ---- importance sampling on the 1080p frame ------------------------------
+    sampling = None
+    if not args.no_sweep:
+        sampling = run_sampling(ctx, dev, stream, flush, w, dq, n, args)
     # ---- training: 2,000 Adam steps on the procedural GGX target ------------
     training = None
     if args.train_steps > 0 and rank == 0:
@@ -440,6 +444,7 @@ def run_ours(args):
             "roofline": roofline,
             "precision_sweep": sweep,
             "precision_sweep_3840x2160": sweep4k,
+            "importance_sampling": sampling,
             "training": training,
             "serving": serving,
             "cpu_baseline": cpu,
@@ -490,6 +495,42 @@ def run_sweep_4k(ctx, dev, stream, flush, args):
     for mat in mats.values():
         mat.destroy()
     return res, {"w": w, "sample": k, "out": host}
+
+
+def run_sampling(ctx, dev, stream, flush, w, dq, n, args):
+    """nam_sample (direction + density) and nam_sample_pdf over the 1080p
+    frame with a seeded 11-32-32-32-9 sampler network, L2 flushed before each
+    timed launch.  Roofline: FP32 FMA issue, 2 x 2,688 MAC per query for the
+    network, against 152 SMs x 128 FP32 lanes x 2 FLOP x the SM clock."""
+    import torch
+
+    import workloads as W
+    from paper_2305_02678_gb300 import binding as B
+    m = w["model"]
+    rng = W.rng_streams(W.SEEDS[2] + 11, 2)
+    sampler = W.make_mlp(rng[0], (11, 32, 32, 32, 9))
+    mat = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"], precision=B.NAM_PREC_F16,
+                       sampler=sampler)
+    u = torch.from_numpy(rng[1].random((n, 3)).astype(np.float32)).to(dev)
+    wo = torch.empty((n, 3), device=dev)
+    pdf = torch.empty(n, device=dev)
+    steps = max(3, args.steps // 2)
+    t_s = statistics.fmean(time_launches(lambda: B.nam_sample(ctx.h, mat.h, dq, n, u, wo, pdf, stream), steps, 2,
+                                         flush, stream))
+    t_p = statistics.fmean(time_launches(lambda: B.nam_sample_pdf(ctx.h, mat.h, dq, n, pdf, stream), steps, 2, flush,
+                                         stream))
+    mat.destroy()
+    ctx.check()
+    flops = 2 * 2688 * n
+    sm_clock = 2.07e9
+    peak = 152 * 128 * 2 * sm_clock / 1e12
+    return {"workload": "fp16-2048sq-1920x1080 + sampler 11-32-32-32-9 (FP32)", "queries": n,
+            "sample_ms": round(t_s, 4), "samples_per_s": round(n / (t_s * 1e-3), 1),
+            "pdf_ms": round(t_p, 4), "pdf_evals_per_s": round(n / (t_p * 1e-3), 1),
+            "roofline": {"bound": "alu", "achieved": round(flops / (t_s * 1e-3) / 1e12, 2), "unit": "TFLOP/s",
+                         "peak": round(peak, 1), "frac": round(flops / (t_s * 1e-3) / 1e12 / peak, 3),
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (non-tensor FMA)",
+                         "alg_flops_per_launch": flops}}
 
 
 def run_training(ctx, dev, stream, steps, batch=262144, pool=8):
