@@ -149,6 +149,9 @@ typedef struct {
   const double* frame_params; /* Wf1[h][8], bf1[h], Wf2[6][h], bf2[6] */
   const double* dec_params;   /* per layer W[out][in] then b[out] */
   const double* act_scale;    /* act_round == 2: input scale s_l of each decoder layer */
+  int32_t frame_form;         /* 0: frame MLP 8 -> h -> 6 with Gram-Schmidt (frame_hidden > 0);
+                                 1: the paper's form, one linear layer 8 -> 12 giving two frames
+                                 (frame_params = Wf[12][8], bf[12]; decoder widths[0] = 20) */
 } orc_model;
 
 typedef struct {
@@ -313,8 +316,10 @@ typedef struct {
   double z[ORC_C];        /* filtered latent */
   double hf_pre[ORC_MAXW];
   double hf[ORC_MAXW];
-  double r[6];
+  double r[12];
   frame_state fr;
+  double pf_n[2][3], pf_t[2][3], pf_b[2][3]; /* paper form: the two frames */
+  double pf_nl[2], pf_tl[2], pf_sin[2];
   double wi[3], wo[3];
   double pre[ORC_MAXL][ORC_MAXW]; /* decoder pre-activations */
   double act[ORC_MAXL + 1][ORC_MAXW]; /* decoder layer inputs, act[0] = x */
@@ -421,6 +426,45 @@ static double round_act_ctx(const orc_model* m, double x, double A, int dec_laye
   return nominal * scale;
 }
 
+/* The paper's frame form (Sec. 4.2, Eq. 4; Sec. 9): one linear layer maps z
+ * to N = 2 (normal, tangent) pairs; each is normalised, not orthogonalised,
+ * and b = n x t / |n x t|.  Readings for degenerate outputs: |n_raw| < 1e-20
+ * gives n = (0,0,1); |t_raw| < 1e-20, or n and t parallel (|n x t| <= 1e-6),
+ * takes t from n by Duff et al.'s basis. */
+static void paper_frames(const orc_model* m, trace* tr) {
+  const double* Wf = m->frame_params;
+  const double* bf = Wf + 12 * ORC_C;
+  for (int j = 0; j < 12; ++j) {
+    double s = bf[j];
+    for (int c = 0; c < ORC_C; ++c) s += Wf[j * ORC_C + c] * tr->z[c];
+    tr->r[j] = s;
+  }
+  for (int k = 0; k < 2; ++k) {
+    const double* nr = tr->r + 6 * k;
+    const double* trw = tr->r + 6 * k + 3;
+    double* n = tr->pf_n[k];
+    double* t = tr->pf_t[k];
+    double* b = tr->pf_b[k];
+    double nl = sqrt(dot3(nr, nr)), tl = sqrt(dot3(trw, trw));
+    tr->pf_nl[k] = nl;
+    tr->pf_tl[k] = tl;
+    if (nl >= 1e-20) for (int a = 0; a < 3; ++a) n[a] = nr[a] / nl;
+    else { n[0] = 0; n[1] = 0; n[2] = 1; }
+    if (tl >= 1e-20) for (int a = 0; a < 3; ++a) t[a] = trw[a] / tl;
+    else basis_tangent(n, t);
+    double c[3];
+    cross3(n, t, c);
+    double cl = sqrt(dot3(c, c));
+    tr->pf_sin[k] = cl;
+    if (!(cl > 1e-6)) {
+      basis_tangent(n, t);
+      cross3(n, t, c);
+      cl = sqrt(dot3(c, c));
+    }
+    for (int a = 0; a < 3; ++a) b[a] = c[a] / cl;
+  }
+}
+
 static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trace* tr, round_ctx* rc,
                        double kappa) {
   double u = q->u[i], v = q->v[i], lod = q->lod[i];
@@ -432,8 +476,20 @@ static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trac
   tr->wi[0] = q->wix[i]; tr->wi[1] = q->wiy[i]; tr->wi[2] = q->wiz[i];
   tr->wo[0] = q->wox[i]; tr->wo[1] = q->woy[i]; tr->wo[2] = q->woz[i];
 
-  double wi_l[3], wo_l[3];
-  if (m->frame_hidden > 0) {
+  double wi_l[6], wo_l[6];
+  int nd = 3;  /* transformed components per direction */
+  if (m->frame_form == 1) {
+    paper_frames(m, tr);
+    nd = 6;
+    for (int k = 0; k < 2; ++k) {
+      wi_l[3 * k + 0] = dot3(tr->pf_t[k], tr->wi);
+      wi_l[3 * k + 1] = dot3(tr->pf_b[k], tr->wi);
+      wi_l[3 * k + 2] = dot3(tr->pf_n[k], tr->wi);
+      wo_l[3 * k + 0] = dot3(tr->pf_t[k], tr->wo);
+      wo_l[3 * k + 1] = dot3(tr->pf_b[k], tr->wo);
+      wo_l[3 * k + 2] = dot3(tr->pf_n[k], tr->wo);
+    }
+  } else if (m->frame_hidden > 0) {
     int H = m->frame_hidden;
     const double* Wf1 = m->frame_params;
     const double* bf1 = Wf1 + H * ORC_C;
@@ -456,7 +512,8 @@ static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trac
   } else {
     for (int k = 0; k < 3; ++k) { wi_l[k] = tr->wi[k]; wo_l[k] = tr->wo[k]; }
   }
-  /* decoder input order: z0..z7, wi', wo' */
+  /* decoder input order: z0..z7, wi', wo' (paper form: T wi = (t1, b1, n1,
+   * t2, b2, n2) . wi, then T wo) */
   double* x = tr->act[0];
   for (int c = 0; c < ORC_C; ++c) {
     double A = 0.0;
@@ -466,9 +523,9 @@ static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trac
   /* directions: FP32 transform by an FP32 frame whose error grows with the
    * frame's condition number */
   const double Ad = 3.0 + 8.0 * kappa;
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < nd; ++k) {
     x[ORC_C + k] = round_act_ctx(m, wi_l[k], Ad, 0, ORC_C + k, rc);
-    x[ORC_C + 3 + k] = round_act_ctx(m, wo_l[k], Ad, 0, ORC_C + 3 + k, rc);
+    x[ORC_C + nd + k] = round_act_ctx(m, wo_l[k], Ad, 0, ORC_C + nd + k, rc);
   }
 
   const double* p = m->dec_params;
@@ -633,6 +690,7 @@ double orc_loss(const double* g, const float* y, int64_t n, double* dldg_out) {
  * degenerate n is a constant; the fallback tangent depends on n only). */
 void orc_grad(const orc_model* m, const orc_queries* q, int64_t n, const double* dl_dy,
               double* g_frame, double* g_dec, double* g_pyr) {
+  if (m->frame_form == 1) return; /* reverse mode of the paper's frame form is not built */
   trace* tr = (trace*)malloc(sizeof(trace));
   orc_model mm = *m;
   mm.act_round = 0;
@@ -766,6 +824,27 @@ void orc_relu_pattern(const orc_model* m, const orc_queries* q, int64_t n, uint6
  * ill-conditioned queries (where any finite-precision evaluation of the
  * method departs from the exact result) from the rest. */
 static double frame_kappa(const orc_model* m, const trace* tr) {
+  if (m->frame_form == 1) {
+    /* each frame: relative rounding of n_raw, t_raw over 1 / sin(n, t) */
+    const double* Wf = m->frame_params;
+    const double* bf = Wf + 12 * ORC_C;
+    double kmax = 1.0;
+    for (int k = 0; k < 2; ++k) {
+      double a[6];
+      for (int j = 0; j < 6; ++j) {
+        double s = fabs(bf[6 * k + j]);
+        for (int c = 0; c < ORC_C; ++c) s += fabs(Wf[(6 * k + j) * ORC_C + c] * tr->z[c]);
+        a[j] = s;
+      }
+      double An = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+      double At = sqrt(a[3] * a[3] + a[4] * a[4] + a[5] * a[5]);
+      double rn = An / tr->pf_nl[k], rt = At / tr->pf_tl[k];
+      double kk = (rn > rt ? rn : rt) / tr->pf_sin[k];
+      if (!isfinite(kk)) kk = 1e300;
+      if (kk > kmax) kmax = kk;
+    }
+    return kmax;
+  }
   if (m->frame_hidden <= 0) return 1.0;
   int H = m->frame_hidden;
   const double* Wf1 = m->frame_params;
@@ -794,7 +873,7 @@ void orc_frame_condition(const orc_model* m, const orc_queries* q, int64_t n, do
   orc_model mm = *m;
   mm.act_round = 0;
   for (int64_t i = 0; i < n; ++i) {
-    if (m->frame_hidden <= 0) { kappa_out[i] = 1.0; continue; }
+    if (m->frame_hidden <= 0 && m->frame_form != 1) { kappa_out[i] = 1.0; continue; }
     forward(&mm, q, i, tr);
     kappa_out[i] = frame_kappa(m, tr);
   }
@@ -829,7 +908,7 @@ static void* alt_worker(void* arg) {
     double* o = j->out + i * ORC_MAX_ALT * 3;
     for (int k = 0; k < ORC_MAX_ALT * 3; ++k) o[k] = NAN;
     double kappa = 1.0;
-    if (m->frame_hidden > 0) {
+    if (m->frame_hidden > 0 || m->frame_form == 1) {
       forward(&plain, j->q, i, tr);
       kappa = frame_kappa(m, tr);
     }

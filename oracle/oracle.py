@@ -41,7 +41,7 @@ class _Model(C.Structure):
                 ("out_cosine", C.c_int32), ("frame_hidden", C.c_int32), ("n_layers", C.c_int32),
                 ("widths", C.c_int32 * (MAXL + 1)), ("act_round", C.c_int32),
                 ("pyramid", C.c_void_p), ("frame_params", C.c_void_p),
-                ("dec_params", C.c_void_p), ("act_scale", C.c_void_p)]
+                ("dec_params", C.c_void_p), ("act_scale", C.c_void_p), ("frame_form", C.c_int32)]
 
 
 class _Queries(C.Structure):
@@ -156,8 +156,12 @@ class Model:
         self.decoder = decoder
         self.widths = [decoder[0][0].shape[1]] + [W.shape[0] for W, _ in decoder]
         self.weight_scales = None
+        # frame: [(Wf1, bf1), (Wf2, bf2)] = the MLP form 8 -> h -> 6 with
+        # Gram-Schmidt; [(Wf, bf)] with Wf [12][8] = the paper's form (one
+        # linear layer, two frames, decoder input width 20)
+        self.frame_form = 1 if (frame is not None and len(frame) == 1) else 0
         if frame is not None:
-            fp = np.concatenate([frame[0][0].ravel(), frame[0][1], frame[1][0].ravel(), frame[1][1]])
+            fp = np.concatenate([np.concatenate([W.ravel(), b]) for W, b in frame])
             fp = fp.astype(np.float64)
             if params in ("fp16", "fp8"):
                 fp = round_f16(fp)
@@ -185,7 +189,8 @@ class Model:
         s.address = address
         s.filter = filter
         s.out_cosine = int(bool(out_cosine))
-        s.frame_hidden = 0 if frame is None else frame[0][0].shape[0]
+        s.frame_hidden = 0 if (frame is None or self.frame_form == 1) else frame[0][0].shape[0]
+        s.frame_form = self.frame_form
         s.n_layers = len(decoder)
         for i, w in enumerate(self.widths):
             s.widths[i] = w
@@ -367,6 +372,8 @@ def loss(g, y):
 
 def grad(model: Model, q, dl_dy, with_pyramid=True):
     """Gradients of sum <dl_dy, y> w.r.t. frame params, decoder params, pyramid."""
+    if model.frame_form == 1:
+        raise NotImplementedError("reverse mode of the paper's frame form is not built")
     n = _nq(q)
     dl = np.ascontiguousarray(dl_dy, dtype=np.float64).reshape(n, 3)
     gf = np.zeros(model.n_frame_params(), dtype=np.float64)
