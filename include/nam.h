@@ -100,7 +100,8 @@ nam_status nam_check_device_error(nam_ctx* ctx);
 typedef struct nam_material_s* nam_material;
 
 enum { NAM_LATENT_F32 = 0, NAM_LATENT_F16 = 1 };
-/* Arithmetic of the MLPs.  F32: plain FP32 FMA on CUDA cores, one query per
+/* Arithmetic of the MLPs (FP8: NAM_FRAME_MLP and two hidden layers only).
+ * F32: plain FP32 FMA on CUDA cores, one query per
  * thread.  F16: parameters quantised to binary16 at creation (post-training
  * quantisation, Sec. 5.2), decoder layers on tensor cores with FP16 operands
  * and FP32 accumulation; the frame MLP keeps FP32 accuracy by splitting its
@@ -111,6 +112,7 @@ enum { NAM_LATENT_F32 = 0, NAM_LATENT_F16 = 1 };
 enum { NAM_PREC_F32 = 0, NAM_PREC_F16 = 1, NAM_PREC_FP8 = 2 };
 enum { NAM_FILTER_TRILINEAR = 0, NAM_FILTER_STOCHASTIC = 1 };
 enum { NAM_ADDRESS_WRAP = 0, NAM_ADDRESS_CLAMP = 1 };
+enum { NAM_FRAME_MLP = 0, NAM_FRAME_PAPER = 1 };
 
 #define NAM_MAX_LEVELS 16
 #define NAM_MAX_LAYERS 8
@@ -126,16 +128,23 @@ typedef struct {
   int32_t params_on_device;   /* 1: pyramid and weight pointers are device memory */
   const void* pyramid;        /* copied at creation */
 
-  /* frame MLP 8 -> frame_hidden -> 6, ReLU hidden, linear out r = (n_raw,
-   * t_raw).  frame_hidden = 0: no frame MLP, T = I (directions are already
-   * local).  Weights FP32, [Wf1 (h x 8), bf1 (h), Wf2 (6 x h), bf2 (6)],
-   * matrices [out][in] row-major. */
-  int32_t frame_hidden;       /* 0 or 16 */
-  int32_t n_layers;           /* decoder linear layers: 3 (two hidden layers) */
+  /* shading frames (Sec. 4.2).  frame_form NAM_FRAME_MLP: frame MLP 8 ->
+   * frame_hidden -> 6, ReLU hidden, linear out r = (n_raw, t_raw), one frame
+   * by Gram-Schmidt, b = n x t / |n x t|; weights FP32 [Wf1 (h x 8), bf1 (h),
+   * Wf2 (6 x h), bf2 (6)]; frame_hidden = 0: no frame, T = I (directions
+   * are already local).  frame_form NAM_FRAME_PAPER: the paper's single
+   * linear layer 8 -> 12 giving two (normal, tangent) pairs, each
+   * normalised but not orthogonalised, b = n x t / |n x t| (Sec. 4.2, Eq. 4,
+   * Sec. 9); weights [Wf (12 x 8), bf (12)]; frame_hidden must be 0; the
+   * decoder then reads 20 inputs (z, T wi (6), T wo (6)).  Matrices are
+   * [out][in] row-major. */
+  int32_t frame_hidden;       /* 0 or 16 (NAM_FRAME_MLP) */
+  int32_t n_layers;           /* decoder linear layers: 3 (two hidden layers) or
+                                 4 (three hidden layers, H = 64) */
   const float* frame_weights;
-  /* decoder widths[0] = 14, widths[1..n_layers-1] = H (16, 32 or 64, all
-   * equal), widths[n_layers] = 3.  Weights FP32 master values, per layer
-   * W (out x in) then b (out), layers in order. */
+  /* decoder widths[0] = 14 (20 with NAM_FRAME_PAPER), widths[1..n_layers-1]
+   * = H (16, 32 or 64, all equal), widths[n_layers] = 3.  Weights FP32
+   * master values, per layer W (out x in) then b (out), layers in order. */
   int32_t widths[NAM_MAX_LAYERS + 1];
   const float* decoder_weights;
 
@@ -143,7 +152,8 @@ typedef struct {
   int32_t filter;             /* NAM_FILTER_* */
   int32_t address;            /* NAM_ADDRESS_* */
   int32_t trainable;          /* 1: keep FP32 masters on the device for
-                                 nam_backward / nam_train_step (F32 only) */
+                                 nam_backward / nam_train_step (F32 only;
+                                 NAM_FRAME_MLP, two hidden layers) */
   const float* fp8_act_scale; /* NAM_PREC_FP8: host array, input scale of
                                  each decoder layer (n_layers values > 0) */
   /* importance sampler (Sec. 4.3, Appendix A): an MLP from (z, wi) to the
@@ -153,6 +163,7 @@ typedef struct {
    * or device memory as params_on_device says), copied at creation. */
   int32_t sampler_hidden;
   const float* sampler_weights;
+  int32_t frame_form;         /* NAM_FRAME_MLP (0) or NAM_FRAME_PAPER (1) */
 } nam_material_desc;
 
 typedef struct {

@@ -24,11 +24,12 @@ def __getattr__(name):
 
 
 def flatten_frame(frame):
-    """[(Wf1, bf1), (Wf2, bf2)] -> FP32 [Wf1, bf1, Wf2, bf2] (matrices [out][in])."""
+    """[(Wf1, bf1), (Wf2, bf2)] (frame MLP) or [(Wf, bf)] (the paper's single
+    12-output layer) -> FP32 [W, b, ...] (matrices [out][in])."""
     if frame is None:
         return None
-    (W1, b1), (W2, b2) = frame
-    return np.ascontiguousarray(np.concatenate([W1.ravel(), b1, W2.ravel(), b2]), dtype=np.float32)
+    return np.ascontiguousarray(np.concatenate([np.concatenate([W.ravel(), b]) for W, b in frame]),
+                                dtype=np.float32)
 
 
 def flatten_decoder(decoder):
@@ -89,7 +90,9 @@ class Material:
         d.params_on_device = 0
         d.pyramid = pyr.ctypes.data
         fr = flatten_frame(frame)
-        d.frame_hidden = 0 if frame is None else frame[0][0].shape[0]
+        paper = frame is not None and len(frame) == 1
+        d.frame_form = B.NAM_FRAME_PAPER if paper else B.NAM_FRAME_MLP
+        d.frame_hidden = 0 if (frame is None or paper) else frame[0][0].shape[0]
         d.frame_weights = None if fr is None else fr.ctypes.data
         widths = [decoder[0][0].shape[1]] + [W.shape[0] for W, _ in decoder]
         d.n_layers = len(decoder)

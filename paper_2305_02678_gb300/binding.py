@@ -26,6 +26,7 @@ NAM_ADDRESS_WRAP, NAM_ADDRESS_CLAMP = 0, 1
 NAM_OUT_COSINE = 1
 NAM_FAULT_NONE, NAM_FAULT_ALLOC, NAM_FAULT_LAUNCH, NAM_FAULT_STALL = 0, 1, 2, 3
 NAM_MAX_LEVELS, NAM_MAX_LAYERS = 16, 8
+NAM_FRAME_MLP, NAM_FRAME_PAPER = 0, 1
 
 QUERY_FIELDS = ("u", "v", "lod", "wix", "wiy", "wiz", "wox", "woy", "woz", "xi")
 
@@ -41,7 +42,8 @@ class nam_material_desc(C.Structure):
                 ("frame_hidden", C.c_int32), ("n_layers", C.c_int32), ("frame_weights", C.c_void_p),
                 ("widths", C.c_int32 * (NAM_MAX_LAYERS + 1)), ("decoder_weights", C.c_void_p),
                 ("precision", C.c_int32), ("filter", C.c_int32), ("address", C.c_int32), ("trainable", C.c_int32),
-                ("fp8_act_scale", C.c_void_p), ("sampler_hidden", C.c_int32), ("sampler_weights", C.c_void_p)]
+                ("fp8_act_scale", C.c_void_p), ("sampler_hidden", C.c_int32), ("sampler_weights", C.c_void_p),
+                ("frame_form", C.c_int32)]
 
 
 class nam_material_info(C.Structure):

@@ -228,18 +228,28 @@ nam_status nam::validate_desc(const nam_material_desc* d, Shape* shape, PyrDesc*
   if (d->latent_dtype != NAM_LATENT_F32 && d->latent_dtype != NAM_LATENT_F16)
     return fail(NAM_ERR_INVALID_ARG, "bad latent dtype %d", d->latent_dtype);
   if (!d->pyramid) return fail(NAM_ERR_INVALID_ARG, "pyramid is NULL");
-  if (d->frame_hidden != 0 && d->frame_hidden != 16)
-    return fail(NAM_ERR_UNSUPPORTED, "frame_hidden must be 0 or 16 (got %d)", d->frame_hidden);
-  if (d->frame_hidden && !d->frame_weights) return fail(NAM_ERR_INVALID_ARG, "frame weights are NULL");
+  if (d->frame_form != NAM_FRAME_MLP && d->frame_form != NAM_FRAME_PAPER)
+    return fail(NAM_ERR_INVALID_ARG, "bad frame_form %d", d->frame_form);
+  const bool paper = d->frame_form == NAM_FRAME_PAPER;
+  if (d->frame_hidden != 0 && (d->frame_hidden != 16 || paper))
+    return fail(NAM_ERR_UNSUPPORTED, "frame_hidden must be 0 or 16 (0 with the paper's frame form), got %d",
+                d->frame_hidden);
+  if ((d->frame_hidden || paper) && !d->frame_weights) return fail(NAM_ERR_INVALID_ARG, "frame weights are NULL");
   if (!d->decoder_weights) return fail(NAM_ERR_INVALID_ARG, "decoder weights are NULL");
-  if (d->n_layers != 3)
-    return fail(NAM_ERR_UNSUPPORTED, "n_layers must be 3: two hidden layers (got %d)", d->n_layers);
+  if (d->n_layers != 3 && d->n_layers != 4)
+    return fail(NAM_ERR_UNSUPPORTED, "n_layers must be 3 or 4: two or three hidden layers (got %d)", d->n_layers);
   const int H = d->widths[1];
-  if (d->widths[0] != 14 || d->widths[d->n_layers] != 3)
-    return fail(NAM_ERR_UNSUPPORTED, "decoder must map 14 inputs to 3 outputs");
+  const int in = paper ? 20 : 14;
+  if (d->widths[0] != in || d->widths[d->n_layers] != 3)
+    return fail(NAM_ERR_UNSUPPORTED, "decoder must map %d inputs to 3 outputs", in);
   for (int l = 1; l < d->n_layers; ++l)
     if (d->widths[l] != H) return fail(NAM_ERR_UNSUPPORTED, "hidden widths must be equal");
   if (H != 16 && H != 32 && H != 64) return fail(NAM_ERR_UNSUPPORTED, "hidden width %d not in {16, 32, 64}", H);
+  if (d->n_layers == 4 && H != 64) return fail(NAM_ERR_UNSUPPORTED, "three hidden layers need H = 64");
+  if (d->precision == NAM_PREC_FP8 && (paper || d->n_layers != 3))
+    return fail(NAM_ERR_UNSUPPORTED, "FP8 needs the frame MLP form and two hidden layers");
+  if (d->trainable && (paper || d->n_layers != 3))
+    return fail(NAM_ERR_UNSUPPORTED, "training needs the frame MLP form and two hidden layers");
   if (d->precision < NAM_PREC_F32 || d->precision > NAM_PREC_FP8)
     return fail(NAM_ERR_INVALID_ARG, "bad precision %d", d->precision);
   if (d->filter != NAM_FILTER_TRILINEAR && d->filter != NAM_FILTER_STOCHASTIC)
@@ -259,7 +269,8 @@ nam_status nam::validate_desc(const nam_material_desc* d, Shape* shape, PyrDesc*
   if (d->sampler_hidden && !d->sampler_weights) return fail(NAM_ERR_INVALID_ARG, "sampler_weights is NULL");
   shape->H = H;
   shape->NH = d->n_layers - 1;
-  shape->frame = d->frame_hidden ? 1 : 0;
+  shape->frame = paper ? 2 : (d->frame_hidden ? 1 : 0);
+  shape->in = in;
   std::memset(pyr, 0, sizeof *pyr);
   pyr->levels = d->levels;
   pyr->f16 = d->latent_dtype == NAM_LATENT_F16;
@@ -291,7 +302,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   const size_t pyr_bytes = (size_t)pd.texels * texel_bytes;
   const int64_t np = n_params_of(sh);
   // host copies of the FP32 masters (the descriptor may point to device memory)
-  const int64_t nframe = sh.frame ? 246 : 0;
+  const int64_t nframe = frame_params_of(sh.frame);
   std::vector<float> master((size_t)np);
   cudaMemcpyKind kind = d->params_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
   if (nframe) cudaMemcpy(master.data(), d->frame_weights, nframe * 4, kind);
@@ -630,7 +641,7 @@ nam_status nam::check_multi(nam_ctx* ctx, const nam_material* mats, int32_t nmat
     const nam_material m = mats[k];
     if (m->desc.precision == NAM_PREC_F32) return fail(NAM_ERR_UNSUPPORTED, "multi-material launches use the tensor-core path");
     if (m->desc.precision != m0->desc.precision || m->shape.H != m0->shape.H || m->shape.NH != m0->shape.NH ||
-        m->shape.frame != m0->shape.frame)
+        m->shape.frame != m0->shape.frame || m->shape.in != m0->shape.in)
       return fail(NAM_ERR_INVALID_ARG, "materials must share precision and MLP shape");
     if (std::memcmp(&m->pyr, &m0->pyr, sizeof(PyrDesc)) != 0)
       return fail(NAM_ERR_INVALID_ARG, "materials must share pyramid geometry, dtype, filter and addressing");

@@ -252,6 +252,48 @@ __device__ __forceinline__ Frame build_frame(const float r[6]) {
   return F;
 }
 
+// One frame of the paper's form (Sec. 4.2, Eq. 4; Sec. 9) from r = (n_raw,
+// t_raw): n and t normalised but not orthogonalised, b = n x t / |n x t|.
+// Degenerate outputs: |n_raw|^2 < 1e-40 -> n = (0,0,1); |t_raw|^2 < 1e-40, or
+// |n x t|^2 <= 1e-12 (parallel), -> t from n by Duff et al.'s basis.
+__device__ __forceinline__ Frame paper_frame(const float r[6]) {
+  Frame F;
+  const float nl2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+  if (!(nl2 >= 1e-40f)) {
+    F.n[0] = 0.0f; F.n[1] = 0.0f; F.n[2] = 1.0f;
+  } else {
+    const float inv = rsqrtf(nl2);
+    F.n[0] = r[0] * inv; F.n[1] = r[1] * inv; F.n[2] = r[2] * inv;
+  }
+  const float tl2 = r[3] * r[3] + r[4] * r[4] + r[5] * r[5];
+  bool basis = !(tl2 >= 1e-40f);
+  if (!basis) {
+    const float inv = rsqrtf(tl2);
+    F.t[0] = r[3] * inv; F.t[1] = r[4] * inv; F.t[2] = r[5] * inv;
+  }
+  float c0 = 0.0f, c1 = 0.0f, c2 = 0.0f;
+  if (!basis) {
+    c0 = F.n[1] * F.t[2] - F.n[2] * F.t[1];
+    c1 = F.n[2] * F.t[0] - F.n[0] * F.t[2];
+    c2 = F.n[0] * F.t[1] - F.n[1] * F.t[0];
+    basis = !(c0 * c0 + c1 * c1 + c2 * c2 > 1e-12f);
+  }
+  if (basis) {
+    const float sg = copysignf(1.0f, F.n[2]);
+    const float a = -1.0f / (sg + F.n[2]);
+    const float bb = F.n[0] * F.n[1] * a;
+    F.t[0] = 1.0f + sg * F.n[0] * F.n[0] * a;
+    F.t[1] = sg * bb;
+    F.t[2] = -sg * F.n[0];
+    c0 = F.n[1] * F.t[2] - F.n[2] * F.t[1];
+    c1 = F.n[2] * F.t[0] - F.n[0] * F.t[2];
+    c2 = F.n[0] * F.t[1] - F.n[1] * F.t[0];
+  }
+  const float inv = rsqrtf(c0 * c0 + c1 * c1 + c2 * c2);
+  F.b[0] = c0 * inv; F.b[1] = c1 * inv; F.b[2] = c2 * inv;
+  return F;
+}
+
 __device__ __forceinline__ void to_local(const Frame& F, float x, float y, float z, float out[3]) {
   out[0] = F.t[0] * x + F.t[1] * y + F.t[2] * z;
   out[1] = F.b[0] * x + F.b[1] * y + F.b[2] * z;

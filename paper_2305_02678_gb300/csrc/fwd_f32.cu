@@ -9,44 +9,49 @@
 namespace nam {
 
 int64_t n_params_of(const Shape& s) {
-  int64_t n = 0;
-  if (s.frame) n += 16 * 8 + 16 + 6 * 16 + 6;
-  n += (int64_t)14 * s.H + s.H;
+  int64_t n = frame_params_of(s.frame);
+  n += (int64_t)s.in * s.H + s.H;
   for (int i = 1; i < s.NH; ++i) n += (int64_t)s.H * s.H + s.H;
   n += 3 * s.H + 3;
   return n;
 }
 
 // Shared-memory image of the parameters, rows padded for 16-byte loads.
-template <int H, int NH>
+// FK: frame form (0 none, 1 MLP 8-16-6, 2 the paper's linear 8 -> 12);
+// INP: decoder input row length (14 inputs padded to 16, or 20).
+template <int H, int NH, int FK, int INP>
 struct SmemF32 {
-  float fW1[16 * 8];
+  float fW1[FK == 2 ? 12 * 8 : 16 * 8];  // FK 1: Wf1 [16][8]; FK 2: Wf [12][8]
   float fb1[16];
   float fW2[6 * 16];
   float fb2[8];
-  float W1[H * 16];        // [H][16], inputs 14, 15 are zero
+  float W1[H * INP];        // [H][INP], inputs past the decoder's width are zero
   float b1[H];
-  float Wh[NH - 1][H * H]; // hidden -> hidden
+  float Wh[NH - 1][H * H];  // hidden -> hidden
   float bh[NH - 1][H];
-  float WoT[H * 4];        // output weights transposed [H][4]
+  float WoT[H * 4];         // output weights transposed [H][4]
   float bo[4];
 };
 
-template <int H, int NH>
-__device__ void load_params_f32(SmemF32<H, NH>& S, const float* __restrict__ p, bool frame) {
+template <int H, int NH, int FK, int INP>
+__device__ void load_params_f32(SmemF32<H, NH, FK, INP>& S, const float* __restrict__ p, int in) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  if (frame) {
+  if (FK == 1) {
     for (int i = tid; i < 128; i += nt) S.fW1[i] = p[i];
     for (int i = tid; i < 16; i += nt) S.fb1[i] = p[128 + i];
     for (int i = tid; i < 96; i += nt) S.fW2[i] = p[144 + i];
     for (int i = tid; i < 8; i += nt) S.fb2[i] = i < 6 ? p[240 + i] : 0.0f;
     p += 246;
+  } else if (FK == 2) {
+    for (int i = tid; i < 96; i += nt) S.fW1[i] = p[i];
+    for (int i = tid; i < 16; i += nt) S.fb1[i] = i < 12 ? p[96 + i] : 0.0f;
+    p += 108;
   }
-  for (int i = tid; i < H * 16; i += nt) {
-    int j = i >> 4, k = i & 15;
-    S.W1[i] = k < 14 ? p[j * 14 + k] : 0.0f;
+  for (int i = tid; i < H * INP; i += nt) {
+    int j = i / INP, k = i % INP;
+    S.W1[i] = k < in ? p[j * in + k] : 0.0f;
   }
-  p += 14 * H;
+  p += in * H;
   for (int i = tid; i < H; i += nt) S.b1[i] = p[i];
   p += H;
   for (int l = 0; l < NH - 1; ++l) {
@@ -78,11 +83,12 @@ __device__ __forceinline__ float dot_row(const float* __restrict__ row, const fl
   return s0 + s1;
 }
 
-template <int H, int NH, bool FRAME, bool F16>
+template <int H, int NH, int FK, bool F16>
 __global__ void __launch_bounds__(128) eval_f32_kernel(LaunchCommon L) {
+  constexpr int INP = FK == 2 ? 20 : 16;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  SmemF32<H, NH>& S = *reinterpret_cast<SmemF32<H, NH>*>(smem_raw);
-  load_params_f32<H, NH>(S, reinterpret_cast<const float*>(L.w0), FRAME);
+  SmemF32<H, NH, FK, INP>& S = *reinterpret_cast<SmemF32<H, NH, FK, INP>*>(smem_raw);
+  load_params_f32<H, NH, FK, INP>(S, reinterpret_cast<const float*>(L.w0), FK == 2 ? 20 : 14);
   __syncthreads();
   const QueryPtrs& q = L.q;
   const bool cosine = (L.flags & NAM_OUT_COSINE) != 0;
@@ -95,10 +101,10 @@ __global__ void __launch_bounds__(128) eval_f32_kernel(LaunchCommon L) {
     fetch_latent<F16>(L.pyr, L.pyr0, q.u[i], q.v[i], q.lod[i], xi, z);
     const float wix = q.wix[i], wiy = q.wiy[i], wiz = q.wiz[i];
     const float wox = q.wox[i], woy = q.woy[i], woz = q.woz[i];
-    float x[16];
+    float x[INP];
 #pragma unroll
     for (int c = 0; c < 8; ++c) x[c] = z[c];
-    if (FRAME) {
+    if constexpr (FK == 1) {
       float hf[16];
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
@@ -113,18 +119,34 @@ __global__ void __launch_bounds__(128) eval_f32_kernel(LaunchCommon L) {
       Frame F = build_frame(r);
       to_local(F, wix, wiy, wiz, x + 8);
       to_local(F, wox, woy, woz, x + 11);
+    } else if constexpr (FK == 2) {
+      float r[12];
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        float s = S.fb1[j];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s = fmaf(S.fW1[j * 8 + c], z[c], s);
+        r[j] = s;
+      }
+      Frame F1 = paper_frame(r), F2 = paper_frame(r + 6);
+      to_local(F1, wix, wiy, wiz, x + 8);
+      to_local(F2, wix, wiy, wiz, x + 11);
+      to_local(F1, wox, woy, woz, x + 14);
+      to_local(F2, wox, woy, woz, x + 17);
     } else {
       x[8] = wix; x[9] = wiy; x[10] = wiz;
       x[11] = wox; x[12] = woy; x[13] = woz;
     }
-    x[14] = 0.0f;
-    x[15] = 0.0f;
+    if constexpr (FK != 2) {
+      x[14] = 0.0f;
+      x[15] = 0.0f;
+    }
     float h1[H];
 #pragma unroll
-    for (int j = 0; j < H; ++j) h1[j] = fmaxf(S.b1[j] + dot_row<16>(&S.W1[j * 16], x), 0.0f);
+    for (int j = 0; j < H; ++j) h1[j] = fmaxf(S.b1[j] + dot_row<INP>(&S.W1[j * INP], x), 0.0f);
     if (calib) {
 #pragma unroll
-      for (int c = 0; c < 14; ++c) am0 = fmaxf(am0, fabsf(x[c]));
+      for (int c = 0; c < INP; ++c) am0 = fmaxf(am0, fabsf(x[c]));
 #pragma unroll
       for (int j = 0; j < H; ++j) am1 = fmaxf(am1, h1[j]);
     }
@@ -141,7 +163,7 @@ __global__ void __launch_bounds__(128) eval_f32_kernel(LaunchCommon L) {
       }
     } else {
       float h2[H];
-#pragma unroll
+#pragma unroll 4
       for (int j = 0; j < H; ++j) h2[j] = fmaxf(S.bh[0][j] + dot_row<H>(&S.Wh[0][j * H], h1), 0.0f);
 #pragma unroll 4
       for (int j = 0; j < H; ++j) {
@@ -177,10 +199,10 @@ __global__ void __launch_bounds__(128) eval_f32_kernel(LaunchCommon L) {
   }
 }
 
-template <int H, int NH, bool FRAME, bool F16>
+template <int H, int NH, int FK, bool F16>
 static int launch_one(const LaunchCommon& L, cudaStream_t s) {
-  auto k = eval_f32_kernel<H, NH, FRAME, F16>;
-  const int smem = (int)sizeof(SmemF32<H, NH>);
+  auto k = eval_f32_kernel<H, NH, FK, F16>;
+  const int smem = (int)sizeof(SmemF32<H, NH, FK, FK == 2 ? 20 : 16>);
   static int occ = -1;  // per instantiation
   if (occ < 0) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -196,10 +218,12 @@ static int launch_one(const LaunchCommon& L, cudaStream_t s) {
 
 template <int H, int NH>
 static int dispatch_frame(const LaunchCommon& L, cudaStream_t s) {
-  if (L.shape.frame) {
-    return L.pyr.f16 ? launch_one<H, NH, true, true>(L, s) : launch_one<H, NH, true, false>(L, s);
+  const bool f16 = L.pyr.f16;
+  switch (L.shape.frame) {
+    case 1: return f16 ? launch_one<H, NH, 1, true>(L, s) : launch_one<H, NH, 1, false>(L, s);
+    case 2: return f16 ? launch_one<H, NH, 2, true>(L, s) : launch_one<H, NH, 2, false>(L, s);
+    default: return f16 ? launch_one<H, NH, 0, true>(L, s) : launch_one<H, NH, 0, false>(L, s);
   }
-  return L.pyr.f16 ? launch_one<H, NH, false, true>(L, s) : launch_one<H, NH, false, false>(L, s);
 }
 
 int launch_eval_f32(const LaunchCommon& L, void* stream) {
@@ -211,6 +235,7 @@ int launch_eval_f32(const LaunchCommon& L, void* stream) {
     if (sh.H == 32) return dispatch_frame<32, 2>(L, s);
     if (sh.H == 64) return dispatch_frame<64, 2>(L, s);
   }
+  if (sh.NH == 3 && sh.H == 64) return dispatch_frame<64, 3>(L, s);
   return (int)cudaErrorInvalidValue;
 }
 

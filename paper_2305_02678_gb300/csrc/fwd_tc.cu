@@ -43,31 +43,43 @@ __host__ __device__ constexpr int kmajor_off(int R, int row, int k) {
   return (k / 8) * (R * 16) + row * 16 + (k % 8) * 2;
 }
 
-template <int H, bool FRAME>
-struct TcLayout {
-  // weight blob: every bias rides in the MMA as the weight of the constant-1
-  // input column (one extra K step of 16)
-  static constexpr int B_F1 = 0;                          // 16 x 32: [Wf1 | Wf1 | bf1 0..]
-  static constexpr int B_F2 = FRAME ? 1024 : 0;           // 16 x 48: [Wf2 | Wf2 | bf2 0..]
-  static constexpr int B_L1 = FRAME ? 2560 : 0;           // H x 16: [W1 | b1 0]
-  static constexpr int B_L2 = B_L1 + H * 16 * 2;          // H x (H + 16)
-  static constexpr int B_LO = B_L2 + H * (H + 16) * 2;    // 16 x (H + 16)
-  static constexpr int BLOB = B_LO + 16 * (H + 16) * 2;
+// Weight blob offsets (bytes) for hidden width H, frame form FK (0 none,
+// 1 MLP 8-16-6, 2 the paper's linear 8 -> 12) and NH hidden layers.  Every
+// FP16 bias rides in the MMA as the weight of a constant-1 input column.
+struct TcOff {
+  int b_f1, b_f2;  // FK 1: 16 x 32 [Wf1 | Wf1 | bf1 0..], 16 x 48 [Wf2 | Wf2 | bf2 0..]
+                   // FK 2: b_f1 = 16 x 32 [Wf | Wf | bf 0..] (12 rows used)
+  int b_l1, kl1;   // H x kl1: [W1 | b1 0..], kl1 = 16 (14 inputs) or 32 (20 inputs)
+  int b_l2;        // (NH - 1) blocks of H x (H + 16): hidden -> hidden
+  int b_lo;        // 16 x (H + 16): hidden -> RGB (3 rows used)
+  int blob;
 };
+__host__ __device__ constexpr TcOff tc_off(int H, int FK, int NH) {
+  TcOff o{};
+  o.b_f1 = 0;
+  o.b_f2 = 1024;
+  o.b_l1 = FK == 1 ? 2560 : FK == 2 ? 1024 : 0;
+  o.kl1 = FK == 2 ? 32 : 16;
+  o.b_l2 = o.b_l1 + H * o.kl1 * 2;
+  o.b_lo = o.b_l2 + (NH - 1) * H * (H + 16) * 2;
+  o.blob = o.b_lo + 16 * (H + 16) * 2;
+  return o;
+}
 
-// FP8 (E4M3) decoder: the A region and the frame blocks are those of the FP16
-// layout; the decoder's B operands hold E4M3 codes in the canonical K-major
-// layout for 8-bit types (8-row x 16-byte core matrices = 16 codes along K),
-// K padded to the 32 of one kind::f8f6f4 MMA.  The biases stay FP32 and are
-// added in the epilogue together with the per-layer scales:
+// FP8 (E4M3) decoder (frame forms 0 and 1, two hidden layers): the frame
+// blocks are those of the FP16 layout; the decoder's B operands hold E4M3
+// codes in the canonical K-major layout for 8-bit types (8-row x 16-byte core
+// matrices = 16 codes along K), K padded to the 32 of one kind::f8f6f4 MMA.
+// The biases stay FP32 and are added in the epilogue together with the
+// per-layer scales:
 //   next-layer code = E4M3(relu(D * c_l + b'_l)),  c_l = s_l sw_l / s_{l+1},
 //   b'_l = b_l / s_{l+1};  output = D * c_2 + b_2,  c_2 = s_2 sw_2,
 // where D = sum of code products (FP32, in TMEM), s_l the static input scale
 // of decoder layer l and sw_l its weight scale.
-template <int H, bool FRAME>
+template <int H, int FK>
 struct TcLayout8 {
   static constexpr int KP = H < 32 ? 32 : H;              // hidden K padded to one MMA step
-  static constexpr int B_L1 = FRAME ? 2560 : 0;           // H x 32 codes
+  static constexpr int B_L1 = FK ? 2560 : 0;              // H x 32 codes
   static constexpr int B_L2 = B_L1 + H * 32;              // H x KP codes
   static constexpr int B_LO = B_L2 + H * KP;              // 16 x KP codes
   static constexpr int B_SC = (B_LO + 16 * KP + 15) / 16 * 16;  // FP32: inv_s0, c0, c1, c2
@@ -77,23 +89,28 @@ struct TcLayout8 {
   static constexpr int BLOB = B_B3 + 16;
 };
 
-template <int H, bool FRAME>
-static size_t blob_bytes_of(int precision) {
-  return precision == NAM_PREC_FP8 ? (size_t)TcLayout8<H, FRAME>::BLOB : (size_t)TcLayout<H, FRAME>::BLOB;
+template <int H, int FK>
+static size_t blob8_bytes() {
+  return (size_t)TcLayout8<H, FK>::BLOB;
+}
+
+// Shapes with a tensor-core kernel: two hidden layers of 16, 32 or 64, or
+// three of 64; FP8 with frame forms 0 and 1 and two hidden layers.
+static bool tc_supported(const Shape& s, int precision) {
+  if (precision != NAM_PREC_F16 && precision != NAM_PREC_FP8) return false;
+  const bool hidden_ok = (s.NH == 2 && (s.H == 16 || s.H == 32 || s.H == 64)) || (s.NH == 3 && s.H == 64);
+  if (!hidden_ok || s.frame < 0 || s.frame > 2) return false;
+  if (precision == NAM_PREC_FP8 && (s.NH != 2 || s.frame == 2)) return false;
+  return true;
 }
 
 size_t tc_blob_bytes(const Shape& s, int precision) {
-  if ((precision != NAM_PREC_F16 && precision != NAM_PREC_FP8) || s.NH != 2) return 0;
-  if (s.frame) {
-    if (s.H == 16) return blob_bytes_of<16, true>(precision);
-    if (s.H == 32) return blob_bytes_of<32, true>(precision);
-    if (s.H == 64) return blob_bytes_of<64, true>(precision);
-  } else {
-    if (s.H == 16) return blob_bytes_of<16, false>(precision);
-    if (s.H == 32) return blob_bytes_of<32, false>(precision);
-    if (s.H == 64) return blob_bytes_of<64, false>(precision);
-  }
-  return 0;
+  if (!tc_supported(s, precision)) return 0;
+  if (precision == NAM_PREC_F16) return (size_t)tc_off(s.H, s.frame, s.NH).blob;
+  const bool f = s.frame == 1;
+  if (s.H == 16) return f ? blob8_bytes<16, 1>() : blob8_bytes<16, 0>();
+  if (s.H == 32) return f ? blob8_bytes<32, 1>() : blob8_bytes<32, 0>();
+  return f ? blob8_bytes<64, 1>() : blob8_bytes<64, 0>();
 }
 
 static void put_h(uint8_t* base, int R, int row, int k, float v) {
@@ -155,29 +172,34 @@ int pack_tc_blob(const Shape& s, int precision, const float* frame, const float*
   const size_t bytes = tc_blob_bytes(s, precision);
   if (!bytes) return -1;
   std::memset(out, 0, bytes);
-  const int H = s.H;
-  const int B_L1 = s.frame ? 2560 : 0;
-  const int B_L2 = B_L1 + H * 16 * 2;
-  const int B_LO = B_L2 + H * (H + 16) * 2;
-  if (s.frame) {
+  const int H = s.H, IN = s.in;
+  const TcOff o = tc_off(H, s.frame, s.NH);
+  if (s.frame == 1) {
     const float* Wf1 = frame;            // [16][8]
     const float* bf1 = Wf1 + 128;        // [16]
     const float* Wf2 = bf1 + 16;         // [6][16]
     const float* bf2 = Wf2 + 96;         // [6]
     for (int n = 0; n < 16; ++n) {
-      for (int k = 0; k < 16; ++k) put_h(out + 0, 16, n, k, Wf1[n * 8 + (k & 7)]);
-      put_h(out + 0, 16, n, 16, bf1[n]);
+      for (int k = 0; k < 16; ++k) put_h(out + o.b_f1, 16, n, k, Wf1[n * 8 + (k & 7)]);
+      put_h(out + o.b_f1, 16, n, 16, bf1[n]);
     }
     for (int n = 0; n < 6; ++n) {
-      for (int k = 0; k < 32; ++k) put_h(out + 1024, 16, n, k, Wf2[n * 16 + (k & 15)]);
-      put_h(out + 1024, 16, n, 32, bf2[n]);
+      for (int k = 0; k < 32; ++k) put_h(out + o.b_f2, 16, n, k, Wf2[n * 16 + (k & 15)]);
+      put_h(out + o.b_f2, 16, n, 32, bf2[n]);
+    }
+  } else if (s.frame == 2) {
+    const float* Wf = frame;             // [12][8]
+    const float* bf = Wf + 96;           // [12]
+    for (int n = 0; n < 12; ++n) {
+      for (int k = 0; k < 16; ++k) put_h(out + o.b_f1, 16, n, k, Wf[n * 8 + (k & 7)]);
+      put_h(out + o.b_f1, 16, n, 16, bf[n]);
     }
   }
-  const float* W1 = dec;                 // [H][14]
-  const float* b1 = W1 + 14 * H;
-  const float* W2 = b1 + H;              // [H][H]
+  const float* W1 = dec;                 // [H][IN]
+  const float* b1 = W1 + IN * H;
+  const float* W2 = b1 + H;              // [H][H] (then the third layer's, NH = 3)
   const float* b2 = W2 + H * H;
-  const float* W3 = b2 + H;              // [3][H]
+  const float* W3 = b2 + H;              // [3][H] (NH = 2)
   const float* b3 = W3 + 3 * H;
   if (precision == NAM_PREC_FP8) {
     if (!act_scale) return -1;
@@ -203,16 +225,25 @@ int pack_tc_blob(const Shape& s, int precision, const float* frame, const float*
     return 0;
   }
   for (int n = 0; n < H; ++n) {
-    for (int k = 0; k < 14; ++k) put_h(out + B_L1, H, n, k, W1[n * 14 + k]);
-    put_h(out + B_L1, H, n, 14, b1[n]);
+    for (int k = 0; k < IN; ++k) put_h(out + o.b_l1, H, n, k, W1[n * IN + k]);
+    put_h(out + o.b_l1, H, n, IN, b1[n]);
   }
-  for (int n = 0; n < H; ++n) {
-    for (int k = 0; k < H; ++k) put_h(out + B_L2, H, n, k, W2[n * H + k]);
-    put_h(out + B_L2, H, n, H, b2[n]);
+  const float* p = b1 + H;
+  for (int l = 0; l < s.NH - 1; ++l) {
+    const float* Wh = p;
+    const float* bh = Wh + H * H;
+    uint8_t* dst = out + o.b_l2 + l * H * (H + 16) * 2;
+    for (int n = 0; n < H; ++n) {
+      for (int k = 0; k < H; ++k) put_h(dst, H, n, k, Wh[n * H + k]);
+      put_h(dst, H, n, H, bh[n]);
+    }
+    p = bh + H;
   }
+  const float* Wo = p;
+  const float* bo = Wo + 3 * H;
   for (int n = 0; n < 3; ++n) {
-    for (int k = 0; k < H; ++k) put_h(out + B_LO, 16, n, k, W3[n * H + k]);
-    put_h(out + B_LO, 16, n, H, b3[n]);
+    for (int k = 0; k < H; ++k) put_h(out + o.b_lo, 16, n, k, Wo[n * H + k]);
+    put_h(out + o.b_lo, 16, n, H, bo[n]);
   }
   return 0;
 }
@@ -276,17 +307,17 @@ __device__ __forceinline__ QueryIn load_query(const QueryPtrs& q, int64_t i) {
 // a bias step live in TMEM instead of shared memory, which leaves most of the
 // SM's 256 KB of L1/shared storage to the L1 cache that serves the texel
 // gathers.
-template <int H, bool FRAME, bool P8>
+template <int H, int FK, int NH, bool P8>
 struct WgSlot {
-  static constexpr int BLOB = P8 ? TcLayout8<H, FRAME>::BLOB : TcLayout<H, FRAME>::BLOB;
+  static constexpr int BLOB = P8 ? TcLayout8<H, (FK == 1 ? 1 : 0)>::BLOB : tc_off(H, FK, NH).blob;
   static constexpr int BLOB_AL = (BLOB + 127) / 128 * 128;
   static constexpr int A8_BLOCKS = P8 ? ((H / 16) > 1 ? (H / 16) : 1) : 0;  // E4M3 A blocks
   static constexpr int A8_BYTES = P8 ? (A8_BLOCKS + 1) * 2048 : 0;          // + zero block
   static constexpr int BYTES = BLOB_AL + A8_BYTES + 128;                     // + mbarriers
 };
-template <int H, bool FRAME, bool P8, int NWG>
+template <int H, int FK, int NH, bool P8, int NWG>
 __host__ __device__ constexpr int smem_bytes() {
-  return 4096 + NWG * WgSlot<H, FRAME, P8>::BYTES + 16;
+  return 4096 + NWG * WgSlot<H, FK, NH, P8>::BYTES + 16;
 }
 
 // TMEM columns of one warpgroup: FP32 accumulator [0, 64), FP16 A operand
@@ -302,11 +333,12 @@ constexpr int kNwg = 5;
 // its own tiles of 128 queries (thread r = query r = TMEM lane r), with its
 // own TMEM columns, weight copy and mbarriers, so warpgroups never wait for
 // each other.  P8: the decoder in E4M3 (kind::f8f6f4) instead of FP16.
-template <int H, bool FRAME, bool F16P, bool P8, int NWG>
+template <int H, int FK, int NH, bool F16P, bool P8, int NWG>
 __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommon L) {
-  using Lay = TcLayout<H, FRAME>;
-  using Lay8 = TcLayout8<H, FRAME>;
-  using S = WgSlot<H, FRAME, P8>;
+  static_assert(!P8 || (NH == 2 && FK != 2), "FP8: frame forms 0 and 1, two hidden layers");
+  constexpr TcOff O = tc_off(H, FK, NH);
+  using Lay8 = TcLayout8<H, (FK == 1 ? 1 : 0)>;
+  using S = WgSlot<H, FK, NH, P8>;
   constexpr int BLOB = S::BLOB;
   extern __shared__ __align__(1024) uint8_t smem[];
 
@@ -444,8 +476,38 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
       zp[3] = ptx::pack_h2(z[6], z[7]);
     }
 
-    float xl[6];
-    if (FRAME) {
+    float xl[12];
+    if (FK == 2) {
+      // ---- 2'. the paper's frame layer 8 -> 12 at FP32 accuracy -----------
+      {
+        uint32_t v[8];
+        split2(z[0], z[1], v[0], v[4]);
+        split2(z[2], z[3], v[1], v[5]);
+        split2(z[4], z[5], v[2], v[6]);
+        split2(z[6], z[7], v[3], v[7]);
+        ptx::tmem_st8(tAl, v);  // A = (z_hi, z_lo)
+        ptx::tmem_st_wait();
+      }
+      if (!mma_stage([&] {
+            ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + O.b_f1, 256, 128), ID_16, 0);
+            ptx::mma_f16(tD, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + O.b_f1 + 512, 256, 128), ID_16, 1);
+          }))
+        break;
+      {
+        uint32_t acc[16];
+        ptx::tmem_ld16(tDl, acc);
+        ptx::tmem_ld_wait();
+        float rr[12];
+#pragma unroll
+        for (int j = 0; j < 12; ++j) rr[j] = u2f(acc[j]);
+        // ---- 3'. two frames (normalised n, t; b = n x t / |n x t|) --------
+        const Frame F1 = paper_frame(rr), F2 = paper_frame(rr + 6);
+        to_local(F1, qc.wix, qc.wiy, qc.wiz, xl);
+        to_local(F2, qc.wix, qc.wiy, qc.wiz, xl + 3);
+        to_local(F1, qc.wox, qc.woy, qc.woz, xl + 6);
+        to_local(F2, qc.wox, qc.woy, qc.woz, xl + 9);
+      }
+    } else if (FK == 1) {
       // ---- 2. frame MLP at FP32 accuracy (split FP16 operands) -----------
       {
         uint32_t v[8];
@@ -457,8 +519,8 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
         ptx::tmem_st_wait();
       }
       if (!mma_stage([&] {
-            ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + Lay::B_F1, 256, 128), ID_16, 0);
-            ptx::mma_f16(tD, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + Lay::B_F1 + 512, 256, 128), ID_16, 1);
+            ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + O.b_f1, 256, 128), ID_16, 0);
+            ptx::mma_f16(tD, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + O.b_f1 + 512, 256, 128), ID_16, 1);
           }))
         break;
       {
@@ -473,9 +535,9 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
         ptx::tmem_st_wait();
       }
       if (!mma_stage([&] {
-            ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + Lay::B_F2, 256, 128), ID_16, 0);
-            ptx::mma_f16_ts(tD, tA + 8, ptx::sdesc(aW + Lay::B_F2 + 512, 256, 128), ID_16, 1);
-            ptx::mma_f16(tD, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + Lay::B_F2 + 1024, 256, 128), ID_16, 1);
+            ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + O.b_f2, 256, 128), ID_16, 0);
+            ptx::mma_f16_ts(tD, tA + 8, ptx::sdesc(aW + O.b_f2 + 512, 256, 128), ID_16, 1);
+            ptx::mma_f16(tD, ptx::sdesc(aConst, 2048, 128), ptx::sdesc(aW + O.b_f2 + 1024, 256, 128), ID_16, 1);
           }))
         break;
       {
@@ -508,13 +570,39 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
             ptx::mma_f8(tD, ptx::sdesc(aA8, aZ8 - aA8, 128), ptx::sdesc(aW + Lay8::B_L1, H * 16, 128), ID8_H, 0);
           }))
         break;
+    } else if (FK == 2) {
+      // L1 operand: (z, T wi (6), T wo (6), 1, 0...), K = 32; the 1 meets
+      // the bias column of W1
+      uint32_t v[16] = {zp[0],
+                        zp[1],
+                        zp[2],
+                        zp[3],
+                        ptx::pack_h2(xl[0], xl[1]),
+                        ptx::pack_h2(xl[2], xl[3]),
+                        ptx::pack_h2(xl[4], xl[5]),
+                        ptx::pack_h2(xl[6], xl[7]),
+                        ptx::pack_h2(xl[8], xl[9]),
+                        ptx::pack_h2(xl[10], xl[11]),
+                        0x00003C00u,
+                        0u,
+                        0u,
+                        0u,
+                        0u,
+                        0u};
+      ptx::tmem_st16(tAl, v);
+      ptx::tmem_st_wait();
+      if (!mma_stage([&] {
+            ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + O.b_l1, H * 16, 128), ID_H, 0);
+            ptx::mma_f16_ts(tD, tA + 8, ptx::sdesc(aW + O.b_l1 + 2 * H * 16, H * 16, 128), ID_H, 1);
+          }))
+        break;
     } else {
       // L1 operand: (z, wi', wo', 1, 0); the 1 meets the bias column of W1
       uint32_t v[8] = {zp[0], zp[1], zp[2], zp[3], ptx::pack_h2(xl[0], xl[1]), ptx::pack_h2(xl[2], xl[3]),
                        ptx::pack_h2(xl[4], xl[5]), 0x00003C00u};
       ptx::tmem_st8(tAl, v);
       ptx::tmem_st_wait();
-      if (!mma_stage([&] { ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + Lay::B_L1, H * 16, 128), ID_H, 0); }))
+      if (!mma_stage([&] { ptx::mma_f16_ts(tD, tA, ptx::sdesc(aW + O.b_l1, H * 16, 128), ID_H, 0); }))
         break;
     }
 
@@ -522,7 +610,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
     // ReLU -> FP16 (or scaled E4M3) -> A operand
     bool ok = true;
 #pragma unroll
-    for (int layer = 0; layer < 2; ++layer) {
+    for (int layer = 0; layer < NH; ++layer) {
       constexpr int NC = H < 32 ? H : 32;
 #pragma unroll
       for (int c0 = 0; c0 < H; c0 += NC) {
@@ -580,9 +668,10 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
           }
         });
       } else {
-        const int boff = layer == 0 ? Lay::B_L2 : Lay::B_LO;
-        const int nrows = layer == 0 ? H : 16;
-        const uint32_t id = layer == 0 ? ID_H : ID_16;
+        const bool last = layer == NH - 1;
+        const int boff = last ? O.b_lo : O.b_l2 + layer * H * (H + 16) * 2;
+        const int nrows = last ? 16 : H;
+        const uint32_t id = last ? ID_16 : ID_H;
         staged = mma_stage([&] {
 #pragma unroll
           for (int s2 = 0; s2 < H / 16; ++s2)
@@ -645,10 +734,10 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
 // ---------------------------------------------------------------------------
 // host launch
 // ---------------------------------------------------------------------------
-template <int H, bool FRAME, bool F16P, bool P8>
+template <int H, int FK, int NH, bool F16P, bool P8>
 static int launch_tc_one(const LaunchCommon& L, cudaStream_t s) {
-  constexpr int SMEM = smem_bytes<H, FRAME, P8, kNwg>();
-  auto k = eval_tc_kernel<H, FRAME, F16P, P8, kNwg>;
+  constexpr int SMEM = smem_bytes<H, FK, NH, P8, kNwg>();
+  auto k = eval_tc_kernel<H, FK, NH, F16P, P8, kNwg>;
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
@@ -667,27 +756,31 @@ static int launch_tc_one(const LaunchCommon& L, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
-template <int H, bool P8>
+template <int H, int NH, bool P8>
 static int tc_dispatch(const LaunchCommon& L, cudaStream_t s) {
-  if (L.shape.frame)
-    return L.pyr.f16 ? launch_tc_one<H, true, true, P8>(L, s) : launch_tc_one<H, true, false, P8>(L, s);
-  return L.pyr.f16 ? launch_tc_one<H, false, true, P8>(L, s) : launch_tc_one<H, false, false, P8>(L, s);
-}
-
-template <bool P8>
-static int tc_dispatch_h(const LaunchCommon& L, cudaStream_t s) {
-  if (L.shape.H == 16) return tc_dispatch<16, P8>(L, s);
-  if (L.shape.H == 32) return tc_dispatch<32, P8>(L, s);
-  if (L.shape.H == 64) return tc_dispatch<64, P8>(L, s);
-  return (int)cudaErrorInvalidValue;
+  const bool f16 = L.pyr.f16;
+  if (L.shape.frame == 1)
+    return f16 ? launch_tc_one<H, 1, NH, true, P8>(L, s) : launch_tc_one<H, 1, NH, false, P8>(L, s);
+  if constexpr (!P8) {
+    if (L.shape.frame == 2)
+      return f16 ? launch_tc_one<H, 2, NH, true, P8>(L, s) : launch_tc_one<H, 2, NH, false, P8>(L, s);
+  }
+  if (L.shape.frame != 0) return (int)cudaErrorInvalidValue;
+  return f16 ? launch_tc_one<H, 0, NH, true, P8>(L, s) : launch_tc_one<H, 0, NH, false, P8>(L, s);
 }
 
 int launch_eval_tc(const LaunchCommon& L, int precision, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  if (L.shape.NH != 2) return (int)cudaErrorInvalidValue;
-  if (precision == NAM_PREC_F16) return tc_dispatch_h<false>(L, s);
-  if (precision == NAM_PREC_FP8) return tc_dispatch_h<true>(L, s);
-  return (int)cudaErrorInvalidValue;
+  if (!tc_supported(L.shape, precision)) return (int)cudaErrorInvalidValue;
+  if (precision == NAM_PREC_FP8) {
+    if (L.shape.H == 16) return tc_dispatch<16, 2, true>(L, s);
+    if (L.shape.H == 32) return tc_dispatch<32, 2, true>(L, s);
+    return tc_dispatch<64, 2, true>(L, s);
+  }
+  if (L.shape.NH == 3) return tc_dispatch<64, 3, false>(L, s);
+  if (L.shape.H == 16) return tc_dispatch<16, 2, false>(L, s);
+  if (L.shape.H == 32) return tc_dispatch<32, 2, false>(L, s);
+  return tc_dispatch<64, 2, false>(L, s);
 }
 
 // ---------------------------------------------------------------------------

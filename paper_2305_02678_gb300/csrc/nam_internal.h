@@ -34,9 +34,14 @@ struct QueryPtrs {
 // optional frame MLP 8 -> 16 -> 6.
 struct Shape {
   int32_t H;        // hidden width: 16, 32, 64
-  int32_t NH;       // hidden layers: 2 or 3
-  int32_t frame;    // 1: frame MLP present
+  int32_t NH;       // hidden layers: 2 or 3 (3 only with H = 64)
+  int32_t frame;    // 0: none, 1: frame MLP 8 -> 16 -> 6 + Gram-Schmidt,
+                    // 2: the paper's linear 8 -> 12, two frames
+  int32_t in;       // decoder inputs: 14, or 20 with frame == 2
 };
+
+// Frame parameters per form: MLP 16*8 + 16 + 6*16 + 6, paper 12*8 + 12.
+inline int64_t frame_params_of(int frame) { return frame == 1 ? 246 : frame == 2 ? 108 : 0; }
 
 // A chunk of at most 128 consecutive queries that all use one material.
 struct Chunk {

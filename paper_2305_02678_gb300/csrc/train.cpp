@@ -15,7 +15,8 @@ static nam_status check_trainable(nam_ctx* ctx, nam_material m) {
     if (!ctx->materials.count(m)) return fail(NAM_ERR_NOT_FOUND, "unknown material");
   }
   if (!m->desc.trainable) return fail(NAM_ERR_UNSUPPORTED, "material is not trainable");
-  if (m->shape.NH != 2) return fail(NAM_ERR_UNSUPPORTED, "backward supports two hidden layers");
+  if (m->shape.NH != 2 || m->shape.frame == 2)
+    return fail(NAM_ERR_UNSUPPORTED, "reverse mode supports the frame MLP form with two hidden layers");
   return NAM_OK;
 }
 
