@@ -408,6 +408,10 @@ def run_ours(args):
     sweep4k, outs4k = None, None
     if not args.no_sweep4k:
         sweep4k, outs4k = run_sweep_4k(ctx, dev, stream, flush, args)
+    # ---- the paper's decoder sizes with its frame form ----------------------
+    paper = None
+    if not args.no_sweep:
+        paper = run_paper_decoders(ctx, dev, stream, flush, w, dq, n, args)
     # ---- importance sampling on the 1080p frame ------------------------------
     sampling = None
     if not args.no_sweep:
@@ -444,6 +448,7 @@ def run_ours(args):
             "roofline": roofline,
             "precision_sweep": sweep,
             "precision_sweep_3840x2160": sweep4k,
+            "paper_decoders": paper,
             "importance_sampling": sampling,
             "training": training,
             "serving": serving,
@@ -495,6 +500,28 @@ def run_sweep_4k(ctx, dev, stream, flush, args):
     for mat in mats.values():
         mat.destroy()
     return res, {"w": w, "sample": k, "out": host}
+
+
+def run_paper_decoders(ctx, dev, stream, flush, w, dq, n, args):
+    """The paper's three decoder sizes (2 x 16, 2 x 32, 3 x 64 hidden units)
+    with its frame form (linear 8 -> 12, two frames, 20 decoder inputs), FP16
+    on the 1080p frame (same pyramid and queries), seeded random weights."""
+    import workloads as W
+    from paper_2305_02678_gb300 import binding as B
+    out = {"workload": "fp16-2048sq-1920x1080, frame 8->12 (2 frames), decoder 20-H..-3"}
+    rng = W.rng_streams(W.SEEDS[2] + 21, 3)
+    for k, (H, NH) in enumerate(((16, 2), (32, 2), (64, 3))):
+        model = W.make_model(rng[k], (20,) + (H,) * NH + (3,), (8, 12))
+        mat = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], model["frame"], model["decoder"],
+                           precision=B.NAM_PREC_F16)
+        import torch
+        o = torch.empty((n, 3), device=dev)
+        t = statistics.fmean(time_launches(lambda: B.nam_eval(ctx.h, mat.h, dq, n, o, stream, 0),
+                                           max(3, args.steps // 2), 2, flush, stream))
+        out[f"{NH}x{H}_ms"] = round(t, 4)
+        out[f"{NH}x{H}_evals_per_s"] = round(n / (t * 1e-3), 1)
+        mat.destroy()
+    return out
 
 
 def run_sampling(ctx, dev, stream, flush, w, dq, n, args):
