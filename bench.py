@@ -355,6 +355,12 @@ def run_ours(args):
 
     e2e_times = time_launches(step_host, max(3, args.steps // 2), 2, flush, stream)
     e2e_ms = max_over_ranks(world, statistics.fmean(e2e_times), dev)
+    # the same through the staged-copy path (device staging area, chunked
+    # copies overlapping the kernels), for comparison
+    staged_times = time_launches(lambda: B.nam_eval_host(ctx.h, mat16.h, pinned, n, host_out, stream,
+                                                         B.NAM_HOST_STAGED), max(3, args.steps // 2), 2, flush,
+                                 stream)
+    staged_ms = statistics.fmean(staged_times)
     h2d = sum(int(t.numel()) * 4 for t in pinned.values())
     d2h = n * 12
 
@@ -443,7 +449,11 @@ def run_ours(args):
                        "l2": "flushed (256 MiB write) before every timed step, outside the timed kernel",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": round(world * n / (e2e_ms * 1e-3), 1), "unit": "evals/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4)},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),
+                    "api": "nam_eval_host with pinned host queries and output: the kernel reads the inputs and "
+                           "writes the RGB in host memory over NVLink-C2C where the device reads host page "
+                           "tables, else staged copies",
+                    "staged_copies_ms_per_step": round(staged_ms, 4)},
             "gpu_launches": args.steps,
             "roofline": roofline,
             "precision_sweep": sweep,

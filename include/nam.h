@@ -200,16 +200,24 @@ typedef struct {
                                  Required for NAM_FILTER_STOCHASTIC, else ignored. */
 } nam_queries;
 
-enum { NAM_OUT_COSINE = 1u << 0 };  /* multiply the RGB by max(0, wi.z) (Eq. 1) */
+enum {
+  NAM_OUT_COSINE = 1u << 0,  /* multiply the RGB by max(0, wi.z) (Eq. 1) */
+  NAM_HOST_STAGED = 1u << 8  /* nam_eval_host: always take the staged-copy path */
+};
 
 /* Evaluate n queries whose arrays are device memory; writes rgb_out (device,
  * [n][3]).  n = 0 is a no-op.  Asynchronous on `stream`. */
 nam_status nam_eval(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
                     float* rgb_out, void* stream, uint32_t flags);
 
-/* Same with HOST query and output arrays: copies the inputs to a device
- * staging area owned by the context, evaluates, copies the RGB back and
- * synchronises the stream.  Pinned host memory gives full copy bandwidth. */
+/* Same with HOST query and output arrays; synchronises the stream before it
+ * returns.  Where the device reads host memory through the host's page
+ * tables (cudaDevAttrPageableMemoryAccess, e.g. a GB300 with its CPU over
+ * NVLink-C2C), the kernel reads the host queries and writes the host RGB
+ * directly, with no staging copies; otherwise, or with NAM_HOST_STAGED in
+ * flags, the inputs go to a device staging area owned by the context in up
+ * to four chunks whose copies overlap the kernels (pinned host memory gives
+ * full copy bandwidth).  Both paths give identical results. */
 nam_status nam_eval_host(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
                          float* rgb_out, void* stream, uint32_t flags);
 

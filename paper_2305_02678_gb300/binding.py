@@ -23,6 +23,7 @@ NAM_LATENT_F32, NAM_LATENT_F16 = 0, 1
 NAM_PREC_F32, NAM_PREC_F16, NAM_PREC_FP8 = 0, 1, 2
 NAM_FILTER_TRILINEAR, NAM_FILTER_STOCHASTIC = 0, 1
 NAM_ADDRESS_WRAP, NAM_ADDRESS_CLAMP = 0, 1
+NAM_HOST_STAGED = 1 << 8
 NAM_OUT_COSINE = 1
 NAM_FAULT_NONE, NAM_FAULT_ALLOC, NAM_FAULT_LAUNCH, NAM_FAULT_STALL = 0, 1, 2, 3
 NAM_MAX_LEVELS, NAM_MAX_LAYERS = 16, 8

@@ -139,6 +139,9 @@ extern "C" nam_status nam_init(nam_ctx** out, const nam_config* cfg) {
   nam_ctx* ctx = new nam_ctx();
   ctx->device = c.device;
   ctx->num_sms = prop.multiProcessorCount;
+  int pageable = 0;
+  if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, c.device) != cudaSuccess) pageable = 0;
+  ctx->host_direct = pageable == 1;
   ctx->budget = c.hbm_budget_bytes;
   ctx->timeout_ns = c.wait_timeout_ns ? c.wait_timeout_ns : 2000000000ull;
   ctx->serve_streams = c.serve_streams > 0 ? c.serve_streams : 4;
@@ -549,6 +552,16 @@ extern "C" nam_status nam_eval_host(nam_ctx* ctx, nam_material m, const nam_quer
   nam_status st = check_queries(m, q);
   if (st) return st;
   DeviceGuard g(ctx->device);
+  if (ctx->host_direct && !(flags & NAM_HOST_STAGED)) {
+    // the kernel reads the host queries and writes the host RGB itself
+    LaunchCommon L;
+    fill_launch(ctx, m, q, n, rgb_out, flags, &L);
+    int e = launch_material(L, m->desc.precision, stream);
+    if (e) return cuda_fail(e, "nam_eval_host: launch");
+    cudaError_t ce = cudaStreamSynchronize((cudaStream_t)stream);
+    if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_eval_host: sync");
+    return NAM_OK;
+  }
   std::lock_guard<std::mutex> lk(ctx->stage_mu);
   const bool has_xi = m->desc.filter == NAM_FILTER_STOCHASTIC;
   const int nf = has_xi ? 10 : 9;

@@ -41,6 +41,7 @@ struct ServeState;
 struct nam_ctx {
   int device = 0;
   int num_sms = 0;
+  bool host_direct = false;             // kernels may read host memory (page tables)
   uint64_t budget = 0;
   uint64_t timeout_ns = 0;
   int serve_streams = 4;

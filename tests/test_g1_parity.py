@@ -252,12 +252,14 @@ def test_host_path_pipelined_chunks_identical(gctx, w2, precision, n):
     q = W.slice_queries(w2["queries"], 0, n)
     mat = gctx.material(w2["W0"], w2["H0"], w2["L"], w2["pyramid"], m["frame"], m["decoder"], precision=precision)
     a = mat.eval(to_device(q)).cpu().numpy()
+    from paper_2305_02678_gb300 import binding as B
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in q.items()}
-    h = mat.eval_host(pinned)
-    assert np.array_equal(a, h)
-    # pageable numpy inputs take the same path
-    h2 = mat.eval_host(q)
-    assert np.array_equal(a, h2)
+    for flags in (0, B.NAM_HOST_STAGED):   # direct host access (where available) and staged copies
+        h = mat.eval_host(pinned, flags=flags)
+        assert np.array_equal(a, h)
+        # pageable numpy inputs take the same path
+        h2 = mat.eval_host(q, flags=flags)
+        assert np.array_equal(a, h2)
     mat.destroy()
     gctx.check()
 
