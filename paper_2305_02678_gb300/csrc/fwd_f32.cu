@@ -203,13 +203,14 @@ template <int H, int NH, int FK, bool F16>
 static int launch_one(const LaunchCommon& L, cudaStream_t s) {
   auto k = eval_f32_kernel<H, NH, FK, F16>;
   const int smem = (int)sizeof(SmemF32<H, NH, FK, FK == 2 ? 20 : 16>);
-  static int occ = -1;  // per instantiation
-  if (occ < 0) {
+  static std::atomic<uint64_t> configured{0};
+  static std::atomic<int> occ{0};  // per instantiation (one GPU model)
+  once_per_device(configured, [&] {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    occ = blocks_per_sm((const void*)k, 128, smem, 16);
-  }
+    occ.store(blocks_per_sm((const void*)k, 128, smem, 16));
+  });
   int64_t blocks = (L.n + 127) / 128;
-  int64_t cap = (int64_t)occ * L.num_sms;
+  int64_t cap = (int64_t)occ.load() * L.num_sms;
   int grid = (int)(blocks < cap ? blocks : cap);
   if (grid < 1) grid = 1;
   k<<<grid, 128, smem, s>>>(L);

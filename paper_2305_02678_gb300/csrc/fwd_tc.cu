@@ -738,15 +738,14 @@ template <int H, int FK, int NH, bool F16P, bool P8>
 static int launch_tc_one(const LaunchCommon& L, cudaStream_t s) {
   constexpr int SMEM = smem_bytes<H, FK, NH, P8, kNwg>();
   auto k = eval_tc_kernel<H, FK, NH, F16P, P8, kNwg>;
-  static bool configured = false;
-  if (!configured) {
+  static std::atomic<uint64_t> configured{0};
+  once_per_device(configured, [&] {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     // ask for the smallest shared-memory carveout that holds the CTA: the
     // rest of the SM's L1/shared storage caches the texel gathers
     const int pct = (SMEM + 1024) * 100 / (228 * 1024) + 1;
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-    configured = true;
-  }
+  });
   const int64_t nchunks = L.chunks ? (int64_t)L.n_chunks : (L.n + 127) / 128;
   if (nchunks == 0) return 0;
   // one CTA per SM (TMEM: kNwg x 96 of 512 columns)

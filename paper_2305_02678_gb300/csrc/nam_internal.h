@@ -1,6 +1,9 @@
 // Internal types shared by the libnam translation units (not part of the ABI).
 #pragma once
+#include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 
 #include "../../include/nam.h"
 
@@ -85,6 +88,21 @@ struct LaunchCommon {
 // memory and threads.  The API answers 1 for kernels that use TMEM, whose
 // true limit (columns allocated per CTA) the caller passes as `cap`.
 int blocks_per_sm(const void* func, int threads, int dyn_smem, int cap, bool resources_only = false);
+
+// Kernel attributes (dynamic shared memory, carveout) belong to a device's
+// context: `fn` runs once per device for each call site's `done` mask.
+template <class F>
+inline void once_per_device(std::atomic<uint64_t>& done, F fn) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    fn();
+    return;
+  }
+  const uint64_t bit = 1ull << dev;
+  if (done.load(std::memory_order_acquire) & bit) return;
+  fn();
+  done.fetch_or(bit, std::memory_order_acq_rel);
+}
 
 int launch_eval_f32(const LaunchCommon& L, void* stream);
 int launch_eval_tc(const LaunchCommon& L, int precision, void* stream);

@@ -178,18 +178,25 @@ __global__ void __launch_bounds__(128) sampler_kernel(const LaunchCommon L, cons
 
 }  // namespace
 
+template <bool F16>
+static int launch_sampler_one(const LaunchCommon& L, const float* sampler, int mode, const float* u, float* wo_out,
+                              float* pdf_out, cudaStream_t s) {
+  auto k = sampler_kernel<F16>;
+  static std::atomic<int> occ{0};  // per instantiation (one GPU model)
+  if (occ.load() == 0) occ.store(blocks_per_sm((const void*)k, 128, 0, 16));
+  const int64_t blocks = (L.n + 127) / 128;
+  const int64_t cap = (int64_t)occ.load() * L.num_sms;
+  const int grid = (int)(blocks < cap ? blocks : cap);
+  k<<<grid, 128, 0, s>>>(L, sampler, mode, u, wo_out, pdf_out);
+  return (int)cudaGetLastError();
+}
+
 int launch_sampler(const LaunchCommon& L, const float* sampler, int mode, const float* u, float* wo_out,
                    float* pdf_out, void* stream) {
   if (L.n == 0) return 0;
   cudaStream_t s = (cudaStream_t)stream;
-  auto k = L.pyr.f16 ? sampler_kernel<true> : sampler_kernel<false>;
-  static int occ = -1;
-  if (occ < 0) occ = blocks_per_sm((const void*)k, 128, 0, 16);
-  const int64_t blocks = (L.n + 127) / 128;
-  const int64_t cap = (int64_t)occ * L.num_sms;
-  const int grid = (int)(blocks < cap ? blocks : cap);
-  k<<<grid, 128, 0, s>>>(L, sampler, mode, u, wo_out, pdf_out);
-  return (int)cudaGetLastError();
+  return L.pyr.f16 ? launch_sampler_one<true>(L, sampler, mode, u, wo_out, pdf_out, s)
+                   : launch_sampler_one<false>(L, sampler, mode, u, wo_out, pdf_out, s);
 }
 
 }  // namespace nam
