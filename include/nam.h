@@ -301,22 +301,27 @@ typedef struct {
 /* One training step on a trainable material: forward, loss
  * L = mean |log(1+max(g,0)) - log(1+y)| + 0.01 mean max(-g,0) over the n x 3
  * outputs (L1 in log space, Sec. 5.2), backward, Adam on the MLP masters
- * and the pyramid.  target_rgb is device [n][3]; *loss_out (host) receives L
- * of this step's forward (the call synchronises the stream to read it).
- * Optimiser moments live in the material. */
+ * and the pyramid.  One kernel runs the forward, the loss and the backward;
+ * two more apply Adam.  target_rgb is device [n][3]; *loss_out (host)
+ * receives L of this step's forward (the call synchronises the stream to
+ * read it).  Optimiser moments live in the material; the first call
+ * allocates the material's 256-byte loss accumulator. */
 nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
                           int64_t n, const nam_adam* opt, float* loss_out, void* stream, uint32_t flags);
 
 /* A training step that allocates no device memory.  The paper has no
- * counterpart: this is a library facility.  nam_train_step allocates its
- * per-batch buffers (forward RGB, dL/dRGB, loss accumulator) on first use and
- * again when the batch grows; callers that may not call cudaMalloc while they
- * run -- a fixed memory plan, an embedding host that owns all allocation, a
- * loop that must not synchronise the device the way cudaMalloc/cudaFree can --
- * call this instead.  It does exactly what nam_train_step does, with those
- * buffers in one static device array of the library
- * (NAM_NOALLOC_TRAIN_MAX_QUERIES * 24 + 256 bytes, held by every GPU that
- * loads libnam until the process exits).
+ * counterpart: this is a library facility.  nam_train_step allocates a
+ * per-material buffer on its first call; callers that may not call
+ * cudaMalloc while they run -- a fixed memory plan, an embedding host that
+ * owns all allocation, a loop that must not synchronise the device the way
+ * cudaMalloc/cudaFree can -- call this instead.  It computes what
+ * nam_train_step computes (loss, gradients, Adam update) as separate passes:
+ * the forward, the loss, the backward, Adam, with the per-batch buffers
+ * (forward RGB, dL/dRGB, loss accumulator) in one static device array of the
+ * library (NAM_NOALLOC_TRAIN_MAX_QUERIES * 24 + 256 bytes, held by every GPU
+ * that loads libnam until the process exits).  Its results agree with
+ * nam_train_step's to FP32 rounding: the fused step takes the forward values
+ * from its backward kernel, which sums in another order.
  *  - n must be at most NAM_NOALLOC_TRAIN_MAX_QUERIES; larger batches are
  *    refused with NAM_ERR_INVALID_ARG before anything is enqueued.
  *  - The first call on a device looks up the array's device address

@@ -128,11 +128,22 @@ struct BackwardArgs {
   int64_t n;
   const void* pyramid;     // FP32 master pyramid
   const float* params;     // FP32 master params (frame then decoder)
-  const float* grad_rgb;   // [n][3]
+  const float* grad_rgb;   // [n][3] dL/drgb, or null when target is set
+  // fused log-space L1 loss (training step): when target is set the kernel
+  // takes dL/drgb from the loss of its own forward values against target
+  // [n][3] and adds loss_inv * sum of the per-element losses to *loss_acc
+  const float* target;
+  float* loss_acc;
+  float loss_inv;
   float* grad_params;
   float* grad_pyramid;     // may be null
   uint32_t flags;
   int num_sms;
+  // set by the launcher: the gradient of texels [tiny_tex0, texels) is summed
+  // in per-warp shared copies, that of [cta_tex0, tiny_tex0) in one shared
+  // copy per CTA, before it reaches the global buffer
+  int64_t tiny_tex0, cta_tex0;
+  int32_t tiny_n, cta_n;
 };
 int launch_backward(const BackwardArgs& a, void* stream);
 int launch_loss(const float* rgb, const float* target, int64_t n, float* grad_rgb, float* loss_accum,

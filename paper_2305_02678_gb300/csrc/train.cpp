@@ -67,8 +67,9 @@ extern "C" nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_que
   if (st) return st;
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  // per-material scratch: rgb [n][3], dL/drgb [n][3], loss accumulator
-  const size_t need = (size_t)n * 24 + 256;
+  // per-material scratch: the loss accumulator (the backward kernel runs the
+  // forward and the loss itself)
+  const size_t need = 256;
   if (need > m->train_scratch_bytes) {
     if (m->train_scratch) {
       cudaStreamSynchronize(s);
@@ -88,16 +89,13 @@ extern "C" nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_que
     m->info.resident_bytes += need;
   }
   float* loss_acc = (float*)m->train_scratch;
-  float* rgb = loss_acc + 64;
-  float* grad_rgb = rgb + 3 * n;
-  cudaMemsetAsync(loss_acc, 0, sizeof(float), s);
-  LaunchCommon L;
-  fill_launch(ctx, m, q, n, rgb, flags, &L);
-  int e = launch_eval_f32(L, s);
-  if (!e) e = launch_loss(rgb, target_rgb, n, grad_rgb, loss_acc, s);
+  int e = (int)cudaMemsetAsync(loss_acc, 0, sizeof(float), s);
   BackwardArgs a;
   const int64_t np = m->n_params, po = m->pyr_off, nt = m->pyr.texels * 8;
-  fill_bwd(ctx, m, q, n, grad_rgb, m->grad, m->grad + po, flags, &a);
+  fill_bwd(ctx, m, q, n, nullptr, m->grad, m->grad + po, flags, &a);
+  a.target = target_rgb;
+  a.loss_acc = loss_acc;
+  a.loss_inv = 1.0f / (float)(3 * n);
   if (!e) e = launch_backward(a, s);
   if (!e)
     e = launch_adam(m->params, m->grad, m->adam_m, m->adam_v, np, opt->lr_params, opt->beta1, opt->beta2, opt->eps,

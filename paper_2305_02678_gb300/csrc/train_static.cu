@@ -1,13 +1,13 @@
 // A training step for callers that cannot allocate device memory.
 //
-// nam_train_step keeps its per-batch buffers (the forward's RGB, dL/dRGB and
-// the loss accumulator) in device memory it allocates on first use and
-// re-allocates when the batch grows.  Callers that must not allocate once
-// they are running -- a renderer or trainer with a fixed memory plan, a host
-// that forbids cudaMalloc outside its own allocator, code that must not
-// synchronise the device (cudaMalloc/cudaFree may) -- use
-// nam_train_step_noalloc instead, which keeps those buffers in the
-// file-scope device array below.  The array is part of the library image:
+// nam_train_step keeps its loss accumulator in device memory it allocates on
+// its first call.  Callers that must not allocate once they are running -- a
+// renderer or trainer with a fixed memory plan, a host that forbids
+// cudaMalloc outside its own allocator, code that must not synchronise the
+// device (cudaMalloc/cudaFree may) -- use nam_train_step_noalloc instead,
+// which runs the forward, the loss and the backward as separate passes and
+// keeps their per-batch buffers (the forward's RGB, dL/dRGB and the loss
+// accumulator) in the file-scope device array below.  The array is part of the library image:
 // every GPU that loads libnam holds it (NAM_NOALLOC_TRAIN_MAX_QUERIES * 24 +
 // 256 bytes, 1.5 MiB) until the process exits.
 #include <cuda_runtime.h>

@@ -35,7 +35,7 @@ def _well_conditioned(oracle, om, q, limit=50.0):
 
 @pytest.mark.parametrize("frame", [True, False])
 @pytest.mark.parametrize("filt", [0, 1])
-@pytest.mark.parametrize("H", [32, 64])
+@pytest.mark.parametrize("H", [16, 32, 64])
 def test_backward_matches_oracle_gradient(gctx, oracle, frame, filt, H):
     import torch
     from paper_2305_02678_gb300 import binding as B

@@ -47,7 +47,8 @@ def test_noalloc_training_step_matches_allocating_step():
         pn, zn = nal.params()
         P = lambda p, m: torch.as_tensor(_DevArray(p, m), device="cuda")
         a, b = P(pr, ref.info.n_params), P(pn, nal.info.n_params)
-        # same kernels; only the order of FP32 atomic additions in the backward differs
+        # the allocating step fuses forward and loss into its backward kernel:
+        # the two differ in FP32 summation order only
         assert torch.allclose(a, b, rtol=1e-4, atol=1e-6), (a - b).abs().max().item()
         za, zb = P(zr, ref.info.texels * 8), P(zn, nal.info.texels * 8)
         assert torch.allclose(za, zb, rtol=1e-4, atol=1e-6), (za - zb).abs().max().item()
