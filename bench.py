@@ -38,6 +38,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "neural-BRDF evals/s FP16/FP8 vs plain FP32 at stated error; p50/p99 frame ms"
 WORKLOAD = "fp16-2048sq-1920x1080"
+# FP32 FMA (non-tensor) peak: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz
+ALU_PEAK_TFLOPS = round(152 * 128 * 2 * 2.07e9 / 1e12, 1)
+# matrix FLOPs per query of the reverse mode (frame MLP 8-16-6, decoder
+# 14-64-64-3): forward recompute, deltas and weight gradients, 3 x 10,816
+BWD_FLOPS_PER_QUERY = 3 * 2 * (8 * 16 + 16 * 6 + 14 * 64 + 64 * 64 + 64 * 3)
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -559,8 +564,7 @@ def run_sampling(ctx, dev, stream, flush, w, dq, n, args):
     mat.destroy()
     ctx.check()
     flops = 2 * 2688 * n
-    sm_clock = 2.07e9
-    peak = 152 * 128 * 2 * sm_clock / 1e12
+    peak = ALU_PEAK_TFLOPS
     return {"workload": "fp16-2048sq-1920x1080 + sampler 11-32-32-32-9 (FP32)", "queries": n,
             "sample_ms": round(t_s, 4), "samples_per_s": round(n / (t_s * 1e-3), 1),
             "pdf_ms": round(t_p, 4), "pdf_evals_per_s": round(n / (t_p * 1e-3), 1),
@@ -607,14 +611,42 @@ def run_training(ctx, dev, stream, steps, batch=262144, pool=8):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / (steps - 3)
+    # the reverse-mode kernel alone (nam_backward: the step's kernel without
+    # the fused loss) on one batch, for its ALU roofline
+    g = torch.Generator(device=dev)
+    g.manual_seed(W.SEEDS[4] + 8)
+    gr = torch.randn((batch, 3), device=dev, generator=g) * (1.0 / (3 * batch))
+    gp = torch.zeros(mat.info.n_params, device=dev)
+    gz = torch.zeros((mat.info.texels, 8), device=dev)
+    dq0 = batches[0][0]
+    for _ in range(3):
+        B.nam_backward(ctx.h, mat.h, dq0, batch, gr, gp, gz, stream)
+    torch.cuda.synchronize()
+    reps = 20
+    a.record(stream)
+    for _ in range(reps):
+        B.nam_backward(ctx.h, mat.h, dq0, batch, gr, gp, gz, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    bwd_ms = a.elapsed_time(b) / reps
+    tflops = BWD_FLOPS_PER_QUERY * batch / (bwd_ms * 1e-3) / 1e12
     mat.destroy()
     ctx.check()
     return {"workload": "train-1024sq-262144", "steps": steps, "batch": batch, "ms_per_step": round(ms, 4),
+            "backward_ms": round(bwd_ms, 4),
+            "backward_roofline": {"kernel": "backward_kernel, H = 64, frame MLP", "bound": "alu",
+                                  "achieved": round(tflops, 2), "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                  "frac": round(tflops / ALU_PEAK_TFLOPS, 4),
+                                  "flops_per_query": BWD_FLOPS_PER_QUERY,
+                                  "note": "matrix FLOPs (2 per multiply-add) of the forward recompute, the "
+                                          "deltas and the weight gradients; FP32 FMA peak of 152 SMs x 128 "
+                                          "lanes at 2.07 GHz"},
             "steps_per_s": round(1e3 / ms, 1), "samples_per_s": round(batch * 1e3 / ms, 1),
             "loss_first": round(losses[0], 5), "loss_last": round(losses[-1], 5),
             "loss_every_100": [round(x, 5) for x in losses[3:]],
-            "note": "each step: FP32 forward, log-L1 loss, hand-written reverse mode (atomic pyramid scatter), "
-                    "Adam over 11.18 M pyramid + MLP parameters; loss read back every 100 steps"}
+            "note": "each step: one kernel for the FP32 forward, the log-L1 loss and the hand-written reverse "
+                    "mode (atomic pyramid scatter), then Adam over 11.18 M pyramid + MLP parameters; loss read "
+                    "back every 100 steps"}
 
 
 def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_frames=None):

@@ -756,7 +756,8 @@ int launch_adam(float* p, const float* g, float* m, float* v, int64_t count, flo
   const AdamStep a{lr, b1, b2, eps, 1.0f - powf(b1, (float)step), 1.0f - powf(b2, (float)step)};
   float* gm = const_cast<float*>(g);
   int64_t head = 0;
-  if ((((uintptr_t)p | (uintptr_t)g | (uintptr_t)m | (uintptr_t)v) & 15u) == 0) {
+  // small arrays (the MLP masters) in one scalar launch
+  if (count >= (1 << 16) && (((uintptr_t)p | (uintptr_t)g | (uintptr_t)m | (uintptr_t)v) & 15u) == 0) {
     const int64_t count4 = count / 4;
     if (count4 > 0) {
       int grid = (int)((count4 + 255) / 256);
