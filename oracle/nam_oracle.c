@@ -23,7 +23,7 @@
  * order, activations, loss form, FP8 quantisation) are listed in the design
  * notes and restated at each function below.
  *
- * Pins: tests/test_oracle_pins.py checks every function here against closed
+ * Pins: tests/test_oracle_pins*.py check every function here against closed
  * forms, invariants, library routines and brute force on tiny inputs.
  */
 #include <math.h>
@@ -156,6 +156,10 @@ typedef struct {
 
 typedef struct {
   const float *u, *v, *lod, *wix, *wiy, *wiz, *wox, *woy, *woz, *xi;
+  /* encoder phase of training (Sec. 5.1): when set, the latent of query i is
+   * z[8 i .. 8 i + 7] as given (the encoder's output), bypassing the latent
+   * texture; u, v, lod and xi are then not read */
+  const double* z;
 } orc_queries;
 
 /* Level sizes: level l is max(1, W0 >> l) by max(1, H0 >> l) texels, levels
@@ -467,12 +471,18 @@ static void paper_frames(const orc_model* m, trace* tr) {
 
 static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trace* tr, round_ctx* rc,
                        double kappa) {
-  double u = q->u[i], v = q->v[i], lod = q->lod[i];
-  double xi = q->xi ? q->xi[i] : 0.0;
-  tr->ntaps = latent_taps(m, u, v, lod, xi, tr->idx, tr->w);
-  for (int c = 0; c < ORC_C; ++c) tr->z[c] = 0.0;
-  for (int k = 0; k < tr->ntaps; ++k)
-    for (int c = 0; c < ORC_C; ++c) tr->z[c] += tr->w[k] * texel(m, tr->idx[k], c);
+  if (q->z) {
+    /* the latent comes from the encoder, not from the texture */
+    tr->ntaps = 0;
+    for (int c = 0; c < ORC_C; ++c) tr->z[c] = q->z[i * ORC_C + c];
+  } else {
+    double u = q->u[i], v = q->v[i], lod = q->lod[i];
+    double xi = q->xi ? q->xi[i] : 0.0;
+    tr->ntaps = latent_taps(m, u, v, lod, xi, tr->idx, tr->w);
+    for (int c = 0; c < ORC_C; ++c) tr->z[c] = 0.0;
+    for (int k = 0; k < tr->ntaps; ++k)
+      for (int c = 0; c < ORC_C; ++c) tr->z[c] += tr->w[k] * texel(m, tr->idx[k], c);
+  }
   tr->wi[0] = q->wix[i]; tr->wi[1] = q->wiy[i]; tr->wi[2] = q->wiz[i];
   tr->wo[0] = q->wox[i]; tr->wo[1] = q->woy[i]; tr->wo[2] = q->woz[i];
 
@@ -687,9 +697,11 @@ double orc_loss(const double* g, const float* y, int64_t n, double* dldg_out) {
  * pyramid ([texel][C]).  Accumulates into the outputs.  Exact derivative of
  * the forward above (no activation rounding), with two readings: ReLU'(0) = 0,
  * and no gradient flows through the degenerate-frame fallbacks (a
- * degenerate n is a constant; the fallback tangent depends on n only). */
+ * degenerate n is a constant; the fallback tangent depends on n only).
+ * g_z (may be NULL) receives dL/dz per query [n][8] (overwritten, not
+ * accumulated): the gradient the encoder of Sec. 5.1 back-propagates. */
 void orc_grad(const orc_model* m, const orc_queries* q, int64_t n, const double* dl_dy,
-              double* g_frame, double* g_dec, double* g_pyr) {
+              double* g_frame, double* g_dec, double* g_pyr, double* g_z) {
   if (m->frame_form == 1) return; /* reverse mode of the paper's frame form is not built */
   trace* tr = (trace*)malloc(sizeof(trace));
   orc_model mm = *m;
@@ -789,6 +801,9 @@ void orc_grad(const orc_model* m, const orc_queries* q, int64_t n, const double*
         dz[c] += s;
       }
     }
+    /* dL/dz of the query (the encoder's output gradient, Sec. 5.1) */
+    if (g_z)
+      for (int c = 0; c < ORC_C; ++c) g_z[i * ORC_C + c] = dz[c];
     /* z = sum_k w_k texel_k */
     if (g_pyr)
       for (int k = 0; k < tr->ntaps; ++k)

@@ -45,7 +45,9 @@ class _Model(C.Structure):
 
 
 class _Queries(C.Structure):
-    _fields_ = [(k, C.c_void_p) for k in ("u", "v", "lod", "wix", "wiy", "wiz", "wox", "woy", "woz", "xi")]
+    # "z" (float64 [n][8], optional): latents given directly (encoder phase,
+    # Sec. 5.1); the other fields are float32 arrays
+    _fields_ = [(k, C.c_void_p) for k in ("u", "v", "lod", "wix", "wiy", "wiz", "wox", "woy", "woz", "xi", "z")]
 
 
 def lib():
@@ -77,7 +79,7 @@ def lib():
         _lib.orc_eval.argtypes = [p, p, i64, p, C.c_int]
         _lib.orc_decoder_input_absmax.argtypes = [p, p, i64, p]
         _lib.orc_loss.restype = d; _lib.orc_loss.argtypes = [p, p, i64, p]
-        _lib.orc_grad.argtypes = [p, p, i64, p, p, p, p]
+        _lib.orc_grad.argtypes = [p, p, i64, p, p, p, p, p]
         _lib.orc_relu_pattern.argtypes = [p, p, i64, p]
         _lib.orc_frame_condition.argtypes = [p, p, i64, p]
         _lib.orc_eval_alternatives.argtypes = [p, p, i64, d, p, p, p, C.c_int]
@@ -225,7 +227,7 @@ class _QueryView:
             if a is None:
                 self.arrays[name] = None
                 continue
-            a = np.ascontiguousarray(a, dtype=np.float32)
+            a = np.ascontiguousarray(a, dtype=np.float64 if name == "z" else np.float32)
             assert a.shape[0] >= n
             self.arrays[name] = a
         s = _Queries()
@@ -370,8 +372,11 @@ def loss(g, y):
     return val, d
 
 
-def grad(model: Model, q, dl_dy, with_pyramid=True):
-    """Gradients of sum <dl_dy, y> w.r.t. frame params, decoder params, pyramid."""
+def grad(model: Model, q, dl_dy, with_pyramid=True, with_z=False):
+    """Gradients of sum <dl_dy, y> w.r.t. frame params, decoder params, pyramid
+    and, with_z, the latent of each query ("z", [n][8]: what the encoder of
+    Sec. 5.1 back-propagates; with q["z"] given the latents bypass the
+    texture and the pyramid gradient stays zero)."""
     if model.frame_form == 1:
         raise NotImplementedError("reverse mode of the paper's frame form is not built")
     n = _nq(q)
@@ -379,10 +384,11 @@ def grad(model: Model, q, dl_dy, with_pyramid=True):
     gf = np.zeros(model.n_frame_params(), dtype=np.float64)
     gd = np.zeros(model.n_dec_params(), dtype=np.float64)
     gp = np.zeros((model.texel_count(), 8), dtype=np.float64) if with_pyramid else None
+    gz = np.zeros((n, 8), dtype=np.float64) if with_z else None
     qv = _QueryView(q, n)
     lib().orc_grad(C.byref(model._s), C.byref(qv.s), n, _ptr(dl),
-                   _ptr(gf) if gf.size else None, _ptr(gd), _ptr(gp))
-    return {"frame": gf, "decoder": gd, "pyramid": gp}
+                   _ptr(gf) if gf.size else None, _ptr(gd), _ptr(gp), _ptr(gz))
+    return {"frame": gf, "decoder": gd, "pyramid": gp, "z": gz}
 
 
 def split_decoder(model: Model, flat):
@@ -504,3 +510,41 @@ def sampler_sample(model: Model, sampler, q, u):
     qv = _QueryView(q, n)
     lib().orc_sampler_sample(C.byref(model._s), _ptr(sp), C.byref(qv.s), n, _ptr(u), _ptr(wo), _ptr(pdf))
     return wo, pdf
+
+
+# ----------------------------------------------------------------------------
+# encoder (Sec. 5.1): material parameters k(x) -> latent z(x), used in the
+# first training phase in place of the latent texture and then evaluated
+# once per texel to initialise it
+# ----------------------------------------------------------------------------
+def encoder_forward(layers, k) -> np.ndarray:
+    """z = E(k) for k [n][K]; layers [(W [out][in], b [out]), ...] with ReLU
+    hidden layers and a linear output (FP64)."""
+    a = np.asarray(k, dtype=np.float64)
+    for l, (W, b) in enumerate(layers):
+        s = a @ np.asarray(W, dtype=np.float64).T + np.asarray(b, dtype=np.float64)
+        a = s if l == len(layers) - 1 else np.maximum(s, 0.0)
+    return a
+
+
+def encoder_grad(layers, k, dz):
+    """Gradients of sum_i <dz_i, E(k_i)> with respect to every (W, b), by the
+    chain rule through the layers above (ReLU'(0) = 0)."""
+    acts, pres = [np.asarray(k, dtype=np.float64)], []
+    for l, (W, b) in enumerate(layers):
+        s = acts[-1] @ np.asarray(W, dtype=np.float64).T + np.asarray(b, dtype=np.float64)
+        pres.append(s)
+        acts.append(s if l == len(layers) - 1 else np.maximum(s, 0.0))
+    d = np.asarray(dz, dtype=np.float64)
+    out = [None] * len(layers)
+    for l in range(len(layers) - 1, -1, -1):
+        out[l] = (d.T @ acts[l], d.sum(axis=0))
+        if l > 0:
+            d = (d @ np.asarray(layers[l][0], dtype=np.float64)) * (pres[l - 1] > 0.0)
+    return out
+
+
+def flat_encoder(layers) -> np.ndarray:
+    """Per layer W (out x in, row-major) then b: the library's layout."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float64).ravel(), np.asarray(b, np.float64)])
+                           for W, b in layers])

@@ -357,3 +357,31 @@ def target_rgb(target: ProceduralBRDF, q) -> np.ndarray:
     wi = np.stack([q["wix"], q["wiy"], q["wiz"]]).astype(np.float64)
     wo = np.stack([q["wox"], q["woy"], q["woz"]]).astype(np.float64)
     return target(q["u"].astype(np.float64), q["v"].astype(np.float64), wi, wo).astype(np.float32)
+
+
+def material_attributes(target: ProceduralBRDF, q) -> np.ndarray:
+    """[n, 4] float32 material parameters k(x) = (albedo RGB, roughness) of the
+    procedural material at the queries' uv: the encoder's inputs."""
+    a, r = target.params(q["u"].astype(np.float64), q["v"].astype(np.float64))
+    return np.concatenate([a, r[:, None]], axis=1).astype(np.float32)
+
+
+def texel_attributes(target: ProceduralBRDF, W0: int, H0: int, L: int) -> np.ndarray:
+    """[texels, 4] float32 material parameters for every texel of an L-level
+    pyramid, levels packed finest first: level 0 at the texel centres,
+    each coarser level the mean of its 2x2 (or 2x1) finer texels (the
+    prefiltered parameters the encoder maps to the coarse latents)."""
+    xs, ys = np.meshgrid(np.arange(W0), np.arange(H0))
+    u = (xs.ravel() + 0.5) / W0
+    v = (ys.ravel() + 0.5) / H0
+    a, r = target.params(u, v)
+    lvl = np.concatenate([a, r[:, None]], axis=1).reshape(H0, W0, 4)
+    out = [lvl.reshape(-1, 4)]
+    w, h = W0, H0
+    for _ in range(1, L):
+        w2, h2 = max(1, w // 2), max(1, h // 2)
+        fx, fy = w // w2, h // h2
+        lvl = lvl.reshape(h2, fy, w2, fx, 4).mean(axis=(1, 3))
+        out.append(lvl.reshape(-1, 4))
+        w, h = w2, h2
+    return np.concatenate(out).astype(np.float32)
