@@ -164,7 +164,19 @@ typedef struct {
   int32_t sampler_hidden;
   const float* sampler_weights;
   int32_t frame_form;         /* NAM_FRAME_MLP (0) or NAM_FRAME_PAPER (1) */
+  /* Encoder of the first training phase (Sec. 5.1): an MLP from the material
+   * parameters k(x) (encoder_inputs of them, 1..16; 0: no encoder) to the
+   * 8-channel latent, widths K -> 32 -> 32 -> 8, ReLU hidden layers, linear
+   * output; FP32 weights per layer W (out x in) then b (out), host or device
+   * memory as params_on_device says, copied at creation.  Trainable
+   * materials only: the encoder exists for training and for initialising
+   * the latent texture (nam_encoder_bake), never for evaluation. */
+  int32_t encoder_inputs;
+  const float* encoder_weights;
 } nam_material_desc;
+
+#define NAM_ENCODER_HIDDEN 32
+#define NAM_ENCODER_MAX_INPUTS 16
 
 typedef struct {
   uint64_t resident_bytes;    /* device bytes this material holds */
@@ -335,6 +347,49 @@ nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_queries* q, co
 #define NAM_NOALLOC_TRAIN_MAX_QUERIES 65536
 nam_status nam_train_step_noalloc(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
                                   int64_t n, const nam_adam* opt, float* loss_out, void* stream, uint32_t flags);
+
+/* ------------------------------------------------------------------------ */
+/* encoder phase of training (Sec. 5.1)                                     */
+/* ------------------------------------------------------------------------ */
+/* The paper trains in two phases.  First the latent of a query is the
+ * encoder's output for the material parameters at the query, fed to the
+ * decoder directly (the latent texture is bypassed); then the texture is
+ * initialised by evaluating the encoder for every texel, the encoder is
+ * dropped and the texels are trained directly (nam_train_step).  All calls
+ * below need a trainable material created with encoder_inputs = K > 0.
+ * attrs are device arrays [n][K] (row-major, FP32): the K material
+ * parameters of each query, or of each texel for the bake.  Queries need
+ * wi and wo (and xi is ignored); u, v and lod are not read. */
+
+/* z_out [n][8] (device, 16-byte aligned) = encoder(attrs). */
+nam_status nam_encode(nam_ctx* ctx, nam_material m, const float* attrs, int64_t n, float* z_out, void* stream);
+
+/* Initialise the latent texture: texel t of the FP32 pyramid master =
+ * encoder(texel_attrs[t]) for all texels (levels packed finest first; the
+ * caller prefilters the parameters of the coarse levels).  Clears the
+ * pyramid's Adam moments and gradient, so that finetuning starts afresh. */
+nam_status nam_encoder_bake(nam_ctx* ctx, nam_material m, const float* texel_attrs, void* stream);
+
+/* Reverse mode with latents from the encoder: accumulates the gradient of
+ * sum <grad_rgb, rgb> into grad_params (frame then decoder, as nam_backward)
+ * and grad_encoder (device [encoder parameters], the layout of
+ * encoder_weights).  Keeps a per-material buffer for the batch's latents and
+ * their gradients (allocated on first use, grown with the batch). */
+nam_status nam_backward_encoded(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* attrs,
+                                int64_t n, const float* grad_rgb, float* grad_params, float* grad_encoder,
+                                void* stream, uint32_t flags);
+
+/* One step of the first training phase: forward with latents from the
+ * encoder, the loss of nam_train_step, backward through decoder, frame and
+ * encoder, Adam (lr_params) on the frame, decoder and encoder masters.  The
+ * latent texture is untouched.  *loss_out as in nam_train_step. */
+nam_status nam_train_step_encoded(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* attrs,
+                                  const float* target_rgb, int64_t n, const nam_adam* opt, float* loss_out,
+                                  void* stream, uint32_t flags);
+
+/* Device pointer to the encoder's FP32 masters (layout of encoder_weights);
+ * owned by the material. */
+nam_status nam_material_encoder(nam_ctx* ctx, nam_material m, float** encoder_dev);
 
 /* ------------------------------------------------------------------------ */
 /* serving: continuous batching of frames (Sec. 7.3 coherency analogue)      */

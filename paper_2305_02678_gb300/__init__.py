@@ -58,11 +58,12 @@ class Context:
         self.close()
 
     def material(self, W0, H0, L, pyramid, frame, decoder, precision=1, filter=0, address=0, trainable=False,
-                 act_scale=None, sampler=None):
+                 act_scale=None, sampler=None, encoder=None):
         """precision: NAM_PREC_F32/F16/FP8 (0/1/2); filter: trilinear/stochastic (0/1); address: wrap/clamp;
-        sampler: None or [(W, b)] * 4 of the 11-32-32-32-9 importance-sampling MLP."""
+        sampler: None or [(W, b)] * 4 of the 11-32-32-32-9 importance-sampling MLP;
+        encoder: None or [(W, b)] * 3 of the K-32-32-8 encoder of a trainable material."""
         return Material(self, W0, H0, L, pyramid, frame, decoder, precision, filter, address, trainable, act_scale,
-                        sampler)
+                        sampler, encoder)
 
     def stats(self):
         from . import binding as B
@@ -77,7 +78,7 @@ class Material:
     """A neural material resident on the device (pyramid + MLP weights)."""
 
     def __init__(self, ctx, W0, H0, L, pyramid, frame, decoder, precision, filter, address, trainable, act_scale,
-                 sampler=None):
+                 sampler=None, encoder=None):
         from . import binding as B
         self.ctx = ctx
         pyr = np.ascontiguousarray(pyramid)
@@ -110,7 +111,12 @@ class Material:
             smp = flatten_decoder(sampler)
             d.sampler_hidden = sampler[0][0].shape[0]
             d.sampler_weights = smp.ctypes.data
-        self._keep = [pyr, fr, dec, sc, smp]
+        enc = None
+        if encoder is not None:
+            enc = flatten_decoder(encoder)
+            d.encoder_inputs = encoder[0][0].shape[1]
+            d.encoder_weights = enc.ctypes.data
+        self._keep = [pyr, fr, dec, sc, smp, enc]
         self.h = B.nam_create_material(ctx.h, d)
         self._keep = []
         self.precision, self.filter, self.address = precision, filter, address

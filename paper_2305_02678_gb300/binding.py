@@ -28,6 +28,7 @@ NAM_OUT_COSINE = 1
 NAM_FAULT_NONE, NAM_FAULT_ALLOC, NAM_FAULT_LAUNCH, NAM_FAULT_STALL = 0, 1, 2, 3
 NAM_MAX_LEVELS, NAM_MAX_LAYERS = 16, 8
 NAM_FRAME_MLP, NAM_FRAME_PAPER = 0, 1
+NAM_ENCODER_HIDDEN, NAM_ENCODER_MAX_INPUTS = 32, 16
 
 QUERY_FIELDS = ("u", "v", "lod", "wix", "wiy", "wiz", "wox", "woy", "woz", "xi")
 
@@ -44,7 +45,7 @@ class nam_material_desc(C.Structure):
                 ("widths", C.c_int32 * (NAM_MAX_LAYERS + 1)), ("decoder_weights", C.c_void_p),
                 ("precision", C.c_int32), ("filter", C.c_int32), ("address", C.c_int32), ("trainable", C.c_int32),
                 ("fp8_act_scale", C.c_void_p), ("sampler_hidden", C.c_int32), ("sampler_weights", C.c_void_p),
-                ("frame_form", C.c_int32)]
+                ("frame_form", C.c_int32), ("encoder_inputs", C.c_int32), ("encoder_weights", C.c_void_p)]
 
 
 class nam_material_info(C.Structure):
@@ -88,7 +89,8 @@ class nam_stats(C.Structure):
 EXPORTS = ("nam_status_string", "nam_last_error_message", "nam_init", "nam_shutdown", "nam_check_device_error",
            "nam_create_material", "nam_destroy_material", "nam_material_get_info", "nam_material_params",
            "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_fp8_calibrate", "nam_sample", "nam_sample_pdf", "nam_backward", "nam_train_step",
-           "nam_train_step_noalloc", "nam_now",
+           "nam_train_step_noalloc", "nam_encode", "nam_encoder_bake", "nam_backward_encoded",
+           "nam_train_step_encoded", "nam_material_encoder", "nam_now",
            "nam_submit", "nam_poll", "nam_wait", "nam_cancel", "nam_get_stats", "nam_inject_fault",
            "nam_debug_mma_selftest", "nam_debug_mma_selftest_ts")
 
@@ -120,6 +122,11 @@ def _load():
         "nam_backward": (i32, [p, p, p, i64, p, p, p, p, u32]),
         "nam_train_step": (i32, [p, p, p, p, i64, p, p, p, u32]),
         "nam_train_step_noalloc": (i32, [p, p, p, p, i64, p, p, p, u32]),
+        "nam_encode": (i32, [p, p, p, i64, p, p]),
+        "nam_encoder_bake": (i32, [p, p, p, p]),
+        "nam_backward_encoded": (i32, [p, p, p, p, i64, p, p, p, p, u32]),
+        "nam_train_step_encoded": (i32, [p, p, p, p, p, i64, p, p, p, u32]),
+        "nam_material_encoder": (i32, [p, p, p]),
         "nam_fp8_calibrate": (i32, [p, p, p, i64, p, p]),
         "nam_sample": (i32, [p, p, p, i64, p, p, p, p]),
         "nam_sample_pdf": (i32, [p, p, p, i64, p, p]),
@@ -305,6 +312,44 @@ def nam_train_step_noalloc(ctx, mat, q, target_rgb, n, lr_params=1e-3, lr_pyrami
     _check(_lib.nam_train_step_noalloc(ctx, mat, C.byref(qs), ptr(target_rgb), int(n), C.byref(opt), C.byref(loss),
                                        _stream(stream), flags), "nam_train_step_noalloc")
     return loss.value
+
+
+def encoder_param_count(k_inputs):
+    """Parameters of the K -> 32 -> 32 -> 8 encoder (Sec. 5.1)."""
+    return 32 * k_inputs + 32 + 32 * 32 + 32 + 8 * 32 + 8
+
+
+def nam_encode(ctx, mat, attrs, n, z_out, stream=None):
+    _check(_lib.nam_encode(ctx, mat, ptr(attrs), int(n), ptr(z_out), _stream(stream)), "nam_encode")
+
+
+def nam_encoder_bake(ctx, mat, texel_attrs, stream=None):
+    _check(_lib.nam_encoder_bake(ctx, mat, ptr(texel_attrs), _stream(stream)), "nam_encoder_bake")
+
+
+def nam_backward_encoded(ctx, mat, q, attrs, n, grad_rgb, grad_params, grad_encoder, stream=None, flags=0):
+    qs = make_queries(q)
+    _check(_lib.nam_backward_encoded(ctx, mat, C.byref(qs), ptr(attrs), int(n), ptr(grad_rgb), ptr(grad_params),
+                                     ptr(grad_encoder), _stream(stream), flags), "nam_backward_encoded")
+
+
+def nam_train_step_encoded(ctx, mat, q, attrs, target_rgb, n, lr_params=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                           step=1, stream=None, flags=0, want_loss=True):
+    """One step of the encoder phase; returns the batch loss (synchronising
+    the stream) or None if want_loss is False."""
+    opt = nam_adam(lr_params, 0.0, beta1, beta2, eps, step)
+    loss = C.c_float(0.0)
+    qs = make_queries(q)
+    _check(_lib.nam_train_step_encoded(ctx, mat, C.byref(qs), ptr(attrs), ptr(target_rgb), int(n), C.byref(opt),
+                                       C.byref(loss) if want_loss else None, _stream(stream), flags),
+           "nam_train_step_encoded")
+    return loss.value if want_loss else None
+
+
+def nam_material_encoder(ctx, mat):
+    pe = C.c_void_p()
+    _check(_lib.nam_material_encoder(ctx, mat, C.byref(pe)), "nam_material_encoder")
+    return pe.value
 
 
 def nam_now():

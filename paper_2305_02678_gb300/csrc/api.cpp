@@ -179,6 +179,8 @@ static void free_material(nam_ctx* ctx, nam_material m) {
   cudaFree(m->adam_v);
   cudaFree(m->grad);
   cudaFree(m->train_scratch);
+  cudaFree(m->enc);
+  cudaFree(m->enc_scratch);
   budget_release(ctx, m->info.resident_bytes);
   delete m;
 }
@@ -270,6 +272,11 @@ nam_status nam::validate_desc(const nam_material_desc* d, Shape* shape, PyrDesc*
   if (d->sampler_hidden != 0 && d->sampler_hidden != 32)
     return fail(NAM_ERR_UNSUPPORTED, "sampler_hidden must be 0 or 32");
   if (d->sampler_hidden && !d->sampler_weights) return fail(NAM_ERR_INVALID_ARG, "sampler_weights is NULL");
+  if (d->encoder_inputs < 0 || d->encoder_inputs > NAM_ENCODER_MAX_INPUTS)
+    return fail(NAM_ERR_INVALID_ARG, "encoder_inputs %d not in [0, %d]", d->encoder_inputs, NAM_ENCODER_MAX_INPUTS);
+  if (d->encoder_inputs && !d->trainable)
+    return fail(NAM_ERR_UNSUPPORTED, "an encoder needs a trainable material (it exists only for training)");
+  if (d->encoder_inputs && !d->encoder_weights) return fail(NAM_ERR_INVALID_ARG, "encoder_weights is NULL");
   shape->H = H;
   shape->NH = d->n_layers - 1;
   shape->frame = paper ? 2 : (d->frame_hidden ? 1 : 0);
@@ -312,6 +319,13 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   cudaMemcpy(master.data() + nframe, d->decoder_weights, (np - nframe) * 4, kind);
   for (float v : master)
     if (!std::isfinite(v)) return fail(NAM_ERR_INVALID_ARG, "non-finite weight");
+  std::vector<float> encw;
+  if (d->encoder_inputs) {
+    encw.resize((size_t)encoder_params_of(d->encoder_inputs));
+    cudaMemcpy(encw.data(), d->encoder_weights, encw.size() * 4, kind);
+    for (float v : encw)
+      if (!std::isfinite(v)) return fail(NAM_ERR_INVALID_ARG, "non-finite encoder weight");
+  }
   std::vector<float> smp;
   if (d->sampler_hidden) {
     smp.resize(kSamplerFloats);
@@ -335,7 +349,10 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
       return fail(NAM_ERR_UNSUPPORTED, "no tensor-core kernel for this shape/precision");
     }
   }
-  uint64_t resident = pyr_bytes + blob_bytes + (uint64_t)np * 4 + (uint64_t)smp.size() * 4;
+  uint64_t resident = pyr_bytes + blob_bytes + (uint64_t)np * 4 + (uint64_t)smp.size() * 4 +
+                      4ull * encw.size() * 4;
+  m->enc_in = d->encoder_inputs;
+  m->enc_n = (int64_t)encw.size();
   m->pyr_off = (np + 3) / 4 * 4;
   if (d->trainable) {
     // FP32 pyramid masters are the pyramid itself; Adam moments and gradients
@@ -352,6 +369,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   if (!e) e = dev_alloc(ctx, (void**)&m->params, np * 4);
   if (!e && blob_bytes) e = dev_alloc(ctx, &m->blob, blob_bytes);
   if (!e && !smp.empty()) e = dev_alloc(ctx, (void**)&m->sampler, smp.size() * 4);
+  if (!e && !encw.empty()) e = dev_alloc(ctx, (void**)&m->enc, 4 * encw.size() * 4);
   if (!e && d->trainable) {
     const size_t nb = (m->pyr_off + pd.texels * 8) * 4;
     e = dev_alloc(ctx, (void**)&m->adam_m, nb);
@@ -366,6 +384,10 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
                       d->params_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
   if (!e) e = (int)cudaMemcpy(m->params, master.data(), np * 4, cudaMemcpyHostToDevice);
   if (!e && !smp.empty()) e = (int)cudaMemcpy(m->sampler, smp.data(), smp.size() * 4, cudaMemcpyHostToDevice);
+  if (!e && !encw.empty()) {
+    e = (int)cudaMemcpy(m->enc, encw.data(), encw.size() * 4, cudaMemcpyHostToDevice);
+    if (!e) e = (int)cudaMemset(m->enc + encw.size(), 0, 3 * encw.size() * 4);  // gradient, Adam m, v
+  }
   if (!e && blob_bytes) {
     std::vector<uint8_t> blob(blob_bytes);
     if (pack_tc_blob(sh, d->precision, nframe ? master.data() : nullptr, master.data() + nframe,

@@ -179,8 +179,15 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
     // ---- quad: latent, frame MLP, frame, decoder input ----------------------
     {
       float z[8];
-      const float xi = A.q.xi ? A.q.xi[i] : 0.0f;
-      fetch_latent<F16>(A.pyr, A.pyramid, A.q.u[i], A.q.v[i], A.q.lod[i], xi, z);
+      if (A.z_in) {
+        // encoder phase (Sec. 5.1): the latent is given, the texture bypassed
+        const float4 a = reinterpret_cast<const float4*>(A.z_in + 8 * i)[0];
+        const float4 b = reinterpret_cast<const float4*>(A.z_in + 8 * i)[1];
+        z[0] = a.x; z[1] = a.y; z[2] = a.z; z[3] = a.w; z[4] = b.x; z[5] = b.y; z[6] = b.z; z[7] = b.w;
+      } else {
+        const float xi = A.q.xi ? A.q.xi[i] : 0.0f;
+        fetch_latent<F16>(A.pyr, A.pyramid, A.q.u[i], A.q.v[i], A.q.lod[i], xi, z);
+      }
       const float wi[3] = {A.q.wix[i], A.q.wiy[i], A.q.wiz[i]};
       const float wo[3] = {A.q.wox[i], A.q.woy[i], A.q.woz[i]};
       float x[14];
@@ -501,8 +508,14 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
 #pragma unroll
         for (int c = 0; c < 8; ++c) dz[c] += quad_sum(gz[c]);
       }
-      // pyramid scatter: z = sum_k w_k texel_k  =>  dtexel_k += w_k dz
-      if (valid && A.grad_pyramid) {
+      if (A.dz_out) {
+        // encoder phase: dL/dz goes to the encoder's backward
+        if (valid && p == 0) {
+          reinterpret_cast<float4*>(A.dz_out + 8 * i)[0] = make_float4(dz[0], dz[1], dz[2], dz[3]);
+          reinterpret_cast<float4*>(A.dz_out + 8 * i)[1] = make_float4(dz[4], dz[5], dz[6], dz[7]);
+        }
+      } else if (valid && A.grad_pyramid) {
+        // pyramid scatter: z = sum_k w_k texel_k  =>  dtexel_k += w_k dz
         const float u = A.q.u[i], v = A.q.v[i], lod = A.q.lod[i];
         const float xi = A.q.xi ? A.q.xi[i] : 0.0f;
         LevelPick lp = pick_levels(A.pyr, lod);

@@ -29,8 +29,15 @@ struct nam_material_s {
   float* adam_m = nullptr;    // trainable: [pyr_off + texels*8]
   float* adam_v = nullptr;
   float* grad = nullptr;      // trainable: gradient buffer, same layout
-  void* train_scratch = nullptr;  // trainable: rgb, grad_rgb, loss for a batch
+  void* train_scratch = nullptr;  // trainable: the training step's loss accumulator
   size_t train_scratch_bytes = 0;
+  // encoder (Sec. 5.1), trainable materials created with encoder_inputs > 0:
+  // one allocation of 4 x enc_n floats: masters, gradient, Adam m, Adam v
+  int32_t enc_in = 0;
+  int64_t enc_n = 0;
+  float* enc = nullptr;
+  void* enc_scratch = nullptr;    // a batch's latents and their gradients
+  size_t enc_scratch_bytes = 0;
   nam_material_info info{};
 };
 

@@ -135,6 +135,11 @@ struct BackwardArgs {
   const float* target;
   float* loss_acc;
   float loss_inv;
+  // encoder phase (Sec. 5.1): when z_in is set the latent of query i is
+  // z_in[8 i ..] (the texture is not read) and, when dz_out is set, dL/dz of
+  // query i goes to dz_out[8 i ..] instead of the pyramid gradient
+  const float* z_in;
+  float* dz_out;
   float* grad_params;
   float* grad_pyramid;     // may be null
   uint32_t flags;
@@ -146,6 +151,14 @@ struct BackwardArgs {
   int32_t tiny_n, cta_n;
 };
 int launch_backward(const BackwardArgs& a, void* stream);
+
+// encoder (Sec. 5.1): K -> 32 -> 32 -> 8, ReLU hidden layers, linear output;
+// W = per layer W[out][in] then b[out]
+inline int64_t encoder_params_of(int K) { return 32 * (int64_t)K + 32 + 32 * 32 + 32 + 8 * 32 + 8; }
+int launch_encode(const float* W, int K, const float* attrs, int64_t n, float* z_out, int num_sms, void* stream);
+// accumulates the gradient of sum <dz, encoder(attrs)> into grad (layout of W)
+int launch_encoder_backward(const float* W, int K, const float* attrs, const float* dz, int64_t n, float* grad,
+                            int num_sms, void* stream);
 int launch_loss(const float* rgb, const float* target, int64_t n, float* grad_rgb, float* loss_accum,
                 void* stream);
 int launch_adam(float* p, const float* g, float* m, float* v, int64_t count, float lr, float b1, float b2,
