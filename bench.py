@@ -431,6 +431,9 @@ def run_ours(args):
     training = None
     if args.train_steps > 0 and rank == 0:
         training = run_training(ctx, dev, stream, args.train_steps)
+        if args.train_steps >= 10:
+            training["encoder_bootstrap"] = run_encoder_bootstrap(ctx, dev, stream, args.train_steps // 2,
+                                                                  args.train_steps - args.train_steps // 2)
     # ---- serving stream ---------------------------------------------------
     serving = None
     if not args.no_serve and rank == 0:
@@ -647,6 +650,94 @@ def run_training(ctx, dev, stream, steps, batch=262144, pool=8):
             "note": "each step: one kernel for the FP32 forward, the log-L1 loss and the hand-written reverse "
                     "mode (atomic pyramid scatter), then Adam over 11.18 M pyramid + MLP parameters; loss read "
                     "back every 100 steps"}
+
+
+def run_encoder_bootstrap(ctx, dev, stream, enc_steps, fine_steps, batch=131072, pool=4):
+    """The two training phases of Sec. 5.1 on the training workload's material
+    and decoder shape, with footprint-filtered data (a query at lod l stands
+    for a Gaussian footprint of 2^l texels; its target BRDF and material
+    parameters are means over up to 8 points of it): an encoder 4-32-32-8
+    from the parameters (albedo RGB, roughness) to the latent, trained
+    end-to-end with the decoder for `enc_steps` steps; the 1024^2 x 8 pyramid
+    (11 levels) baked from it (coarse levels from 2x2-mean parameters); then
+    `fine_steps` texel finetuning steps.  Against direct optimisation of the
+    random texture for enc_steps + fine_steps steps on the same batches."""
+    import torch
+
+    import workloads as W
+    from paper_2305_02678_gb300 import binding as B
+    w = W.workload(4)
+    m = w["model"]
+    target = w["target"]
+    enc = W.make_mlp(W.rng_streams(W.SEEDS[4] + 21, 1)[0], (4, 32, 32, 8))
+    rng = W.rng_streams(W.SEEDS[4] + 22, 2)
+    batches = []
+    for _ in range(pool):
+        q = W.uniform_queries(rng[0], batch, 10.0)
+        y, a = W.filtered_targets(rng[1], target, q, w["W0"])
+        batches.append(({k: torch.from_numpy(v).to(dev) for k, v in q.items() if k != "xi"},
+                        torch.from_numpy(y).to(dev), torch.from_numpy(a).to(dev)))
+    ta = torch.from_numpy(W.texel_attributes(target, w["W0"], w["H0"], w["L"])).to(dev)
+
+    def every_100(s, last):
+        return s % 100 == 0 or s == last or s == 1
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    mat = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"], precision=B.NAM_PREC_F32,
+                       trainable=True, encoder=enc)
+    enc_losses = []
+    for s in range(1, enc_steps + 1):
+        dq, y, a = batches[s % pool]
+        if s == 4:
+            ev[0].record(stream)
+        l = B.nam_train_step_encoded(ctx.h, mat.h, dq, a, y, batch, lr_params=1e-3, step=s, stream=stream,
+                                     want_loss=every_100(s, enc_steps))
+        if l is not None:
+            enc_losses.append(l)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ev[2].record(stream)
+    B.nam_encoder_bake(ctx.h, mat.h, ta, stream)
+    ev[3].record(stream)
+    fine_losses = []
+    for s in range(1, fine_steps + 1):
+        dq, y, _ = batches[s % pool]
+        if s == 4:
+            ev[4].record(stream)
+        l = B.nam_train_step(ctx.h, mat.h, dq, y, batch, step=s, stream=stream, want_loss=every_100(s, fine_steps))
+        if l is not None:
+            fine_losses.append(l)
+    ev[5].record(stream)
+    torch.cuda.synchronize()
+    enc_ms = ev[0].elapsed_time(ev[1]) / (enc_steps - 3)
+    bake_ms = ev[2].elapsed_time(ev[3])
+    fine_ms = ev[4].elapsed_time(ev[5]) / (fine_steps - 3)
+    texels = mat.info.texels
+    mat.destroy()
+    # direct optimisation of the random texture on the same batches
+    mat = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"], precision=B.NAM_PREC_F32,
+                       trainable=True)
+    total = enc_steps + fine_steps
+    direct = []
+    for s in range(1, total + 1):
+        dq, y, _ = batches[s % pool]
+        l = B.nam_train_step(ctx.h, mat.h, dq, y, batch, step=s, stream=stream, want_loss=every_100(s, total))
+        if l is not None:
+            direct.append(l)
+    mat.destroy()
+    ctx.check()
+    return {"workload": "encoder-bootstrap-1024sq-131072-filtered", "encoder": "4-32-32-8", "batch": batch,
+            "encoder_steps": enc_steps, "encoder_ms_per_step": round(enc_ms, 4),
+            "encoder_samples_per_s": round(batch * 1e3 / enc_ms, 1),
+            "encoder_loss_every_100": [round(x, 5) for x in enc_losses],
+            "bake_ms": round(bake_ms, 4), "bake_texels": texels,
+            "finetune_steps": fine_steps, "finetune_ms_per_step": round(fine_ms, 4),
+            "finetune_loss_every_100": [round(x, 5) for x in fine_losses],
+            "direct_steps": total, "direct_loss_every_100": [round(x, 5) for x in direct],
+            "note": "footprint-filtered targets and parameters; encoder phase: encoder kernel, fused forward + "
+                    "loss + reverse mode with latents from the encoder, encoder reverse mode, Adam on frame, "
+                    "decoder and encoder; bake: the encoder over every texel; finetuning and direct: the "
+                    "training step of the training leg"}
 
 
 def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_frames=None):

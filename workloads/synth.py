@@ -277,7 +277,11 @@ class ProceduralBRDF:
 
     def __call__(self, u, v, wi, wo):
         """wi, wo: [3, n] float64.  Returns [n, 3] float64."""
-        a, r = self.params(u, v)
+        return self.from_params(*self.params(u, v), wi, wo)
+
+    @staticmethod
+    def from_params(a, r, wi, wo):
+        """The BRDF for albedo a [n, 3] and roughness r [n]."""
         alpha = r * r
         ci, co = wi[2], wo[2]
         h = wi + wo
@@ -385,3 +389,32 @@ def texel_attributes(target: ProceduralBRDF, W0: int, H0: int, L: int) -> np.nda
         out.append(lvl.reshape(-1, 4))
         w, h = w2, h2
     return np.concatenate(out).astype(np.float32)
+
+
+def filtered_targets(rng, target: ProceduralBRDF, q, W0: int, max_samples: int = 8):
+    """Footprint-filtered training data for queries q (the data generation of
+    the paper's training, as this module reads it): a query at lod l stands
+    for a Gaussian footprint of standard deviation 2^l / (2 W0) in uv; its
+    target is the mean of the procedural BRDF, and its material parameters
+    the mean of (albedo RGB, roughness), over m = min(max_samples, ceil(4^l))
+    points drawn from that Gaussian (one point, the query itself, at lod 0),
+    uv wrapped.  Returns (target [n, 3] float32, attributes [n, 4] float32)."""
+    n = q["u"].shape[0]
+    lod = q["lod"].astype(np.float64)
+    m = np.minimum(max_samples, np.ceil(4.0 ** lod)).astype(np.int64)
+    sigma = np.exp2(lod) / (2.0 * W0)
+    S = max_samples
+    off = rng.normal(size=(2, S, n)) * sigma[None, None, :]
+    off[:, 0, m == 1] = 0.0
+    us = np.mod(q["u"].astype(np.float64)[None, :] + off[0], 1.0)
+    vs = np.mod(q["v"].astype(np.float64)[None, :] + off[1], 1.0)
+    take = np.arange(S)[:, None] < m[None, :]            # [S, n]
+    wi = np.stack([q["wix"], q["wiy"], q["wiz"]]).astype(np.float64)
+    wo = np.stack([q["wox"], q["woy"], q["woz"]]).astype(np.float64)
+    a, r = target.params(us.ravel(), vs.ravel())
+    f = target.from_params(a, r, np.tile(wi, S), np.tile(wo, S)).reshape(S, n, 3)
+    k = np.concatenate([a, r[:, None]], axis=1).reshape(S, n, 4)
+    w = take / m[None, :]
+    y = np.einsum("sn,snc->nc", w, f)
+    attrs = np.einsum("sn,snc->nc", w, k)
+    return y.astype(np.float32), attrs.astype(np.float32)
