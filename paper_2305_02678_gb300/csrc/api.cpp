@@ -735,6 +735,58 @@ extern "C" nam_status nam_eval_multi(nam_ctx* ctx, const nam_material* mats, int
   return NAM_OK;
 }
 
+extern "C" nam_status nam_eval_binned(nam_ctx* ctx, const nam_material* mats, int32_t nmat, const nam_queries* q,
+                                      const int32_t* material_ids, int64_t n, float* rgb_out, void* stream,
+                                      uint32_t flags) {
+  if (!ctx) return fail(NAM_ERR_INVALID_ARG, "nam_eval_binned: NULL context");
+  if (n < 0) return fail(NAM_ERR_INVALID_ARG, "n < 0");
+  if (n > INT32_MAX) return fail(NAM_ERR_INVALID_ARG, "n beyond 2^31 - 1");
+  if (nmat > NAM_MAX_BIN_MATERIALS) return fail(NAM_ERR_INVALID_ARG, "more than %d materials", NAM_MAX_BIN_MATERIALS);
+  nam_status st = check_multi(ctx, mats, nmat);
+  if (st) return st;
+  if (n == 0) return NAM_OK;
+  if (!material_ids || !rgb_out) return fail(NAM_ERR_INVALID_ARG, "NULL material ids or output");
+  st = check_queries(mats[0], q);
+  if (st) return st;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // one stream-ordered allocation: binning scratch, pyramid and weight pointers
+  const size_t sb = bin_scratch_bytes(n, nmat, q->xi != nullptr);
+  const size_t pb = (size_t)nmat * sizeof(void*);
+  std::vector<uint8_t> host(2 * pb);
+  for (int32_t k = 0; k < nmat; ++k) {
+    const void* p = mats[k]->pyramid;
+    const void* w = mats[k]->blob;
+    std::memcpy(host.data() + k * sizeof(void*), &p, sizeof p);
+    std::memcpy(host.data() + pb + k * sizeof(void*), &w, sizeof w);
+  }
+  void* dev = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&dev, sb + host.size(), ctx->pool, s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "nam_eval_binned: scratch allocation");
+  uint8_t* tab = (uint8_t*)dev + sb;
+  e = cudaMemcpyAsync(tab, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(dev, s);
+    return cuda_fail((int)e, "nam_eval_binned: table upload");
+  }
+  BinArgs a;
+  fill_launch(ctx, mats[0], q, 0, nullptr, flags, &a.L);
+  a.L.mats.pyramid = (const void* const*)tab;
+  a.L.mats.weights = (const void* const*)(tab + pb);
+  a.L.mats.nmat = nmat;
+  a.ids = material_ids;
+  a.nmat = nmat;
+  a.n = n;
+  a.rgb_out = rgb_out;
+  a.precision = mats[0]->desc.precision;
+  a.num_sms = ctx->num_sms;
+  a.scratch = dev;
+  int le = launch_bin_eval(a, s);
+  cudaFreeAsync(dev, s);
+  if (le) return cuda_fail(le, "nam_eval_binned: launch");
+  return NAM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // diagnostics
 // ---------------------------------------------------------------------------

@@ -1,0 +1,210 @@
+// Material binning for queries whose material varies per query (Sec. 7.3:
+// the paper has the ray tracer reorder shading work so that threads that
+// evaluate the same material run together).  Four passes on the device:
+//   count   per-material histogram (warp-aggregated atomics);
+//   plan    exclusive scan of the counts into per-material cursors, and the
+//           chunk table of the tensor-core kernel (each material's range cut
+//           into 128-query chunks; empty slots have count 0);
+//   scatter each query's fields, read in the caller's order, written to its
+//           slot of its material's range (warp-aggregated cursor bumps), with
+//           the slot's original index;
+//   unbin   the kernel's outputs, read in binned order, written back to the
+//           caller's order.
+// The order inside a material's range is the order in which warps claim
+// slots; it does not change any result, since each query is evaluated on its
+// own.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace nam {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__global__ void __launch_bounds__(kThreads) bin_count_kernel(const int32_t* __restrict__ ids, int64_t n, int nmat,
+                                                             uint32_t* __restrict__ counts, int* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    int m = -1;
+    if (i < n) {
+      m = __ldg(ids + i);
+      if (m < 0 || m >= nmat) {
+        record_error(err, DEVERR_BOUNDS);
+        m = -1;
+      }
+    }
+    const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
+    if (m >= 0) {
+      const uint32_t same = __match_any_sync(act, m);
+      if (lane == __ffs(same) - 1) atomicAdd(counts + m, (uint32_t)__popc(same));
+    }
+  }
+}
+
+// One block: cursors[m] = sum of counts before m; chunks[c] for every slot
+// c < max_chunks (a material with k queries owns ceil(k / 128) chunks).
+__global__ void __launch_bounds__(1024) bin_plan_kernel(const uint32_t* __restrict__ counts, int nmat,
+                                                        uint32_t* __restrict__ cursors, Chunk* __restrict__ chunks,
+                                                        int32_t max_chunks) {
+  extern __shared__ uint32_t sh[];
+  uint32_t* qoff = sh;             // [nmat + 1] first query of each material
+  uint32_t* coff = sh + nmat + 1;  // [nmat + 1] first chunk of each material
+  if (threadIdx.x == 0) {
+    uint32_t q = 0, c = 0;
+    for (int m = 0; m < nmat; ++m) {
+      qoff[m] = q;
+      coff[m] = c;
+      q += counts[m];
+      c += (counts[m] + 127) / 128;
+    }
+    qoff[nmat] = q;
+    coff[nmat] = c;
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < nmat; m += blockDim.x) cursors[m] = qoff[m];
+  const uint32_t used = coff[nmat];
+  for (int32_t c = threadIdx.x; c < max_chunks; c += blockDim.x) {
+    Chunk ch;
+    if ((uint32_t)c < used) {
+      int lo = 0, hi = nmat - 1;  // the material whose chunk range holds c
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (coff[mid] <= (uint32_t)c) lo = mid;
+        else hi = mid - 1;
+      }
+      const uint32_t k = (uint32_t)c - coff[lo];
+      ch.start = (int64_t)qoff[lo] + 128ll * k;
+      const uint32_t left = qoff[lo + 1] - (qoff[lo] + 128u * k);
+      ch.count = (int32_t)(left < 128u ? left : 128u);
+      ch.material = lo;
+    } else {
+      ch.start = 0;
+      ch.count = 0;
+      ch.material = 0;
+    }
+    chunks[c] = ch;
+  }
+}
+
+struct Binned {
+  float *u, *v, *lod, *xi, *wix, *wiy, *wiz, *wox, *woy, *woz;
+};
+
+__global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, const int32_t* __restrict__ ids,
+                                                               int64_t n, int nmat, uint32_t* __restrict__ cursors,
+                                                               Binned out, int32_t* __restrict__ orig) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+    const int64_t i = base + threadIdx.x;
+    int m = -1;
+    if (i < n) {
+      m = __ldg(ids + i);
+      if (m >= nmat) m = -1;
+    }
+    const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
+    if (m < 0) continue;
+    const uint32_t same = __match_any_sync(act, m);
+    const int leader = __ffs(same) - 1;
+    uint32_t slot = 0;
+    if (lane == leader) slot = atomicAdd(cursors + m, (uint32_t)__popc(same));
+    slot = __shfl_sync(same, slot, leader) + __popc(same & lanemask_lt());
+    out.u[slot] = __ldg(q.u + i);
+    out.v[slot] = __ldg(q.v + i);
+    out.lod[slot] = __ldg(q.lod + i);
+    if (q.xi) out.xi[slot] = __ldg(q.xi + i);
+    out.wix[slot] = __ldg(q.wix + i);
+    out.wiy[slot] = __ldg(q.wiy + i);
+    out.wiz[slot] = __ldg(q.wiz + i);
+    out.wox[slot] = __ldg(q.wox + i);
+    out.woy[slot] = __ldg(q.woy + i);
+    out.woz[slot] = __ldg(q.woz + i);
+    orig[slot] = (int32_t)i;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) unbin_kernel(const float* __restrict__ binned, const int32_t* __restrict__ orig,
+                                                         int64_t n, float* __restrict__ rgb) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t i = __ldg(orig + p);
+    if (i < 0) continue;  // slot of a query with an invalid material id
+    rgb[3 * (int64_t)i + 0] = binned[3 * p + 0];
+    rgb[3 * (int64_t)i + 1] = binned[3 * p + 1];
+    rgb[3 * (int64_t)i + 2] = binned[3 * p + 2];
+  }
+}
+
+int grid_for(int64_t n, int num_sms) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)num_sms * 8;
+  return (int)(g < cap ? g : cap);
+}
+
+}  // namespace
+
+size_t bin_scratch_bytes(int64_t n, int nmat, bool xi) {
+  const size_t f = ((size_t)n * 4 + 255) / 256 * 256;
+  return (xi ? 10 : 9) * f + f /* orig */ + 3 * f /* binned rgb */ + 2 * (((size_t)nmat * 4 + 255) / 256 * 256) +
+         ((size_t)max_bin_chunks(n, nmat) * sizeof(Chunk) + 255) / 256 * 256;
+}
+
+int32_t max_bin_chunks(int64_t n, int nmat) { return (int32_t)((n + 127) / 128 + nmat); }
+
+int launch_bin_eval(const BinArgs& a, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = a.n;
+  const size_t f = ((size_t)n * 4 + 255) / 256 * 256;
+  uint8_t* p = (uint8_t*)a.scratch;
+  Binned b;
+  b.u = (float*)p; p += f;
+  b.v = (float*)p; p += f;
+  b.lod = (float*)p; p += f;
+  b.wix = (float*)p; p += f;
+  b.wiy = (float*)p; p += f;
+  b.wiz = (float*)p; p += f;
+  b.wox = (float*)p; p += f;
+  b.woy = (float*)p; p += f;
+  b.woz = (float*)p; p += f;
+  b.xi = nullptr;
+  if (a.L.q.xi) {
+    b.xi = (float*)p;
+    p += f;
+  }
+  int32_t* orig = (int32_t*)p; p += f;
+  float* brgb = (float*)p; p += 3 * f;
+  const size_t mb = ((size_t)a.nmat * 4 + 255) / 256 * 256;
+  uint32_t* counts = (uint32_t*)p; p += mb;
+  uint32_t* cursors = (uint32_t*)p; p += mb;
+  Chunk* chunks = (Chunk*)p;
+  const int32_t maxc = max_bin_chunks(n, a.nmat);
+
+  int e = (int)cudaMemsetAsync(counts, 0, (size_t)a.nmat * 4, s);
+  if (!e) e = (int)cudaMemsetAsync(orig, 0xff, (size_t)n * 4, s);
+  if (e) return e;
+  const int g = grid_for(n, a.num_sms);
+  bin_count_kernel<<<g, kThreads, 0, s>>>(a.ids, n, a.nmat, counts, a.L.err);
+  bin_plan_kernel<<<1, 1024, 2 * (a.nmat + 1) * sizeof(uint32_t), s>>>(counts, a.nmat, cursors, chunks, maxc);
+  bin_scatter_kernel<<<g, kThreads, 0, s>>>(a.L.q, a.ids, n, a.nmat, cursors, b, orig);
+  e = (int)cudaGetLastError();
+  if (e) return e;
+  LaunchCommon L = a.L;
+  L.q = QueryPtrs{b.u, b.v, b.lod, b.wix, b.wiy, b.wiz, b.wox, b.woy, b.woz, b.xi};
+  L.rgb = brgb;
+  L.chunks = chunks;
+  L.n_chunks = maxc;
+  e = launch_material(L, a.precision, stream);
+  if (e) return e;
+  unbin_kernel<<<g, kThreads, 0, s>>>(brgb, orig, n, a.rgb_out);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace nam

@@ -152,6 +152,25 @@ struct BackwardArgs {
 };
 int launch_backward(const BackwardArgs& a, void* stream);
 
+// the evaluation launch for a material's precision (tensor-core or FP32 path)
+int launch_material(const LaunchCommon& L, int precision, void* stream);
+
+// Material binning (per-query material ids): count, plan, scatter into a
+// binned copy of the queries, one chunked launch, unbin the outputs.
+struct BinArgs {
+  LaunchCommon L;          // caller's query pointers, flags, error word, materials table
+  const int32_t* ids;      // [n] material of each query
+  int32_t nmat;
+  int64_t n;
+  float* rgb_out;          // [n][3], the caller's order
+  int precision;
+  int num_sms;
+  void* scratch;           // bin_scratch_bytes(n, nmat, xi) bytes, 256-byte aligned
+};
+int32_t max_bin_chunks(int64_t n, int nmat);
+size_t bin_scratch_bytes(int64_t n, int nmat, bool xi);
+int launch_bin_eval(const BinArgs& a, void* stream);
+
 // encoder (Sec. 5.1): K -> 32 -> 32 -> 8, ReLU hidden layers, linear output;
 // W = per layer W[out][in] then b[out]
 inline int64_t encoder_params_of(int K) { return 32 * (int64_t)K + 32 + 32 * 32 + 32 + 8 * 32 + 8; }
