@@ -423,6 +423,10 @@ def run_ours(args):
     paper = None
     if not args.no_sweep:
         paper = run_paper_decoders(ctx, dev, stream, flush, w, dq, n, args)
+    # ---- per-pixel materials through the binning pre-pass ------------------
+    binned = None
+    if not args.no_sweep:
+        binned = run_binned(ctx, dev, stream, flush, w, dq, n, args)
     # ---- importance sampling on the 1080p frame ------------------------------
     sampling = None
     if not args.no_sweep:
@@ -467,6 +471,7 @@ def run_ours(args):
             "precision_sweep": sweep,
             "precision_sweep_3840x2160": sweep4k,
             "paper_decoders": paper,
+            "binned_materials": binned,
             "importance_sampling": sampling,
             "training": training,
             "serving": serving,
@@ -540,6 +545,40 @@ def run_paper_decoders(ctx, dev, stream, flush, w, dq, n, args):
         out[f"{NH}x{H}_evals_per_s"] = round(n / (t * 1e-3), 1)
         mat.destroy()
     return out
+
+
+def run_binned(ctx, dev, stream, flush, w, dq, n, args, n_mat=16):
+    """Per-query material ids with no tile coherence: 16 FP16 materials (the
+    1080p pyramid, seeded decoders and frame MLPs of their own), a uniformly
+    random material per pixel, evaluated through nam_eval_binned (device
+    histogram, scan, scatter into material ranges, one chunked launch,
+    unbin); against the single-material launch of the headline."""
+    import torch
+
+    import workloads as W
+    from paper_2305_02678_gb300 import binding as B
+    rng = W.rng_streams(W.SEEDS[2] + 31, n_mat + 1)
+    mats = []
+    for k in range(n_mat):
+        model = W.make_model(rng[k], (14, 64, 64, 3), (8, 16, 6))
+        mats.append(ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], model["frame"], model["decoder"],
+                                 precision=B.NAM_PREC_F16))
+    ids = torch.from_numpy(rng[n_mat].integers(0, n_mat, n).astype(np.int32)).to(dev)
+    o = torch.empty((n, 3), device=dev)
+    handles = [m.h for m in mats]
+    t = statistics.fmean(time_launches(lambda: B.nam_eval_binned(ctx.h, handles, dq, ids, n, o, stream, 0),
+                                       max(3, args.steps // 2), 2, flush, stream))
+    t1 = statistics.fmean(time_launches(lambda: B.nam_eval(ctx.h, mats[0].h, dq, n, o, stream, 0),
+                                        max(3, args.steps // 2), 2, flush, stream))
+    for m in mats:
+        m.destroy()
+    ctx.check()
+    return {"workload": f"fp16-2048sq-1920x1080, {n_mat} materials, material drawn per pixel",
+            "binned_ms": round(t, 4), "binned_evals_per_s": round(n / (t * 1e-3), 1),
+            "single_material_ms": round(t1, 4), "overhead_vs_single": round(t / t1, 3),
+            "note": "binning passes (count, plan, scatter of 40 B of query fields per query, unbin of the RGB) "
+                    "plus the chunked tensor-core launch, whose CTAs restage weights when a chunk's material "
+                    "changes"}
 
 
 def run_sampling(ctx, dev, stream, flush, w, dq, n, args):

@@ -309,6 +309,74 @@ nam_status nam_eval_binned(nam_ctx* ctx, const nam_material* mats, int32_t n_mat
                            const int32_t* material_ids, int64_t n, float* rgb_out, void* stream, uint32_t flags);
 
 /* ------------------------------------------------------------------------ */
+/* synthetic-scene harness                                                  */
+/* ------------------------------------------------------------------------ */
+/* A small analytic scene that exercises evaluation, sampling and densities
+ * the way a renderer does (the paper evaluates its materials inside a path
+ * tracer, Sec. 7): primary rays of a pinhole camera against a ground plane
+ * and spheres give a G-buffer; direct lighting from a constant sky is
+ * estimated with one BSDF sample (nam_sample) and one cosine-weighted light
+ * sample, combined with the power heuristic (Veach 1995), with analytic
+ * shadow rays; the shading queries of each material run on their own
+ * contiguous range (pixels binned by material on the device).
+ *
+ * Geometry: ground plane y = ground_y (normal +y, uv = (x, z) /
+ * ground_uv_scale, tangent +x) when ground_material >= 0; spheres with uv =
+ * (atan2(n_z, n_x) / 2 pi + 1/2, acos(n_y) / pi) and tangent along +phi.
+ * Shading frame (t, b, n) with b = n x t; the query directions are in it.
+ * Level of detail from a ray cone (Akenine-Moller et al. 2021): spread
+ * 2 tan(fov_y / 2) / height per unit distance, footprint = spread * t /
+ * max(|cos|, 0.05), converted to level-0 texels of a pyramid of width
+ * lod_base_width through the primitive's world-to-uv scale (ground: 1 /
+ * ground_uv_scale; sphere: 1 / (pi sqrt(2) r)); lod = log2(footprint). */
+typedef struct {
+  float center[3];
+  float radius;
+  int32_t material;
+} nam_sphere;
+
+typedef struct {
+  int32_t width, height;
+  float eye[3], target[3], up[3];
+  float fov_y;                /* radians */
+  float ground_y;
+  int32_t ground_material;    /* < 0: no ground plane */
+  float ground_uv_scale;
+  const nam_sphere* spheres;  /* host array */
+  int32_t n_spheres;
+  float sky_radiance;
+} nam_scene;
+
+/* Per-pixel G-buffer, device arrays of width * height entries (row-major
+ * from the top-left pixel): material (-1 where the ray leaves the scene), t,
+ * u, v, lod, frame [9] (t, b, n rows, world space), view [3] (the direction
+ * to the eye in the shading frame). */
+typedef struct {
+  int32_t* material;
+  float *t, *u, *v, *lod;
+  float* frame;
+  float* view;
+} nam_gbuffer;
+
+#define NAM_SCENE_MAX_SPHERES 64
+nam_status nam_scene_gbuffer(nam_ctx* ctx, const nam_scene* scene, int32_t lod_base_width, nam_gbuffer* out,
+                             void* stream);
+
+/* Direct lighting of every pixel (one sample per strategy) into image
+ * [pixels][3] (device); pixels that see the sky get sky_radiance.  Material
+ * k of the scene is mats[k]; all share pyramid geometry and MLP shape (as
+ * for nam_eval_multi) and need an importance sampler.  variates: device
+ * [pixels][5] in [0, 1): three for nam_sample, two for the light sample.
+ * Estimator per pixel with BSDF sample d_b (density p_b, the sampler's, with
+ * the view direction as its wi) and light sample d_l (density p_l = cos/pi):
+ * sum over s of V(d_s) L f(d_s, view) cos(d_s) / p_s(d_s) * p_s^2 / (p_b^2 +
+ * p_l^2), f the material's evaluation with wi = d_s, wo = view.  Synchronises
+ * the stream (per-material ranges are sized on the host); temporary device
+ * memory from the context's pool. */
+nam_status nam_scene_render_direct(nam_ctx* ctx, const nam_scene* scene, const nam_material* mats, int32_t n_materials,
+                                   const float* variates, float* image, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* differentiation and training (Sec. 5.2)                                  */
 /* ------------------------------------------------------------------------ */
 /* Reverse mode of nam_eval for a trainable (F32) material: given grad_rgb

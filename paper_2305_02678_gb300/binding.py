@@ -67,6 +67,39 @@ class nam_adam(C.Structure):
                 ("eps", C.c_float), ("step", C.c_int32)]
 
 
+class nam_sphere(C.Structure):
+    _fields_ = [("center", C.c_float * 3), ("radius", C.c_float), ("material", C.c_int32)]
+
+
+class nam_scene(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("eye", C.c_float * 3), ("target", C.c_float * 3),
+                ("up", C.c_float * 3), ("fov_y", C.c_float), ("ground_y", C.c_float), ("ground_material", C.c_int32),
+                ("ground_uv_scale", C.c_float), ("spheres", C.c_void_p), ("n_spheres", C.c_int32),
+                ("sky_radiance", C.c_float)]
+
+
+class nam_gbuffer(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("material", "t", "u", "v", "lod", "frame", "view")]
+
+
+NAM_SCENE_MAX_SPHERES = 64
+
+
+def make_scene(width, height, eye, target, up, fov_y, spheres, ground_y=0.0, ground_material=-1,
+               ground_uv_scale=1.0, sky_radiance=1.0):
+    """nam_scene (and the sphere array it points to, kept on the object);
+    spheres: list of (cx, cy, cz, radius, material)."""
+    arr = (nam_sphere * max(1, len(spheres)))()
+    for k, (cx, cy, cz, r, m) in enumerate(spheres):
+        arr[k] = nam_sphere((C.c_float * 3)(cx, cy, cz), r, m)
+    sc = nam_scene(width=width, height=height, eye=(C.c_float * 3)(*eye), target=(C.c_float * 3)(*target),
+                   up=(C.c_float * 3)(*up), fov_y=fov_y, ground_y=ground_y, ground_material=ground_material,
+                   ground_uv_scale=ground_uv_scale, spheres=C.addressof(arr), n_spheres=len(spheres),
+                   sky_radiance=sky_radiance)
+    sc._spheres = arr
+    return sc
+
+
 class nam_frame(C.Structure):
     _fields_ = [("n_queries", C.c_int64), ("q", nam_queries), ("items", C.c_void_p), ("n_items", C.c_int32),
                 ("n_materials", C.c_int32), ("materials", C.c_void_p), ("rgb_out", C.c_void_p),
@@ -90,7 +123,8 @@ EXPORTS = ("nam_status_string", "nam_last_error_message", "nam_init", "nam_shutd
            "nam_create_material", "nam_destroy_material", "nam_material_get_info", "nam_material_params",
            "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_eval_binned", "nam_fp8_calibrate", "nam_sample", "nam_sample_pdf", "nam_backward", "nam_train_step",
            "nam_train_step_noalloc", "nam_encode", "nam_encoder_bake", "nam_backward_encoded",
-           "nam_train_step_encoded", "nam_material_encoder", "nam_now",
+           "nam_train_step_encoded", "nam_material_encoder", "nam_scene_gbuffer", "nam_scene_render_direct",
+           "nam_now",
            "nam_submit", "nam_poll", "nam_wait", "nam_cancel", "nam_get_stats", "nam_inject_fault",
            "nam_debug_mma_selftest", "nam_debug_mma_selftest_ts")
 
@@ -128,6 +162,8 @@ def _load():
         "nam_backward_encoded": (i32, [p, p, p, p, i64, p, p, p, p, u32]),
         "nam_train_step_encoded": (i32, [p, p, p, p, p, i64, p, p, p, u32]),
         "nam_material_encoder": (i32, [p, p, p]),
+        "nam_scene_gbuffer": (i32, [p, p, i32, p, p]),
+        "nam_scene_render_direct": (i32, [p, p, p, i32, p, p, p]),
         "nam_fp8_calibrate": (i32, [p, p, p, i64, p, p]),
         "nam_sample": (i32, [p, p, p, i64, p, p, p, p]),
         "nam_sample_pdf": (i32, [p, p, p, i64, p, p]),
@@ -362,6 +398,19 @@ def nam_material_encoder(ctx, mat):
     pe = C.c_void_p()
     _check(_lib.nam_material_encoder(ctx, mat, C.byref(pe)), "nam_material_encoder")
     return pe.value
+
+
+def nam_scene_gbuffer(ctx, scene, lod_base_width, out, stream=None):
+    """out: dict of device tensors material (int32), t, u, v, lod [pixels], frame [pixels][9], view [pixels][3]."""
+    g = nam_gbuffer(**{k: ptr(out[k]) for k in ("material", "t", "u", "v", "lod", "frame", "view")})
+    _check(_lib.nam_scene_gbuffer(ctx, C.byref(scene), int(lod_base_width), C.byref(g), _stream(stream)),
+           "nam_scene_gbuffer")
+
+
+def nam_scene_render_direct(ctx, scene, mats, variates, image, stream=None):
+    arr = (C.c_void_p * len(mats))(*mats)
+    _check(_lib.nam_scene_render_direct(ctx, C.byref(scene), arr, len(mats), ptr(variates), ptr(image),
+                                        _stream(stream)), "nam_scene_render_direct")
 
 
 def nam_now():
