@@ -1,18 +1,22 @@
 // Material binning for queries whose material varies per query (Sec. 7.3:
 // the paper has the ray tracer reorder shading work so that threads that
 // evaluate the same material run together).  Four passes on the device:
-//   count   per-material histogram (warp-aggregated atomics);
+//   count   per-material histogram (each block sums a segment of queries in
+//           shared memory and adds one count per material to the global
+//           histogram: same-address atomics serialise in L2);
 //   plan    exclusive scan of the counts into per-material cursors, and the
 //           chunk table of the tensor-core kernel (each material's range cut
 //           into 128-query chunks; empty slots have count 0);
-//   scatter each query's fields, read in the caller's order, written to its
-//           slot of its material's range (warp-aggregated cursor bumps), with
-//           the slot's original index;
+//   scatter each block reserves, per material, one run of slots for its
+//           segment (one global atomic per block and material) and writes
+//           each query's fields, read in the caller's order, to a slot of its
+//           run, with the slot's original index;
 //   unbin   the kernel's outputs, read in binned order, written back to the
 //           caller's order.
-// The order inside a material's range is the order in which warps claim
-// slots; it does not change any result, since each query is evaluated on its
-// own.
+// Inside a material's range, runs follow the order in which blocks reserve
+// them and slots inside a run the order in which warps claim them; neither
+// changes any result, since each query is evaluated on its own, and a run
+// keeps its segment's screen-space neighbours together.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -28,14 +32,29 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+constexpr int kSeg = 1024;  // queries per block in count and scatter
+
+// warp-aggregated add of 1 per lane to cnt[m] in shared memory; returns the
+// value this lane's increment starts from
+__device__ __forceinline__ uint32_t warp_bump(uint32_t* cnt, int m, uint32_t act) {
+  const uint32_t same = __match_any_sync(act, m);
+  const int leader = __ffs(same) - 1;
+  uint32_t base = 0;
+  if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(cnt + m, (uint32_t)__popc(same));
+  return __shfl_sync(same, base, leader) + __popc(same & lanemask_lt());
+}
+
 __global__ void __launch_bounds__(kThreads) bin_count_kernel(const int32_t* __restrict__ ids, int64_t n, int nmat,
                                                              uint32_t* __restrict__ counts, int* err) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+  extern __shared__ uint32_t cnt[];  // [nmat]
+  for (int m = threadIdx.x; m < nmat; m += blockDim.x) cnt[m] = 0;
+  __syncthreads();
+  const int64_t seg = (int64_t)blockIdx.x * kSeg;
+  const int64_t end = seg + kSeg < n ? seg + kSeg : n;
+  for (int64_t base = seg; base < end; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;
     int m = -1;
-    if (i < n) {
+    if (i < end) {
       m = __ldg(ids + i);
       if (m < 0 || m >= nmat) {
         record_error(err, DEVERR_BOUNDS);
@@ -43,11 +62,11 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const int32_t* __re
       }
     }
     const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
-    if (m >= 0) {
-      const uint32_t same = __match_any_sync(act, m);
-      if (lane == __ffs(same) - 1) atomicAdd(counts + m, (uint32_t)__popc(same));
-    }
+    if (m >= 0) warp_bump(cnt, m, act);
   }
+  __syncthreads();
+  for (int m = threadIdx.x; m < nmat; m += blockDim.x)
+    if (cnt[m]) atomicAdd(counts + m, cnt[m]);
 }
 
 // One block: cursors[m] = sum of counts before m; chunks[c] for every slot
@@ -102,22 +121,33 @@ struct Binned {
 __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, const int32_t* __restrict__ ids,
                                                                int64_t n, int nmat, uint32_t* __restrict__ cursors,
                                                                Binned out, int32_t* __restrict__ orig) {
-  const int lane = threadIdx.x & 31;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+  extern __shared__ uint32_t sh[];
+  uint32_t* cnt = sh;             // [nmat] this segment's queries per material
+  uint32_t* run = sh + nmat;      // [nmat] first slot of the segment's run
+  const int64_t seg = (int64_t)blockIdx.x * kSeg;
+  const int64_t end = seg + kSeg < n ? seg + kSeg : n;
+  for (int m = threadIdx.x; m < nmat; m += blockDim.x) cnt[m] = 0;
+  __syncthreads();
+  for (int64_t base = seg; base < end; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;
-    int m = -1;
-    if (i < n) {
-      m = __ldg(ids + i);
-      if (m >= nmat) m = -1;
-    }
+    int m = i < end ? __ldg(ids + i) : -1;
+    if (m >= nmat) m = -1;
+    const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
+    if (m >= 0) warp_bump(cnt, m, act);
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < nmat; m += blockDim.x) {
+    run[m] = cnt[m] ? atomicAdd(cursors + m, cnt[m]) : 0u;
+    cnt[m] = 0;
+  }
+  __syncthreads();
+  for (int64_t base = seg; base < end; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    int m = i < end ? __ldg(ids + i) : -1;
+    if (m >= nmat) m = -1;
     const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
     if (m < 0) continue;
-    const uint32_t same = __match_any_sync(act, m);
-    const int leader = __ffs(same) - 1;
-    uint32_t slot = 0;
-    if (lane == leader) slot = atomicAdd(cursors + m, (uint32_t)__popc(same));
-    slot = __shfl_sync(same, slot, leader) + __popc(same & lanemask_lt());
+    const uint32_t slot = run[m] + warp_bump(cnt, m, act);
     out.u[slot] = __ldg(q.u + i);
     out.v[slot] = __ldg(q.v + i);
     out.lod[slot] = __ldg(q.lod + i);
@@ -141,12 +171,6 @@ __global__ void __launch_bounds__(kThreads) unbin_kernel(const float* __restrict
     rgb[3 * (int64_t)i + 1] = binned[3 * p + 1];
     rgb[3 * (int64_t)i + 2] = binned[3 * p + 2];
   }
-}
-
-int grid_for(int64_t n, int num_sms) {
-  int64_t g = (n + kThreads - 1) / kThreads;
-  const int64_t cap = (int64_t)num_sms * 8;
-  return (int)(g < cap ? g : cap);
 }
 
 }  // namespace
@@ -190,10 +214,10 @@ int launch_bin_eval(const BinArgs& a, void* stream) {
   int e = (int)cudaMemsetAsync(counts, 0, (size_t)a.nmat * 4, s);
   if (!e) e = (int)cudaMemsetAsync(orig, 0xff, (size_t)n * 4, s);
   if (e) return e;
-  const int g = grid_for(n, a.num_sms);
-  bin_count_kernel<<<g, kThreads, 0, s>>>(a.ids, n, a.nmat, counts, a.L.err);
+  const int gseg = (int)((n + kSeg - 1) / kSeg);
+  bin_count_kernel<<<gseg, kThreads, a.nmat * sizeof(uint32_t), s>>>(a.ids, n, a.nmat, counts, a.L.err);
   bin_plan_kernel<<<1, 1024, 2 * (a.nmat + 1) * sizeof(uint32_t), s>>>(counts, a.nmat, cursors, chunks, maxc);
-  bin_scatter_kernel<<<g, kThreads, 0, s>>>(a.L.q, a.ids, n, a.nmat, cursors, b, orig);
+  bin_scatter_kernel<<<gseg, kThreads, 2 * a.nmat * sizeof(uint32_t), s>>>(a.L.q, a.ids, n, a.nmat, cursors, b, orig);
   e = (int)cudaGetLastError();
   if (e) return e;
   LaunchCommon L = a.L;
@@ -203,7 +227,8 @@ int launch_bin_eval(const BinArgs& a, void* stream) {
   L.n_chunks = maxc;
   e = launch_material(L, a.precision, stream);
   if (e) return e;
-  unbin_kernel<<<g, kThreads, 0, s>>>(brgb, orig, n, a.rgb_out);
+  // one thread per slot: the scattered 12-byte writes want many in flight
+  unbin_kernel<<<(int)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(brgb, orig, n, a.rgb_out);
   return (int)cudaGetLastError();
 }
 
