@@ -415,6 +415,11 @@ def run_ours(args):
         sweep["fp8_speedup_vs_fp32"] = round(ms32 / ms8, 2)
         sweep["fp8_act_scales"] = [float(x) for x in scales]
         mat8.destroy()
+    # ---- serving stream (its own context; before the legs that leave large
+    # host and device allocations behind in this process) --------------------
+    serving = None
+    if not args.no_serve and rank == 0:
+        serving = run_serving(local, args.serve_frames)
     # ---- precision sweep at 3840x2160 ---------------------------------------
     sweep4k, outs4k = None, None
     if not args.no_sweep4k:
@@ -442,10 +447,6 @@ def run_ours(args):
         if args.train_steps >= 10:
             training["encoder_bootstrap"] = run_encoder_bootstrap(ctx, dev, stream, args.train_steps // 2,
                                                                   args.train_steps - args.train_steps // 2)
-    # ---- serving stream ---------------------------------------------------
-    serving = None
-    if not args.no_serve and rank == 0:
-        serving = run_serving(local, args.serve_frames)
 
     # ---- CPU baseline: the FP64 oracle on the host cores -------------------
     cpu = None
