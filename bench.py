@@ -368,6 +368,14 @@ def run_ours(args):
     staged_ms = statistics.fmean(staged_times)
     h2d = sum(int(t.numel()) * 4 for t in pinned.values())
     d2h = n * 12
+    # the host link's own rate: the step's input bytes pinned -> device as one
+    # copy (the e2e step moves them plus the RGB the other way, concurrently)
+    link_src = torch.empty(h2d // 4, dtype=torch.float32).pin_memory()
+    link_dst = torch.empty(h2d // 4, device=dev)
+    link_times = time_launches(lambda: link_dst.copy_(link_src, non_blocking=True), max(3, args.steps // 2), 2,
+                               flush, stream)
+    link_gbs = h2d / (statistics.fmean(link_times) * 1e-3) / 1e9
+    del link_src, link_dst
 
     # ---- roofline of the FP16 kernel ------------------------------------
     hbm, tflops, peak_kind = measured_peaks()
@@ -468,9 +476,14 @@ def run_ours(args):
             "e2e": {"value": round(world * n / (e2e_ms * 1e-3), 1), "unit": "evals/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_ms, 4),
                     "api": "nam_eval_host with pinned host queries and output: the kernel reads the inputs and "
-                           "writes the RGB in host memory over NVLink-C2C where the device reads host page "
-                           "tables, else staged copies",
-                    "staged_copies_ms_per_step": round(staged_ms, 4)},
+                           "writes the RGB in host memory directly where the device reads host page tables, "
+                           "else staged copies",
+                    "staged_copies_ms_per_step": round(staged_ms, 4),
+                    "link": {"h2d_gbs_measured": round(link_gbs, 1),
+                             "bound_ms": round(h2d / (link_gbs * 1e9) * 1e3, 4),
+                             "frac": round(h2d / (link_gbs * 1e9) * 1e3 / e2e_ms, 3),
+                             "note": "the input bytes of a step over the host link's measured rate (one pinned "
+                                     "copy of the same size); the RGB flows the other way at the same time"}},
             "gpu_launches": args.steps,
             "roofline": roofline,
             "precision_sweep": sweep,

@@ -224,9 +224,9 @@ nam_status nam_eval(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t 
 
 /* Same with HOST query and output arrays; synchronises the stream before it
  * returns.  Where the device reads host memory through the host's page
- * tables (cudaDevAttrPageableMemoryAccess, e.g. a GB300 with its CPU over
- * NVLink-C2C), the kernel reads the host queries and writes the host RGB
- * directly, with no staging copies; otherwise, or with NAM_HOST_STAGED in
+ * tables (cudaDevAttrPageableMemoryAccess, e.g. a GB300 sharing page tables
+ * with its Grace CPU), the kernel reads the host queries and writes the host
+ * RGB directly, with no staging copies; otherwise, or with NAM_HOST_STAGED in
  * flags, the inputs go to a device staging area owned by the context in up
  * to four chunks whose copies overlap the kernels (pinned host memory gives
  * full copy bandwidth).  Both paths give identical results. */
