@@ -4,7 +4,7 @@
 // Backward kernel: a CTA of 512 threads takes tiles of 128 queries.  Two
 // lane mappings share the tile:
 //  - a quad of four adjacent lanes per query, for the per-query work: the
-//    latent fetch, the frame MLP (lane p owns frame hidden units 4p..4p+3, the
+//    latent fetch, the frame MLP (lane p owns frame hidden units p + 4e, the
 //    six outputs are summed over the quad), the frame construction and its
 //    backward (redundant in the quad, ALU only), dL/dx (lane p owns x
 //    entries 4p..4p+3) and the pyramid scatter (lane p takes bilinear tap p;
@@ -194,22 +194,26 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
 #pragma unroll
       for (int c = 0; c < 8; ++c) x[c] = z[c];
       if (FRAME) {
+        // lane p owns frame hidden units p + 4e (rows 8 floats apart in four
+        // distinct bank groups)
         float hf[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float4* row = reinterpret_cast<const float4*>(&S.fW1[(4 * p + e) * 8]);
+          const float4* row = reinterpret_cast<const float4*>(&S.fW1[(p + 4 * e) * 8]);
           const float4 a = row[0], b = row[1];
-          float s = S.fb1[4 * p + e];
+          float s = S.fb1[p + 4 * e];
           s = dot4(a, make_float4(z[0], z[1], z[2], z[3]), s);
           s = dot4(b, make_float4(z[4], z[5], z[6], z[7]), s);
           hf[e] = fmaxf(s, 0.0f);
+          S.HF[ql][p + 4 * e] = hf[e];
         }
-        reinterpret_cast<float4*>(&S.HF[ql][0])[p] = make_float4(hf[0], hf[1], hf[2], hf[3]);
         float r[6];
 #pragma unroll
         for (int j = 0; j < 6; ++j) {
-          const float4 w = reinterpret_cast<const float4*>(&S.fW2[j * 16])[p];
-          r[j] = quad_sum(dot4(w, make_float4(hf[0], hf[1], hf[2], hf[3]), 0.0f)) + S.fb2[j];
+          float t = 0.0f;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) t = fmaf(S.fW2[j * 16 + p + 4 * e], hf[e], t);
+          r[j] = quad_sum(t) + S.fb2[j];
         }
         const Frame F = build_frame(r);
         to_local(F, wi[0], wi[1], wi[2], x + 8);
@@ -472,23 +476,16 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
 #pragma unroll
           for (int k = 0; k < 6; ++k) dr[k] = 0.0f;
         }
-        // frame hidden delta, own units 4p .. 4p+3, and its share of dz
-        const float4 hf = reinterpret_cast<const float4*>(&S.HF[ql][0])[p];
-        const float hfv[4] = {hf.x, hf.y, hf.z, hf.w};
+        // frame hidden delta, own units p + 4e, and its share of dz
         float dhf[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) dhf[e] = 0.0f;
+        for (int e = 0; e < 4; ++e) {
+          float g = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 6; ++j) {
-          const float4 w = reinterpret_cast<const float4*>(&S.fW2[j * 16])[p];
-          dhf[0] = fmaf(w.x, dr[j], dhf[0]);
-          dhf[1] = fmaf(w.y, dr[j], dhf[1]);
-          dhf[2] = fmaf(w.z, dr[j], dhf[2]);
-          dhf[3] = fmaf(w.w, dr[j], dhf[3]);
+          for (int j = 0; j < 6; ++j) g = fmaf(S.fW2[j * 16 + p + 4 * e], dr[j], g);
+          dhf[e] = S.HF[ql][p + 4 * e] > 0.0f ? g : 0.0f;
+          S.DHF[ql][p + 4 * e] = dhf[e];
         }
-#pragma unroll
-        for (int e = 0; e < 4; ++e) dhf[e] = hfv[e] > 0.0f ? dhf[e] : 0.0f;
-        reinterpret_cast<float4*>(&S.DHF[ql][0])[p] = make_float4(dhf[0], dhf[1], dhf[2], dhf[3]);
         if (p == 0) {
           reinterpret_cast<float4*>(&S.DR[ql][0])[0] = make_float4(dr[0], dr[1], dr[2], dr[3]);
           reinterpret_cast<float4*>(&S.DR[ql][0])[1] = make_float4(dr[4], dr[5], 0.0f, 0.0f);
@@ -498,7 +495,7 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
         for (int c = 0; c < 8; ++c) gz[c] = 0.0f;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float4* row = reinterpret_cast<const float4*>(&S.fW1[(4 * p + e) * 8]);
+          const float4* row = reinterpret_cast<const float4*>(&S.fW1[(p + 4 * e) * 8]);
           const float4 a = row[0], b = row[1];
           gz[0] = fmaf(a.x, dhf[e], gz[0]); gz[1] = fmaf(a.y, dhf[e], gz[1]);
           gz[2] = fmaf(a.z, dhf[e], gz[2]); gz[3] = fmaf(a.w, dhf[e], gz[3]);
