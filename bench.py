@@ -623,29 +623,36 @@ def run_scene(ctx, dev, stream, args, width=1920, height=1080):
                       [(-1.6, 1.0, 0.0, 1.0, 1), (0.4, 0.6, -0.6, 0.6, 2), (1.9, 1.2, 1.0, 1.2, 3)],
                       0.0, 0, 2.0, 1.5)
     n = width * height
-    var = torch.from_numpy(rng[12].random((n, 5)).astype(np.float32)).to(dev)
+    bounces = 3
+    var = torch.from_numpy(rng[12].random((bounces, n, 5)).astype(np.float32)).to(dev)
     img = torch.empty((n, 3), device=dev)
     handles = [m.h for m in mats]
-    for _ in range(3):
-        B.nam_scene_render_direct(ctx.h, sc, handles, var, img, stream)
-    torch.cuda.synchronize()
     reps = max(3, args.steps // 2)
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(reps):
-        B.nam_scene_render_direct(ctx.h, sc, handles, var, img, stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / reps
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms = timed(lambda: B.nam_scene_render_direct(ctx.h, sc, handles, var[0], img, stream))
+    ms_paths = timed(lambda: B.nam_scene_render_paths(ctx.h, sc, handles, bounces, var, img, stream))
     for m in mats:
         m.destroy()
     ctx.check()
     return {"workload": f"scene {width}x{height}: ground plane + 3 spheres, 4 FP16 materials with samplers",
             "ms_per_frame": round(ms, 4), "frames_per_s": round(1e3 / ms, 1),
-            "note": "per frame: G-buffer, material binning (one device-to-host read of the four counts), "
+            "paths_bounces": bounces, "paths_ms_per_frame": round(ms_paths, 4),
+            "note": "direct: G-buffer, material binning (one device-to-host read of the four counts), "
                     "nam_sample + nam_sample_pdf + 2 x nam_eval per material range, shading with shadow rays; "
-                    "at most 2 x 2.07 M evaluations and 2.07 M samples"}
+                    "paths: the same at each of up to 3 vertices, continuing along the BSDF sample"}
 
 
 def run_sampling(ctx, dev, stream, flush, w, dq, n, args):

@@ -376,6 +376,18 @@ nam_status nam_scene_gbuffer(nam_ctx* ctx, const nam_scene* scene, int32_t lod_b
 nam_status nam_scene_render_direct(nam_ctx* ctx, const nam_scene* scene, const nam_material* mats, int32_t n_materials,
                                    const float* variates, float* image, void* stream);
 
+/* Paths of up to `bounces` vertices: at every vertex the direct-lighting
+ * estimate above, weighted by the path's throughput, then the path goes on
+ * along the BSDF sample (throughput *= f cos / p_b; a sample below the
+ * surface or of zero density ends it; a ray that leaves the scene ends it,
+ * its sky light already counted by the MIS estimate at its vertex).  Cone
+ * of a secondary vertex: spread times the distance travelled along the
+ * path.  variates: device [bounces][pixels][5], one set per vertex.
+ * bounces = 1 is nam_scene_render_direct. */
+#define NAM_SCENE_MAX_BOUNCES 16
+nam_status nam_scene_render_paths(nam_ctx* ctx, const nam_scene* scene, const nam_material* mats, int32_t n_materials,
+                                  int32_t bounces, const float* variates, float* image, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* differentiation and training (Sec. 5.2)                                  */
 /* ------------------------------------------------------------------------ */

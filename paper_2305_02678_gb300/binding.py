@@ -124,6 +124,7 @@ EXPORTS = ("nam_status_string", "nam_last_error_message", "nam_init", "nam_shutd
            "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_eval_binned", "nam_fp8_calibrate", "nam_sample", "nam_sample_pdf", "nam_backward", "nam_train_step",
            "nam_train_step_noalloc", "nam_encode", "nam_encoder_bake", "nam_backward_encoded",
            "nam_train_step_encoded", "nam_material_encoder", "nam_scene_gbuffer", "nam_scene_render_direct",
+           "nam_scene_render_paths",
            "nam_now",
            "nam_submit", "nam_poll", "nam_wait", "nam_cancel", "nam_get_stats", "nam_inject_fault",
            "nam_debug_mma_selftest", "nam_debug_mma_selftest_ts")
@@ -164,6 +165,7 @@ def _load():
         "nam_material_encoder": (i32, [p, p, p]),
         "nam_scene_gbuffer": (i32, [p, p, i32, p, p]),
         "nam_scene_render_direct": (i32, [p, p, p, i32, p, p, p]),
+        "nam_scene_render_paths": (i32, [p, p, p, i32, i32, p, p, p]),
         "nam_fp8_calibrate": (i32, [p, p, p, i64, p, p]),
         "nam_sample": (i32, [p, p, p, i64, p, p, p, p]),
         "nam_sample_pdf": (i32, [p, p, p, i64, p, p]),
@@ -411,6 +413,16 @@ def nam_scene_render_direct(ctx, scene, mats, variates, image, stream=None):
     arr = (C.c_void_p * len(mats))(*mats)
     _check(_lib.nam_scene_render_direct(ctx, C.byref(scene), arr, len(mats), ptr(variates), ptr(image),
                                         _stream(stream)), "nam_scene_render_direct")
+
+
+NAM_SCENE_MAX_BOUNCES = 16
+
+
+def nam_scene_render_paths(ctx, scene, mats, bounces, variates, image, stream=None):
+    """variates: device [bounces][pixels][5]."""
+    arr = (C.c_void_p * len(mats))(*mats)
+    _check(_lib.nam_scene_render_paths(ctx, C.byref(scene), arr, len(mats), int(bounces), ptr(variates), ptr(image),
+                                       _stream(stream)), "nam_scene_render_paths")
 
 
 def nam_now():

@@ -1,7 +1,8 @@
 // Synthetic-scene harness: an analytic scene (ground plane, spheres) ray-cast
-// to a G-buffer, and direct lighting from a constant sky estimated with one
-// BSDF sample and one cosine-weighted light sample under the power heuristic
-// (Veach 1995), with analytic shadow rays.  The materials' own entry points
+// to a G-buffer, and a small wavefront path tracer lit by a constant sky: at
+// every vertex one BSDF sample and one cosine-weighted light sample under the
+// power heuristic (Veach 1995), with analytic shadow rays, and the path goes
+// on along the BSDF sample.  The materials' own entry points
 // (nam_sample, nam_sample_pdf, nam_eval) run on material-contiguous ranges:
 // the hit pixels are binned by material on the device first, the way a
 // renderer reorders shading work so that threads evaluating one material run
@@ -109,10 +110,46 @@ __device__ void surface(const SceneDev& S, const Hit& h, const float p[3], float
   }
 }
 
+// A path's current vertex; pos, dir and cone are kept for the path tracer
+// (null in the public G-buffer call)
 struct GBuf {
   int32_t* material;
   float *t, *u, *v, *lod, *frame, *view;
+  float *pos, *dir, *cone;
 };
+
+// surface data of hit h on ray (o, d) whose cone has width `cone` at the hit
+__device__ void write_vertex(const SceneDev& S, GBuf& g, int64_t i, const Hit& h, const float o[3], const float d[3],
+                             float cone) {
+  g.material[i] = h.mat;
+  if (h.mat < 0) {
+    g.t[i] = INFINITY;
+    g.u[i] = g.v[i] = g.lod[i] = 0.0f;
+    for (int k = 0; k < 9; ++k) g.frame[9 * i + k] = 0.0f;
+    for (int k = 0; k < 3; ++k) g.view[3 * i + k] = 0.0f;
+    return;
+  }
+  const float p[3] = {o[0] + h.t * d[0], o[1] + h.t * d[1], o[2] + h.t * d[2]};
+  float T[9], u, v, uv_scale;
+  surface(S, h, p, T, u, v, uv_scale);
+  const float cosv = fabsf(dot3(T + 6, d));
+  const float footprint = cone / fmaxf(cosv, 0.05f) * uv_scale * S.lod_w0;
+  g.t[i] = h.t;
+  g.u[i] = u;
+  g.v[i] = v;
+  g.lod[i] = log2f(fmaxf(footprint, 1e-6f));
+  for (int k = 0; k < 9; ++k) g.frame[9 * i + k] = T[k];
+  // direction back along the ray in the shading frame
+  const float w[3] = {-d[0], -d[1], -d[2]};
+  for (int k = 0; k < 3; ++k) g.view[3 * i + k] = dot3(T + 3 * k, w);
+  if (g.pos) {
+    for (int k = 0; k < 3; ++k) {
+      g.pos[3 * i + k] = p[k];
+      g.dir[3 * i + k] = d[k];
+    }
+    g.cone[i] = cone;
+  }
+}
 
 __global__ void __launch_bounds__(kThreads) gbuffer_kernel(const SceneDev S, GBuf g) {
   const int64_t n = (int64_t)S.W * S.H;
@@ -121,27 +158,24 @@ __global__ void __launch_bounds__(kThreads) gbuffer_kernel(const SceneDev S, GBu
     float d[3];
     primary_dir(S, px, py, d);
     const Hit h = intersect(S, S.eye, d, kEps);
-    g.material[i] = h.mat;
-    if (h.mat < 0) {
-      g.t[i] = INFINITY;
-      g.u[i] = g.v[i] = g.lod[i] = 0.0f;
-      for (int k = 0; k < 9; ++k) g.frame[9 * i + k] = 0.0f;
-      for (int k = 0; k < 3; ++k) g.view[3 * i + k] = 0.0f;
+    write_vertex(S, g, i, h, S.eye, d, S.spread * h.t);
+  }
+}
+
+// the next vertex of every live path (ray ro, rd; live = rd[3i] is finite);
+// the cone keeps widening with the distance travelled
+__global__ void __launch_bounds__(kThreads) trace_kernel(const SceneDev S, int64_t n, const float* __restrict__ ro,
+                                                         const float* __restrict__ rd, GBuf g) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float d[3] = {rd[3 * i], rd[3 * i + 1], rd[3 * i + 2]};
+    if (!isfinite(d[0])) {
+      g.material[i] = -1;
       continue;
     }
-    const float p[3] = {S.eye[0] + h.t * d[0], S.eye[1] + h.t * d[1], S.eye[2] + h.t * d[2]};
-    float T[9], u, v, uv_scale;
-    surface(S, h, p, T, u, v, uv_scale);
-    const float cosv = fabsf(dot3(T + 6, d));
-    const float footprint = S.spread * h.t / fmaxf(cosv, 0.05f) * uv_scale * S.lod_w0;
-    g.t[i] = h.t;
-    g.u[i] = u;
-    g.v[i] = v;
-    g.lod[i] = log2f(fmaxf(footprint, 1e-6f));
-    for (int k = 0; k < 9; ++k) g.frame[9 * i + k] = T[k];
-    // direction to the eye in the shading frame
-    const float w[3] = {-d[0], -d[1], -d[2]};
-    for (int k = 0; k < 3; ++k) g.view[3 * i + k] = dot3(T + 3 * k, w);
+    const float o[3] = {ro[3 * i], ro[3 * i + 1], ro[3 * i + 2]};
+    const Hit h = intersect(S, o, d, kEps);
+    const float cone = g.cone[i] + S.spread * (h.mat >= 0 ? h.t : 0.0f);
+    write_vertex(S, g, i, h, o, d, cone);
   }
 }
 
@@ -215,44 +249,67 @@ __global__ void __launch_bounds__(kThreads) build_eval_kernel(int64_t nh, Slots 
   }
 }
 
+struct PathState {
+  float* thr;  // [n][3] throughput
+  float* rad;  // [n][3] radiance gathered so far
+  float* ro;   // [n][3] next ray origin
+  float* rd;   // [n][3] next ray direction (NaN: the path ends)
+};
+
 __global__ void __launch_bounds__(kThreads) shade_kernel(const SceneDev S, const int32_t* __restrict__ perm, int64_t nh,
                                                          GBuf g, Slots s, const float* __restrict__ d_b,
                                                          const float* __restrict__ pdf_b, const float* __restrict__ pdf_bl,
-                                                         const float* __restrict__ rgb, float* __restrict__ image) {
+                                                         const float* __restrict__ rgb, PathState ps, bool more) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nh; p += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = perm[p];
-    const int px = (int)(i % S.W), py = (int)(i / S.W);
-    float d[3];
-    primary_dir(S, px, py, d);
-    const float t = g.t[i];
     const float* T = g.frame + 9 * i;
-    // shadow rays leave from just above the surface
+    const float t = g.t[i];
+    // secondary rays leave from just above the surface
     const float off = 1e-3f * fmaxf(1.0f, t);
-    const float o[3] = {S.eye[0] + t * d[0] + off * T[6], S.eye[1] + t * d[1] + off * T[7],
-                        S.eye[2] + t * d[2] + off * T[8]};
+    const float o[3] = {g.pos[3 * i] + off * T[6], g.pos[3 * i + 1] + off * T[7], g.pos[3 * i + 2] + off * T[8]};
     float c[3] = {0.0f, 0.0f, 0.0f};
     for (int k = 0; k < 2; ++k) {
       const float l[3] = {k ? s.lx[p] : d_b[3 * p], k ? s.ly[p] : d_b[3 * p + 1], k ? s.lz[p] : d_b[3 * p + 2]};
       if (!(l[2] > 0.0f)) continue;
       const float pl = l[2] * (1.0f / kPi);
       const float pb = k ? pdf_bl[p] : pdf_b[p];
-      const float ps = k ? pl : pb;
-      if (!(ps > 0.0f)) continue;
-      const float w = ps * ps / (pb * pb + pl * pl);
+      const float pd = k ? pl : pb;
+      if (!(pd > 0.0f)) continue;
+      const float w = pd * pd / (pb * pb + pl * pl);
       const float dw[3] = {T[0] * l[0] + T[3] * l[1] + T[6] * l[2], T[1] * l[0] + T[4] * l[1] + T[7] * l[2],
                            T[2] * l[0] + T[5] * l[1] + T[8] * l[2]};
       if (intersect(S, o, dw, kEps).mat >= 0) continue;  // the sky is blocked
-      const float a = S.sky * w / ps;
+      const float a = S.sky * w / pd;
       for (int ch = 0; ch < 3; ++ch) c[ch] += a * rgb[3 * (2 * p + k) + ch];
     }
-    for (int ch = 0; ch < 3; ++ch) image[3 * i + ch] = c[ch];
+    for (int ch = 0; ch < 3; ++ch) ps.rad[3 * i + ch] += ps.thr[3 * i + ch] * c[ch];
+    if (!more) continue;
+    // the path goes on along the BSDF sample
+    const float l[3] = {d_b[3 * p], d_b[3 * p + 1], d_b[3 * p + 2]};
+    const float pb = pdf_b[p];
+    if (l[2] > 0.0f && pb > 0.0f) {
+      for (int ch = 0; ch < 3; ++ch) ps.thr[3 * i + ch] *= rgb[3 * (2 * p) + ch] / pb;
+      for (int k = 0; k < 3; ++k) {
+        ps.ro[3 * i + k] = o[k];
+        ps.rd[3 * i + k] = T[k] * l[0] + T[3 + k] * l[1] + T[6 + k] * l[2];
+      }
+    }
   }
 }
 
-__global__ void __launch_bounds__(kThreads) sky_kernel(const int32_t* __restrict__ mat, int64_t n, float sky,
-                                                       float* __restrict__ image) {
+// throughput 1, radiance 0 (the sky where the primary ray leaves the scene)
+__global__ void __launch_bounds__(kThreads) init_paths_kernel(const int32_t* __restrict__ mat, int64_t n, float sky,
+                                                              PathState ps) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    if (mat[i] < 0) image[3 * i] = image[3 * i + 1] = image[3 * i + 2] = sky;
+    for (int ch = 0; ch < 3; ++ch) {
+      ps.thr[3 * i + ch] = 1.0f;
+      ps.rad[3 * i + ch] = mat[i] < 0 ? sky : 0.0f;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) end_paths_kernel(int64_t n, float* __restrict__ rd) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    rd[3 * i] = NAN;
 }
 
 int grid_of(int64_t n, int sms) {
@@ -332,7 +389,7 @@ extern "C" nam_status nam_scene_gbuffer(nam_ctx* ctx, const nam_scene* scene, in
   if (!out->material || !out->t || !out->u || !out->v || !out->lod || !out->frame || !out->view)
     return fail(NAM_ERR_INVALID_ARG, "nam_scene_gbuffer: NULL output array");
   DeviceGuard g(ctx->device);
-  GBuf gb{out->material, out->t, out->u, out->v, out->lod, out->frame, out->view};
+  GBuf gb{out->material, out->t, out->u, out->v, out->lod, out->frame, out->view, nullptr, nullptr, nullptr};
   const int64_t n = (int64_t)S.W * S.H;
   gbuffer_kernel<<<grid_of(n, ctx->num_sms), kThreads, 0, (cudaStream_t)stream>>>(S, gb);
   const int e = (int)cudaGetLastError();
@@ -340,9 +397,11 @@ extern "C" nam_status nam_scene_gbuffer(nam_ctx* ctx, const nam_scene* scene, in
   return NAM_OK;
 }
 
-extern "C" nam_status nam_scene_render_direct(nam_ctx* ctx, const nam_scene* scene, const nam_material* mats,
-                                              int32_t nmat, const float* variates, float* image, void* stream) {
-  if (!ctx || !variates || !image) return fail(NAM_ERR_INVALID_ARG, "nam_scene_render_direct: NULL argument");
+static nam_status render_paths(nam_ctx* ctx, const nam_scene* scene, const nam_material* mats, int32_t nmat,
+                               int32_t bounces, const float* variates, float* image, void* stream, const char* who) {
+  if (!ctx || !variates || !image) return fail(NAM_ERR_INVALID_ARG, "%s: NULL argument", who);
+  if (bounces < 1 || bounces > NAM_SCENE_MAX_BOUNCES)
+    return fail(NAM_ERR_INVALID_ARG, "%s: bounces %d not in [1, %d]", who, bounces, NAM_SCENE_MAX_BOUNCES);
   nam_status st = check_multi(ctx, mats, nmat);
   if (st) return st;
   SceneDev S;
@@ -358,15 +417,16 @@ extern "C" nam_status nam_scene_render_direct(nam_ctx* ctx, const nam_scene* sce
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = (int64_t)S.W * S.H;
   const int grid = grid_of(n, ctx->num_sms);
-  // scratch, in units of one 4-byte value per pixel: G-buffer 17, slot
+  // scratch, in units of one 4-byte value per pixel: the path vertex 24, slot
   // permutation 1, per-slot queries and variates 13, BSDF sample and the two
-  // densities 5, shading queries (2 per slot) 20 and their RGB 6
+  // densities 5, shading queries (2 per slot) 20 and their RGB 6, throughput
+  // and next ray 9 (the radiance accumulates in the image)
   const size_t F = ((size_t)n * 4 + 255) / 256 * 256;
   const size_t counts_b = ((size_t)nmat * 4 + 255) / 256 * 256;
-  const size_t total = F * 62 + 2 * counts_b;
+  const size_t total = F * 78 + 2 * counts_b;
   uint8_t* base = nullptr;
   cudaError_t ce = cudaMallocFromPoolAsync((void**)&base, total, ctx->pool, s);
-  if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_scene_render_direct: scratch");
+  if (ce != cudaSuccess) return cuda_fail((int)ce, "scene harness: scratch");
   uint8_t* p = base;
   auto take = [&](size_t k) {
     uint8_t* r = p;
@@ -377,6 +437,7 @@ extern "C" nam_status nam_scene_render_direct(nam_ctx* ctx, const nam_scene* sce
   gb.material = (int32_t*)take(1);
   gb.t = take(1); gb.u = take(1); gb.v = take(1); gb.lod = take(1);
   gb.frame = take(9); gb.view = take(3);
+  gb.pos = take(3); gb.dir = take(3); gb.cone = take(1);
   int32_t* perm = (int32_t*)take(1);
   Slots sl;
   sl.u = take(1); sl.v = take(1); sl.lod = take(1); sl.xi = take(1);
@@ -389,29 +450,40 @@ extern "C" nam_status nam_scene_render_direct(nam_ctx* ctx, const nam_scene* sce
   eq.u = take(2); eq.v = take(2); eq.lod = take(2); eq.xi = take(2);
   eq.wix = take(2); eq.wiy = take(2); eq.wiz = take(2); eq.wox = take(2); eq.woy = take(2); eq.woz = take(2);
   float* rgb = take(6);
+  PathState ps;
+  ps.thr = take(3);
+  ps.ro = take(3);
+  ps.rd = take(3);
+  ps.rad = image;
   uint32_t* counts = (uint32_t*)p;
   uint32_t* cursor = (uint32_t*)(p + counts_b);
 
   int e = 0;
   gbuffer_kernel<<<grid, kThreads, 0, s>>>(S, gb);
-  sky_kernel<<<grid, kThreads, 0, s>>>(gb.material, n, S.sky, image);
-  cudaMemsetAsync(counts, 0, (size_t)nmat * 4, s);
-  count_kernel<<<grid, kThreads, 0, s>>>(gb.material, n, counts);
+  init_paths_kernel<<<grid, kThreads, 0, s>>>(gb.material, n, S.sky, ps);
   std::vector<uint32_t> hc((size_t)nmat), off((size_t)nmat + 1, 0);
-  ce = cudaMemcpyAsync(hc.data(), counts, (size_t)nmat * 4, cudaMemcpyDeviceToHost, s);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-  if (ce != cudaSuccess) {
-    cudaFreeAsync(base, s);
-    return cuda_fail((int)ce, "nam_scene_render_direct: material counts");
-  }
-  for (int k = 0; k < nmat; ++k) off[k + 1] = off[k] + hc[k];
-  const int64_t nh = off[nmat];
-  ce = cudaMemcpyAsync(cursor, off.data(), (size_t)nmat * 4, cudaMemcpyHostToDevice, s);
-  if (ce != cudaSuccess) e = (int)ce;
-  if (!e && nh > 0) {
+  for (int32_t b = 0; b < bounces && !e && !st; ++b) {
+    const bool more = b + 1 < bounces;
+    if (more) end_paths_kernel<<<grid, kThreads, 0, s>>>(n, ps.rd);
+    cudaMemsetAsync(counts, 0, (size_t)nmat * 4, s);
+    count_kernel<<<grid, kThreads, 0, s>>>(gb.material, n, counts);
+    ce = cudaMemcpyAsync(hc.data(), counts, (size_t)nmat * 4, cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) {
+      e = (int)ce;
+      break;
+    }
+    for (int k = 0; k < nmat; ++k) off[k + 1] = off[k] + hc[k];
+    const int64_t nh = off[nmat];
+    if (nh == 0) break;  // every path has left the scene
+    ce = cudaMemcpyAsync(cursor, off.data(), (size_t)nmat * 4, cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) {
+      e = (int)ce;
+      break;
+    }
     const int gh = grid_of(nh, ctx->num_sms);
     scatter_kernel<<<grid, kThreads, 0, s>>>(gb.material, n, cursor, perm);
-    prep_kernel<<<gh, kThreads, 0, s>>>(perm, nh, gb, variates, sl);
+    prep_kernel<<<gh, kThreads, 0, s>>>(perm, nh, gb, variates + (size_t)b * n * 5, sl);
     e = (int)cudaGetLastError();
     // per material: one BSDF sample, and the sampler's density of the light sample
     for (int k = 0; k < nmat && !e; ++k) {
@@ -435,12 +507,27 @@ extern "C" nam_status nam_scene_render_direct(nam_ctx* ctx, const nam_scene* sce
       st = nam_eval(ctx, mats[k], &qe, c, rgb + 3 * o, s, NAM_OUT_COSINE);
     }
     if (!st && !e) {
-      shade_kernel<<<gh, kThreads, 0, s>>>(S, perm, nh, gb, sl, d_b, pdf_b, pdf_bl, rgb, image);
+      shade_kernel<<<gh, kThreads, 0, s>>>(S, perm, nh, gb, sl, d_b, pdf_b, pdf_bl, rgb, ps, more);
+      e = (int)cudaGetLastError();
+    }
+    if (more && !st && !e) {
+      trace_kernel<<<grid, kThreads, 0, s>>>(S, n, ps.ro, ps.rd, gb);
       e = (int)cudaGetLastError();
     }
   }
   cudaFreeAsync(base, s);
   if (st) return st;
-  if (e) return cuda_fail(e, "nam_scene_render_direct: launch");
+  if (e) return cuda_fail(e, who);
   return NAM_OK;
+}
+
+extern "C" nam_status nam_scene_render_direct(nam_ctx* ctx, const nam_scene* scene, const nam_material* mats,
+                                              int32_t nmat, const float* variates, float* image, void* stream) {
+  return render_paths(ctx, scene, mats, nmat, 1, variates, image, stream, "nam_scene_render_direct");
+}
+
+extern "C" nam_status nam_scene_render_paths(nam_ctx* ctx, const nam_scene* scene, const nam_material* mats,
+                                             int32_t nmat, int32_t bounces, const float* variates, float* image,
+                                             void* stream) {
+  return render_paths(ctx, scene, mats, nmat, bounces, variates, image, stream, "nam_scene_render_paths");
 }

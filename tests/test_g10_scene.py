@@ -100,3 +100,50 @@ def test_direct_lighting_matches_oracle(gctx, oracle):
     for m in mats:
         m.destroy()
     gctx.check()
+
+
+def test_paths_match_oracle(gctx, oracle):
+    """Three-vertex paths: the GPU harness against the FP64 version with the
+    same variates.  Sampled directions differ by FP32 rounding, so a few
+    paths take another turn at a silhouette; the bulk agrees closely."""
+    import torch
+
+    import oracle.scene as S
+    from paper_2305_02678_gb300 import binding as B
+    rng = W.rng_streams(95, 10)
+    W0, L = 256, 9
+    sc = dict(SCENE, width=96, height=72)
+    mats, models, samplers = [], [], []
+    for k in range(4):
+        pyr = W.make_pyramid(rng[k], W0, W0, L, dtype=np.float16)
+        model = W.make_model(rng[4 + k], (14, 64, 64, 3), (8, 16, 6))
+        smp = W.make_mlp(W.rng_streams(96 + k, 1)[0], (11, 32, 32, 32, 9))
+        mats.append(gctx.material(W0, W0, L, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_F16,
+                                  sampler=smp))
+        models.append(oracle.Model(W0, W0, L, pyr, model["frame"], model["decoder"], params="fp16",
+                                   act_round=oracle.ROUND_FP16, out_cosine=True))
+        samplers.append(smp)
+    n = sc["width"] * sc["height"]
+    bounces = 3
+    var = rng[9].random((bounces, n, 5)).astype(np.float32)
+    img = torch.empty((n, 3), device="cuda")
+    B.nam_scene_render_paths(gctx.h, _c_scene(B, sc), [m.h for m in mats], bounces, torch.from_numpy(var).cuda(),
+                             img, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    got = img.cpu().numpy().astype(np.float64)
+    ref = S.render_paths(sc, models, samplers, var.astype(np.float64), W0, bounces)
+    direct = S.render_direct(sc, models, samplers, var[0].astype(np.float64), W0)
+    scale = np.abs(ref).mean()
+    rel = np.abs(got - ref).max(axis=1) / (np.abs(ref).max(axis=1) + 1e-3 * scale)
+    print(f"paths: median rel {np.median(rel):.2e}, 95th pct {np.percentile(rel, 95):.2e}, max {rel.max():.2e}; "
+          f"mean |diff| / mean |ref| {np.abs(got - ref).mean() / scale:.2e}; "
+          f"indirect share {np.abs(ref - direct).mean() / scale:.2f}")
+    assert np.median(rel) <= 1e-4
+    assert np.percentile(rel, 95) <= 2e-2
+    assert np.abs(got - ref).mean() / scale <= 1e-2
+    # later vertices contribute (random decoders can return negative values,
+    # so the indirect term is not a sum of positive parts)
+    assert np.abs(ref - direct).mean() > 0.01 * scale
+    for m in mats:
+        m.destroy()
+    gctx.check()
