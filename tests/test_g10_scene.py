@@ -147,3 +147,35 @@ def test_paths_match_oracle(gctx, oracle):
     for m in mats:
         m.destroy()
     gctx.check()
+
+
+def test_paths_one_vertex_is_direct_and_arguments(gctx):
+    import torch
+    from paper_2305_02678_gb300 import binding as B
+    rng = W.rng_streams(97, 9)
+    mats = []
+    for k in range(4):
+        pyr = W.make_pyramid(rng[k], 64, 64, 7, dtype=np.float16)
+        model = W.make_model(rng[4 + k], (14, 64, 64, 3), (8, 16, 6))
+        mats.append(gctx.material(64, 64, 7, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_F16,
+                                  sampler=W.make_mlp(W.rng_streams(98 + k, 1)[0], (11, 32, 32, 32, 9))))
+    sc = dict(SCENE, width=64, height=48)
+    n = 64 * 48
+    var = torch.from_numpy(rng[8].random((1, n, 5)).astype(np.float32)).cuda()
+    a = torch.empty((n, 3), device="cuda")
+    b = torch.empty((n, 3), device="cuda")
+    h = [m.h for m in mats]
+    B.nam_scene_render_direct(gctx.h, _c_scene(B, sc), h, var[0], a)
+    B.nam_scene_render_paths(gctx.h, _c_scene(B, sc), h, 1, var, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    for bad in (0, B.NAM_SCENE_MAX_BOUNCES + 1):
+        with pytest.raises(B.NamError) as e:
+            B.nam_scene_render_paths(gctx.h, _c_scene(B, sc), h, bad, var, b)
+        assert e.value.status == B.NAM_ERR_INVALID_ARG
+    with pytest.raises(B.NamError) as e:   # the scene names material 3; give three
+        B.nam_scene_render_direct(gctx.h, _c_scene(B, sc), h[:3], var[0], a)
+    assert e.value.status == B.NAM_ERR_INVALID_ARG
+    for m in mats:
+        m.destroy()
+    gctx.check()

@@ -43,6 +43,22 @@ def test_encode_matches_oracle(gctx, oracle, n):
     import torch
     from paper_2305_02678_gb300 import binding as B
     W0, L, pyr, model, enc, target, q, attrs = _setup(31, n=max(n, 1))
+    _encode_case(gctx, oracle, W0, L, pyr, model, enc, attrs, n)
+
+
+@pytest.mark.parametrize("k_inputs", [1, 16])
+def test_encode_input_widths(gctx, oracle, k_inputs):
+    """The smallest and largest encoder input counts, on random parameters."""
+    W0, L, pyr, model, _, _, _, _ = _setup(33)
+    rng = np.random.default_rng(34 + k_inputs)
+    enc = W.make_mlp(W.rng_streams(35 + k_inputs, 1)[0], (k_inputs, 32, 32, 8))
+    attrs = rng.random((3001, k_inputs)).astype(np.float32)
+    _encode_case(gctx, oracle, W0, L, pyr, model, enc, attrs, 3001)
+
+
+def _encode_case(gctx, oracle, W0, L, pyr, model, enc, attrs, n):
+    import torch
+    from paper_2305_02678_gb300 import binding as B
     mat = gctx.material(W0, W0, L, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_F32,
                         trainable=True, encoder=enc)
     z = torch.empty((n, 8), device="cuda")

@@ -108,3 +108,17 @@ def test_binned_out_of_range_ids(gctx):
     for m in mats:
         m.destroy()
     gctx.check()
+
+
+def test_binned_many_materials(gctx):
+    """257 materials (the plan kernel's search over material ranges, shared
+    histograms of hundreds of entries), 20,000 queries, ids skewed so that
+    some materials get one query and some none."""
+    mats, rng = _materials(gctx, 75, 257, W0=16, L=4)
+    n = 20000
+    q = W.uniform_queries(rng, n, 3.0)
+    ids = np.minimum(rng.geometric(0.02, n) - 1, 256).astype(np.int32)
+    _check_against_single(gctx, mats, to_device(q), ids, n)
+    for m in mats:
+        m.destroy()
+    gctx.check()
