@@ -41,10 +41,18 @@ struct Slot {
   cudaEvent_t done = nullptr;
   Job* job = nullptr;
   // pinned staging for the frame's work table: an upload from pageable
-  // memory could make the scheduler thread wait for the slot's stream
+  // memory could make the scheduler thread wait for the slot's stream.
+  // Allocated with the slot (kTableBytes); a frame that outgrows it gets a
+  // larger one and the old one is kept until serving stops, because freeing
+  // pinned memory synchronises the device and would stall every frame in
+  // flight.
   void* host_tab = nullptr;
   size_t host_tab_bytes = 0;
+  std::vector<void*> retired_tabs;
 };
+
+// 4 MiB: the work table of a frame of 2^25 queries (262,144 chunks)
+constexpr size_t kTableBytes = 4u << 20;
 
 struct ServeState {
   std::mutex mu;
@@ -59,6 +67,13 @@ struct ServeState {
   nam_ticket next_ticket = 1;
   int64_t in_flight = 0, completed = 0, failed = 0, queries_completed = 0;
   uint64_t serving_bytes = 0;
+  // the context pool is grown on the submitting thread (slots x the largest
+  // frame so far), so that the scheduler's per-frame allocations come from
+  // memory the pool already holds: growing it maps new memory and would hold
+  // the scheduler thread, and with it every frame in flight
+  std::mutex prime_mu;
+  cudaStream_t prime_stream = nullptr;
+  uint64_t primed_bytes = 0;
   std::deque<double> latencies_ms;
   double first_arrival = -1.0, last_finish = 0.0;
 };
@@ -117,12 +132,12 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
   const size_t pb = j->mats.size() * sizeof(void*);
   const size_t tb = cb + 2 * pb;
   if (tb > slot.host_tab_bytes) {
-    if (slot.host_tab) cudaFreeHost(slot.host_tab);
-    slot.host_tab = nullptr;
-    slot.host_tab_bytes = 0;
-    const size_t want = std::max<size_t>(tb * 2, 1 << 20);
-    e = cudaMallocHost(&slot.host_tab, want);
+    void* bigger = nullptr;
+    const size_t want = std::max<size_t>(tb * 2, kTableBytes);
+    e = cudaMallocHost(&bigger, want);
     if (e != cudaSuccess) return cuda_fail((int)e, "serving: pinned table buffer");
+    if (slot.host_tab) slot.retired_tabs.push_back(slot.host_tab);
+    slot.host_tab = bigger;
     slot.host_tab_bytes = want;
   }
   uint8_t* host = (uint8_t*)slot.host_tab;
@@ -223,14 +238,27 @@ static nam_status ensure_serving(nam_ctx* ctx) {
   for (Slot& sl : S->slots) {
     cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&sl.host_tab, kTableBytes);
+    if (e == cudaSuccess) sl.host_tab_bytes = kTableBytes;
     if (e != cudaSuccess) {
       for (Slot& x : S->slots) {
         if (x.stream) cudaStreamDestroy(x.stream);
         if (x.done) cudaEventDestroy(x.done);
+        if (x.host_tab) cudaFreeHost(x.host_tab);
       }
       delete S;
       return cuda_fail((int)e, "serving: stream creation");
     }
+  }
+  cudaError_t pe = cudaStreamCreateWithFlags(&S->prime_stream, cudaStreamNonBlocking);
+  if (pe != cudaSuccess) {
+    for (Slot& x : S->slots) {
+      cudaStreamDestroy(x.stream);
+      cudaEventDestroy(x.done);
+      cudaFreeHost(x.host_tab);
+    }
+    delete S;
+    return cuda_fail((int)pe, "serving: stream creation");
   }
   ctx->serve = S;
   S->thread = std::thread(scheduler, ctx);
@@ -262,7 +290,9 @@ void nam::serve_stop(nam_ctx* ctx) {
     cudaStreamDestroy(sl.stream);
     cudaEventDestroy(sl.done);
     if (sl.host_tab) cudaFreeHost(sl.host_tab);
+    for (void* t : sl.retired_tabs) cudaFreeHost(t);
   }
+  cudaStreamDestroy(S->prime_stream);
   for (auto& kv : S->jobs) delete kv.second;
   delete S;
   ctx->serve = nullptr;
@@ -301,6 +331,23 @@ extern "C" nam_status nam_submit(nam_ctx* ctx, const nam_frame* f, nam_ticket* o
     return st;
   }
   ServeState* S = ctx->serve;
+  {
+    std::lock_guard<std::mutex> pk(S->prime_mu);
+    uint64_t want = (uint64_t)ctx->serve_streams * j->bytes;
+    if (ctx->budget) {
+      const uint64_t res = ctx->resident.load();
+      want = std::min<uint64_t>(want, ctx->budget > res ? ctx->budget - res : 0);
+    }
+    if (want > S->primed_bytes) {
+      DeviceGuard g(ctx->device);
+      void* p = nullptr;
+      if (cudaMallocFromPoolAsync(&p, want, ctx->pool, S->prime_stream) == cudaSuccess) {
+        cudaFreeAsync(p, S->prime_stream);
+        if (cudaStreamSynchronize(S->prime_stream) == cudaSuccess) S->primed_bytes = want;
+      }
+      cudaGetLastError();  // a failed reservation only means the scheduler grows the pool itself
+    }
+  }
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (ctx->budget) {
