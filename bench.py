@@ -589,6 +589,32 @@ def run_binned(ctx, dev, stream, flush, w, dq, n, args, n_mat=16):
                                        max(3, args.steps // 2), 2, flush, stream))
     t1 = statistics.fmean(time_launches(lambda: B.nam_eval(ctx.h, mats[0].h, dq, n, o, stream, 0),
                                         max(3, args.steps // 2), 2, flush, stream))
+    reps = max(3, args.steps // 2)
+    # per-tile selection on the same per-pixel ids: every tile holds more
+    # than 8 of the 16 materials, so every query takes the divergent path
+    t_sel_pp = statistics.fmean(time_launches(lambda: B.nam_eval_select(ctx.h, handles, dq, ids, n, o, stream, 0),
+                                              3, 1, flush, stream))
+    # screen regions: the pixels of the 1920x1080 frame (queries in row-major
+    # pixel order) take the material of the nearest of 16 random sites, so a
+    # 128-pixel run is mixed only where a region boundary crosses it
+    width = 1920
+    sites = W.rng_streams(W.SEEDS[2] + 32, 1)[0].random((n_mat, 2)) * np.array([width, n // width])
+    px = (np.arange(n) % width).astype(np.float32)
+    py = (np.arange(n) // width).astype(np.float32)
+    best = np.full(n, np.inf, np.float32)
+    reg = np.zeros(n, np.int32)
+    for k, (sx, sy) in enumerate(sites):
+        d = (px - sx) ** 2 + (py - sy) ** 2
+        upd = d < best
+        best[upd], reg[upd] = d[upd], k
+    tiles = np.pad(reg, (0, (-n) % 128), mode="edge").reshape(-1, 128)
+    coherent = float(np.mean(np.all(tiles == tiles[:, :1], axis=1)))
+    passes = float(np.mean([np.unique(t).size for t in tiles]))
+    rids = torch.from_numpy(reg).to(dev)
+    t_sel = statistics.fmean(time_launches(lambda: B.nam_eval_select(ctx.h, handles, dq, rids, n, o, stream, 0),
+                                           reps, 2, flush, stream))
+    t_bin_reg = statistics.fmean(time_launches(lambda: B.nam_eval_binned(ctx.h, handles, dq, rids, n, o, stream, 0),
+                                               reps, 2, flush, stream))
     for m in mats:
         m.destroy()
     ctx.check()
@@ -597,7 +623,17 @@ def run_binned(ctx, dev, stream, flush, w, dq, n, args, n_mat=16):
             "single_material_ms": round(t1, 4), "overhead_vs_single": round(t / t1, 3),
             "note": "binning passes (count, plan, scatter of 40 B of query fields per query, unbin of the RGB) "
                     "plus the chunked tensor-core launch, whose CTAs restage weights when a chunk's material "
-                    "changes"}
+                    "changes",
+            "select": {
+                "per_pixel_ms": round(t_sel_pp, 4),
+                "regions_workload": f"{n_mat} screen regions (nearest of {n_mat} random sites), "
+                                    f"{coherent:.3f} of the 128-query tiles coherent, "
+                                    f"{passes:.3f} tensor-core passes per tile",
+                "regions_select_ms": round(t_sel, 4), "regions_binned_ms": round(t_bin_reg, 4),
+                "note": "nam_eval_select, in place: a 128-query tile with k <= 8 materials runs as k masked "
+                        "tensor-core passes (one per material), a tile with more on the divergent path (one query "
+                        "per thread, FP32, each thread's own material weights); three small passes build the "
+                        "pass table"}}
 
 
 def run_scene(ctx, dev, stream, args, width=1920, height=1080):

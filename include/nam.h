@@ -308,6 +308,35 @@ nam_status nam_eval_multi(nam_ctx* ctx, const nam_material* materials, int32_t n
 nam_status nam_eval_binned(nam_ctx* ctx, const nam_material* mats, int32_t n_materials, const nam_queries* q,
                            const int32_t* material_ids, int64_t n, float* rgb_out, void* stream, uint32_t flags);
 
+/* Evaluation of queries whose material varies per query, in place, choosing
+ * a code path per tile (Sec. 7.1: the shader picks per warp between a path
+ * for coherent and one for divergent execution; a tcgen05 MMA spans a CTA's
+ * 128-row tile, so here the unit is a tile of 128 consecutive queries in the
+ * caller's order).  A pass over material_ids lists each tile's distinct
+ * materials:
+ *   1 to NAM_SELECT_MAX_PASSES  one tensor-core pass over the tile per
+ *       material, each storing only the rows of its own material (the way
+ *       SIMT divergence runs a warp once per branch target, at tensor-core
+ *       speed); every such query's result is bitwise that of nam_eval on its
+ *       material;
+ *   more  the divergent path: one query per thread, each thread reading its
+ *       own material's weights from an FP32 image of the values the
+ *       material's tensor-core blob holds (binary16-rounded weights and
+ *       biases; FP8: E4M3 codes times their layer scale, FP32 decoder
+ *       biases) and computing in FP32, so those results differ from
+ *       nam_eval's by the tensor-core path's activation rounding only.
+ * No query is moved: suited to ids that are coherent over runs of 128
+ * queries (screen tiles of a few surfaces); nam_eval_binned suits incoherent
+ * ids.  Arguments, id checks (an id outside [0, n_materials) leaves that
+ * query's rgb_out untouched and makes nam_check_device_error report
+ * NAM_ERR_DEVICE_ASSERT) and material requirements as nam_eval_binned.
+ * Temporary device memory (≈ 40 bytes per tile plus at most 16 bytes per
+ * query, and 24 bytes per material) comes from the context's stream-ordered
+ * pool. */
+#define NAM_SELECT_MAX_PASSES 8
+nam_status nam_eval_select(nam_ctx* ctx, const nam_material* mats, int32_t n_materials, const nam_queries* q,
+                           const int32_t* material_ids, int64_t n, float* rgb_out, void* stream, uint32_t flags);
+
 /* ------------------------------------------------------------------------ */
 /* synthetic-scene harness                                                  */
 /* ------------------------------------------------------------------------ */

@@ -121,7 +121,7 @@ class nam_stats(C.Structure):
 #: every symbol include/nam.h declares
 EXPORTS = ("nam_status_string", "nam_last_error_message", "nam_init", "nam_shutdown", "nam_check_device_error",
            "nam_create_material", "nam_destroy_material", "nam_material_get_info", "nam_material_params",
-           "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_eval_binned", "nam_fp8_calibrate", "nam_sample", "nam_sample_pdf", "nam_backward", "nam_train_step",
+           "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_eval_binned", "nam_eval_select", "nam_fp8_calibrate", "nam_sample", "nam_sample_pdf", "nam_backward", "nam_train_step",
            "nam_train_step_noalloc", "nam_encode", "nam_encoder_bake", "nam_backward_encoded",
            "nam_train_step_encoded", "nam_material_encoder", "nam_scene_gbuffer", "nam_scene_render_direct",
            "nam_scene_render_paths",
@@ -155,6 +155,7 @@ def _load():
         "nam_eval_host": (i32, [p, p, p, i64, p, p, u32]),
         "nam_eval_multi": (i32, [p, p, i32, p, p, i32, p, p, u32]),
         "nam_eval_binned": (i32, [p, p, i32, p, p, i64, p, p, u32]),
+        "nam_eval_select": (i32, [p, p, i32, p, p, i64, p, p, u32]),
         "nam_backward": (i32, [p, p, p, i64, p, p, p, p, u32]),
         "nam_train_step": (i32, [p, p, p, p, i64, p, p, p, u32]),
         "nam_train_step_noalloc": (i32, [p, p, p, p, i64, p, p, p, u32]),
@@ -321,6 +322,7 @@ def nam_eval_multi(ctx, mats, q, items, rgb_out, stream=None, flags=0):
 
 
 NAM_MAX_BIN_MATERIALS = 4096
+NAM_SELECT_MAX_PASSES = 8
 
 
 def nam_eval_binned(ctx, mats, q, material_ids, n, rgb_out, stream=None, flags=0):
@@ -329,6 +331,14 @@ def nam_eval_binned(ctx, mats, q, material_ids, n, rgb_out, stream=None, flags=0
     qs = make_queries(q)
     _check(_lib.nam_eval_binned(ctx, arr, len(mats), C.byref(qs), ptr(material_ids), int(n), ptr(rgb_out),
                                 _stream(stream), flags), "nam_eval_binned")
+
+
+def nam_eval_select(ctx, mats, q, material_ids, n, rgb_out, stream=None, flags=0):
+    """Per-tile coherent/divergent selection; arguments as nam_eval_binned."""
+    arr = (C.c_void_p * len(mats))(*mats)
+    qs = make_queries(q)
+    _check(_lib.nam_eval_select(ctx, arr, len(mats), C.byref(qs), ptr(material_ids), int(n), ptr(rgb_out),
+                                _stream(stream), flags), "nam_eval_select")
 
 
 def nam_backward(ctx, mat, q, n, grad_rgb, grad_params, grad_pyramid, stream=None, flags=0):

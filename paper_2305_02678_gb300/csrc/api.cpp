@@ -173,6 +173,7 @@ static void free_material(nam_ctx* ctx, nam_material m) {
   DeviceGuard g(ctx->device);
   cudaFree(m->pyramid);
   cudaFree(m->blob);
+  cudaFree(m->simt);
   cudaFree(m->params);
   cudaFree(m->sampler);
   cudaFree(m->adam_m);
@@ -339,7 +340,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   m->shape = sh;
   m->pyr = pd;
   m->n_params = np;
-  size_t blob_bytes = 0;
+  size_t blob_bytes = 0, simt_bytes = 0;
   if (d->precision == NAM_PREC_F32) {
     blob_bytes = 0;  // the FP32 kernels read the master layout directly
   } else {
@@ -348,8 +349,9 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
       delete m;
       return fail(NAM_ERR_UNSUPPORTED, "no tensor-core kernel for this shape/precision");
     }
+    simt_bytes = simt_image_floats(sh) * 4;
   }
-  uint64_t resident = pyr_bytes + blob_bytes + (uint64_t)np * 4 + (uint64_t)smp.size() * 4 +
+  uint64_t resident = pyr_bytes + blob_bytes + simt_bytes + (uint64_t)np * 4 + (uint64_t)smp.size() * 4 +
                       4ull * encw.size() * 4;
   m->enc_in = d->encoder_inputs;
   m->enc_n = (int64_t)encw.size();
@@ -368,6 +370,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   int e = dev_alloc(ctx, &m->pyramid, pyr_bytes);
   if (!e) e = dev_alloc(ctx, (void**)&m->params, np * 4);
   if (!e && blob_bytes) e = dev_alloc(ctx, &m->blob, blob_bytes);
+  if (!e && simt_bytes) e = dev_alloc(ctx, (void**)&m->simt, simt_bytes);
   if (!e && !smp.empty()) e = dev_alloc(ctx, (void**)&m->sampler, smp.size() * 4);
   if (!e && !encw.empty()) e = dev_alloc(ctx, (void**)&m->enc, 4 * encw.size() * 4);
   if (!e && d->trainable) {
@@ -396,6 +399,12 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
       return fail(NAM_ERR_UNSUPPORTED, "weight packing failed");
     }
     e = (int)cudaMemcpy(m->blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice);
+  }
+  if (!e && simt_bytes) {
+    std::vector<float> img(simt_bytes / 4);
+    pack_simt_image(sh, d->precision, nframe ? master.data() : nullptr, master.data() + nframe,
+                    m->info.fp8_weight_scale, img.data());
+    e = (int)cudaMemcpy(m->simt, img.data(), simt_bytes, cudaMemcpyHostToDevice);
   }
   if (!e && d->trainable) {
     size_t nb = (m->pyr_off + pd.texels * 8) * 4;
@@ -784,6 +793,53 @@ extern "C" nam_status nam_eval_binned(nam_ctx* ctx, const nam_material* mats, in
   int le = launch_bin_eval(a, s);
   cudaFreeAsync(dev, s);
   if (le) return cuda_fail(le, "nam_eval_binned: launch");
+  return NAM_OK;
+}
+
+extern "C" nam_status nam_eval_select(nam_ctx* ctx, const nam_material* mats, int32_t nmat, const nam_queries* q,
+                                      const int32_t* material_ids, int64_t n, float* rgb_out, void* stream,
+                                      uint32_t flags) {
+  if (!ctx) return fail(NAM_ERR_INVALID_ARG, "nam_eval_select: NULL context");
+  if (n < 0) return fail(NAM_ERR_INVALID_ARG, "n < 0");
+  if (n > INT32_MAX) return fail(NAM_ERR_INVALID_ARG, "n beyond 2^31 - 1");
+  if (nmat > NAM_MAX_BIN_MATERIALS) return fail(NAM_ERR_INVALID_ARG, "more than %d materials", NAM_MAX_BIN_MATERIALS);
+  nam_status st = check_multi(ctx, mats, nmat);
+  if (st) return st;
+  if (n == 0) return NAM_OK;
+  if (!material_ids || !rgb_out) return fail(NAM_ERR_INVALID_ARG, "NULL material ids or output");
+  st = check_queries(mats[0], q);
+  if (st) return st;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  // one stream-ordered allocation: tile table, then pyramid, blob and image pointers
+  const size_t tb = (select_scratch_bytes(n) + 255) / 256 * 256;
+  const size_t pb = (size_t)nmat * sizeof(void*);
+  std::vector<uint8_t> host(3 * pb);
+  for (int32_t k = 0; k < nmat; ++k) {
+    const void* ptrs[3] = {mats[k]->pyramid, mats[k]->blob, mats[k]->simt};
+    for (int j = 0; j < 3; ++j) std::memcpy(host.data() + j * pb + k * sizeof(void*), &ptrs[j], sizeof(void*));
+  }
+  void* dev = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&dev, tb + host.size(), ctx->pool, s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "nam_eval_select: scratch allocation");
+  uint8_t* tab = (uint8_t*)dev + tb;
+  e = cudaMemcpyAsync(tab, host.data(), host.size(), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(dev, s);
+    return cuda_fail((int)e, "nam_eval_select: table upload");
+  }
+  SelectArgs a;
+  fill_launch(ctx, mats[0], q, n, rgb_out, flags, &a.L);
+  a.L.mats.pyramid = (const void* const*)tab;
+  a.L.mats.weights = (const void* const*)(tab + pb);
+  a.L.mats.nmat = nmat;
+  a.ids = material_ids;
+  a.images = (const float* const*)(tab + 2 * pb);
+  a.precision = mats[0]->desc.precision;
+  a.scratch = dev;
+  int le = launch_select_eval(a, s);
+  cudaFreeAsync(dev, s);
+  if (le) return cuda_fail(le, "nam_eval_select: launch");
   return NAM_OK;
 }
 

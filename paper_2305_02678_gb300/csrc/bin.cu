@@ -19,6 +19,8 @@
 // keeps its segment's screen-space neighbours together.
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include "common.cuh"
 
 namespace nam {
@@ -173,6 +175,153 @@ __global__ void __launch_bounds__(kThreads) unbin_kernel(const float* __restrict
   }
 }
 
+// Per-tile selection (Sec. 7.1: the shader picks per warp between a code
+// path for coherent and one for divergent execution).  A tcgen05 MMA covers
+// the 128 rows of a CTA's tile, so the choice is made per 128-query tile, in
+// place (no query moves):
+//   k = 1 material   one tensor-core pass (the coherent path);
+//   2 <= k <= 8      k tensor-core passes over the whole tile, one per
+//                    material, each storing only its own material's rows:
+//                    SIMT divergence serialises a warp over its branch
+//                    targets, and these passes serialise a tile over its
+//                    materials the same way, at tensor-core speed;
+//   k > 8            the divergent FP32 path, one query per thread.
+// Three passes build the pass table in tile order: per-tile material lists
+// and per-group pass counts (one warp per tile, a group = one block's eight
+// tiles), an exclusive scan of the group counts (one block, which also
+// writes the table's length for the tensor-core kernel), and the table
+// itself with the list of the tiles left to the divergent path.
+constexpr int kTilesPerBlock = kThreads / 32;  // one tile per warp in the list pass
+constexpr int kWriteThreads = 256;             // one tile per thread in the write pass
+
+__global__ void __launch_bounds__(kThreads) select_tiles_kernel(const int32_t* __restrict__ ids, int64_t n,
+                                                                int nmat, int32_t* __restrict__ tile_k,
+                                                                int32_t* __restrict__ tile_mats,
+                                                                int32_t* __restrict__ block_sums, int* err) {
+  __shared__ int32_t sum;
+  if (threadIdx.x == 0) sum = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ntiles = (n + 127) / 128;
+  int32_t mine = 0;
+  for (int j = warp; j < kTilesPerBlock; j += kThreads / 32) {
+    const int64_t t = (int64_t)blockIdx.x * kTilesPerBlock + j;
+    if (t >= ntiles) break;  // uniform over the warp
+    const int64_t base = t * 128;
+    const int cnt = (int)(n - base < 128 ? n - base : 128);
+    int v[4];  // this lane's ids; INT_MAX once taken (or absent, or invalid)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = lane + 32 * q;
+      v[q] = INT_MAX;
+      if (r < cnt) {
+        const int m = __ldg(ids + base + r);
+        if (m < 0 || m >= nmat) record_error(err, DEVERR_BOUNDS);
+        else v[q] = m;
+      }
+    }
+    // the tile's distinct materials in increasing order, at most kSelectPasses
+    int k = 0;
+    bool over = false;
+    for (;;) {
+      const int lm = min(min(v[0], v[1]), min(v[2], v[3]));
+      const int m = __reduce_min_sync(0xffffffffu, lm);
+      if (m == INT_MAX) break;
+      if (k == kSelectPasses) {
+        over = true;
+        break;
+      }
+      if (lane == 0) tile_mats[t * kSelectPasses + k] = m;
+      ++k;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (v[q] == m) v[q] = INT_MAX;
+    }
+    if (lane == 0) {
+      tile_k[t] = over ? -1 : k;
+      mine += over ? 0 : k;
+    }
+  }
+  if (lane == 0 && mine) atomicAdd(&sum, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = sum;
+}
+
+// inclusive scan over a warp
+__device__ __forceinline__ int32_t warp_scan(int32_t x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// One block of 1024: block_offs = exclusive scan of block_sums; *total = sum;
+// *n_over = 0 (the write pass counts the divergent tiles there).
+__global__ void __launch_bounds__(1024) select_scan_kernel(const int32_t* __restrict__ block_sums, int64_t nb,
+                                                           int32_t* __restrict__ block_offs,
+                                                           int32_t* __restrict__ total, int32_t* __restrict__ n_over) {
+  __shared__ int32_t wsum[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t carry = 0;
+  for (int64_t base = 0; base < nb; base += 1024) {
+    const int64_t i = base + threadIdx.x;
+    const int32_t v = i < nb ? block_sums[i] : 0;
+    const int32_t x = warp_scan(v);
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) wsum[lane] = warp_scan(wsum[lane]);
+    __syncthreads();
+    if (i < nb) block_offs[i] = carry + (warp ? wsum[warp - 1] : 0) + x - v;
+    carry += wsum[31];
+    __syncthreads();  // wsum is rewritten by the next round
+  }
+  if (threadIdx.x == 0) {
+    *total = carry;
+    *n_over = 0;
+  }
+}
+
+// One thread per tile: the tile's passes at its offset (the group's offset
+// plus the passes of the group's earlier tiles), or, for a tile with more
+// materials than passes, an entry in the divergent path's tile list.
+__global__ void __launch_bounds__(kWriteThreads) select_write_kernel(const int32_t* __restrict__ tile_k,
+                                                                     const int32_t* __restrict__ tile_mats,
+                                                                     int64_t n, const int32_t* __restrict__ block_offs,
+                                                                     Chunk* __restrict__ passes,
+                                                                     int32_t* __restrict__ over_list,
+                                                                     int32_t* __restrict__ n_over) {
+  const int lane = threadIdx.x & 31;
+  const int64_t ntiles = (n + 127) / 128;
+  const int64_t t = (int64_t)blockIdx.x * kWriteThreads + threadIdx.x;
+  const int32_t kraw = t < ntiles ? __ldg(tile_k + t) : 0;
+  const int32_t k = kraw < 0 ? 0 : kraw;
+  int32_t x = k;  // inclusive scan inside the group of kTilesPerBlock lanes
+#pragma unroll
+  for (int o = 1; o < kTilesPerBlock; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o, kTilesPerBlock);
+    if ((lane % kTilesPerBlock) >= o) x += y;
+  }
+  if (t >= ntiles) return;
+  if (kraw < 0) {
+    over_list[atomicAdd(n_over, 1)] = (int32_t)t;
+    return;
+  }
+  if (k == 0) return;
+  const int32_t o = block_offs[t / kTilesPerBlock] + x - k;
+  const int64_t base = t * 128;
+  const int cnt = (int)(n - base < 128 ? n - base : 128);
+  for (int j = 0; j < k; ++j) {
+    Chunk ch;
+    ch.start = base;
+    ch.count = cnt;
+    ch.material = __ldg(tile_mats + t * kSelectPasses + j);
+    passes[o + j] = ch;
+  }
+}
+
 }  // namespace
 
 size_t bin_scratch_bytes(int64_t n, int nmat, bool xi) {
@@ -230,6 +379,65 @@ int launch_bin_eval(const BinArgs& a, void* stream) {
   // one thread per slot: the scattered 12-byte writes want many in flight
   unbin_kernel<<<(int)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(brgb, orig, n, a.rgb_out);
   return (int)cudaGetLastError();
+}
+
+// Scratch of a selection launch: tile_k [ntiles], tile_mats [ntiles][8],
+// group sums and offsets [nb] each, the divergent tile list [ntiles], the
+// pass and divergent-tile counts, the pass table (at most one pass per query
+// and kSelectPasses per tile).
+namespace {
+struct SelectLayout {
+  size_t tile_k, tile_mats, sums, offs, over, total, passes, bytes;
+  int64_t ntiles, nb, cap;
+};
+SelectLayout select_layout(int64_t n) {
+  auto r = [](size_t b) { return (b + 255) / 256 * 256; };
+  SelectLayout l;
+  l.ntiles = (n + 127) / 128;
+  l.nb = (l.ntiles + kTilesPerBlock - 1) / kTilesPerBlock;
+  l.cap = l.ntiles * kSelectPasses < n ? l.ntiles * kSelectPasses : n;
+  l.tile_k = 0;
+  l.tile_mats = l.tile_k + r((size_t)l.ntiles * 4);
+  l.sums = l.tile_mats + r((size_t)l.ntiles * kSelectPasses * 4);
+  l.offs = l.sums + r((size_t)l.nb * 4);
+  l.over = l.offs + r((size_t)l.nb * 4);
+  l.total = l.over + r((size_t)l.ntiles * 4);  // [0] pass count, [1] divergent tiles
+  l.passes = l.total + 256;
+  l.bytes = l.passes + r((size_t)l.cap * sizeof(Chunk));
+  return l;
+}
+}  // namespace
+
+size_t select_scratch_bytes(int64_t n) { return select_layout(n).bytes; }
+
+int launch_select_eval(const SelectArgs& a, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = a.L.n;
+  if (n == 0) return 0;
+  const SelectLayout l = select_layout(n);
+  uint8_t* p = (uint8_t*)a.scratch;
+  int32_t* tile_k = (int32_t*)(p + l.tile_k);
+  int32_t* tile_mats = (int32_t*)(p + l.tile_mats);
+  int32_t* sums = (int32_t*)(p + l.sums);
+  int32_t* offs = (int32_t*)(p + l.offs);
+  int32_t* over = (int32_t*)(p + l.over);
+  int32_t* total = (int32_t*)(p + l.total);
+  int32_t* n_over = total + 1;
+  Chunk* passes = (Chunk*)(p + l.passes);
+  select_tiles_kernel<<<(int)l.nb, kThreads, 0, s>>>(a.ids, n, a.L.mats.nmat, tile_k, tile_mats, sums, a.L.err);
+  select_scan_kernel<<<1, 1024, 0, s>>>(sums, l.nb, offs, total, n_over);
+  select_write_kernel<<<(int)((l.ntiles + kWriteThreads - 1) / kWriteThreads), kWriteThreads, 0, s>>>(
+      tile_k, tile_mats, n, offs, passes, over, n_over);
+  int e = (int)cudaGetLastError();
+  if (e) return e;
+  LaunchCommon L = a.L;
+  L.chunks = passes;
+  L.n_chunks = (int32_t)l.cap;
+  L.n_chunks_dev = total;
+  L.row_ids = a.ids;
+  e = launch_material(L, a.precision, stream);
+  if (e) return e;
+  return launch_eval_divergent(a.L, a.images, a.ids, over, n_over, stream);
 }
 
 }  // namespace nam

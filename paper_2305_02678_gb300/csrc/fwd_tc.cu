@@ -158,6 +158,16 @@ static float quantize_layer_e4m3(const float* W, int rows, int cols, uint8_t* ba
   return sw;
 }
 
+// The value of an E4M3 code: sign bit, exponent field E (bias 7), mantissa
+// m; E = 0 holds the subnormals m 2^-9.
+static float e4m3_value(uint8_t c) {
+  const int E = (c >> 3) & 15, m = c & 7;
+  const float a = E == 0 ? std::ldexp((float)m, -9) : std::ldexp(1.0f + (float)m / 8.0f, E - 7);
+  return (c & 0x80) ? -a : a;
+}
+
+float e4m3_dequant(float w, float sw) { return e4m3_value(e4m3_of(w / sw)) * sw; }
+
 static void put_f(uint8_t* base, int idx, float v) { std::memcpy(base + 4 * idx, &v, 4); }
 
 // Lay out the FP16-quantised weights as MMA B operands (N rows = outputs,
@@ -380,7 +390,11 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
   const uint32_t tA = tD + 64;                          // FP16 A operand
   const uint32_t tDl = tD + lane, tAl = tA + lane;      // this warp's rows
 
-  const int64_t nchunks = L.chunks ? (int64_t)L.n_chunks : (L.n + 127) / 128;
+  int64_t nchunks = L.chunks ? (int64_t)L.n_chunks : (L.n + 127) / 128;
+  if (L.n_chunks_dev) {
+    const int64_t d = *L.n_chunks_dev;  // written by an earlier launch on this stream
+    nchunks = d < 0 ? 0 : d < nchunks ? d : nchunks;
+  }
   const int64_t per = (nchunks + gridDim.x - 1) / gridDim.x;
   const int64_t c_begin = (int64_t)blockIdx.x * per;
   const int64_t c_end = c_begin + per < nchunks ? c_begin + per : nchunks;
@@ -433,6 +447,12 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
       cn = chunk_at(L, c + NWG);
       qn = load_query(L.q, cn.start + (r < cn.count ? r : 0));
     }
+    if (ci.count <= 0) {
+      // an empty slot of a chunk table (count is uniform over the warpgroup)
+      ci = cn;
+      qc = qn;
+      continue;
+    }
     if (ci.mat != cur_mat) {
       // (re)stage the material's weights; no MMA of this warpgroup is in flight
       if (ptx::bar_red_or(bar_id, 128, bad)) break;
@@ -451,6 +471,8 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
     }
     const bool valid = r < ci.count;
     const int64_t i = ci.start + (valid ? r : 0);
+    // masked pass: this row's material, loaded now and compared at the store
+    const int32_t row_mat = L.row_ids ? __ldg(L.row_ids + i) : ci.mat;
 
     // ---- 1. latent fetch ------------------------------------------------
     float z[8];
@@ -706,7 +728,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
         const float cz = fmaxf(qc.wiz, 0.0f);
         y0 *= cz; y1 *= cz; y2 *= cz;
       }
-      if (valid) {
+      if (valid && row_mat == ci.mat) {
         L.rgb[3 * i + 0] = y0;
         L.rgb[3 * i + 1] = y1;
         L.rgb[3 * i + 2] = y2;
