@@ -35,6 +35,8 @@
 #define ORC_C 8          /* latent channels (Sec. 4: eight-dimensional code) */
 #define ORC_MAXW 256     /* widest layer the oracle accepts */
 #define ORC_MAXL 8       /* most decoder layers */
+#define ORC_MAXOUT 6     /* decoder outputs: RGB, or RGB then an albedo RGB (the
+                            optional albedo head of the paper's albedo inference) */
 
 /* ------------------------------------------------------------------------- */
 /* number formats                                                             */
@@ -143,7 +145,8 @@ typedef struct {
   int32_t out_cosine;       /* 1: multiply the output by max(0, wi.z) */
   int32_t frame_hidden;     /* hidden width of the frame MLP, 0: T = I */
   int32_t n_layers;         /* decoder linear layers */
-  int32_t widths[ORC_MAXL + 1]; /* decoder widths, widths[0] = 14 */
+  int32_t widths[ORC_MAXL + 1]; /* decoder widths, widths[0] = 14, widths[n_layers] = 3, or 6 with
+                                   the albedo head (outputs 3..5: directional albedo) */
   int32_t act_round;        /* decoder operand rounding: 0 none, 1 fp16, 2 fp8 */
   const void* pyramid;      /* levels packed finest first, [texel][C] */
   const double* frame_params; /* Wf1[h][8], bf1[h], Wf2[6][h], bf2[6] */
@@ -327,8 +330,8 @@ typedef struct {
   double wi[3], wo[3];
   double pre[ORC_MAXL][ORC_MAXW]; /* decoder pre-activations */
   double act[ORC_MAXL + 1][ORC_MAXW]; /* decoder layer inputs, act[0] = x */
-  double y[3];
-  double cosf;            /* output factor: 1 or max(0, wi.z) */
+  double y[ORC_MAXOUT];
+  double cosf;            /* BRDF output factor: 1 or max(0, wi.z) (not applied to the albedo) */
 } trace;
 
 /* ------------------------------------------------------------------------- */
@@ -560,7 +563,7 @@ static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trac
   int lastl = m->n_layers - 1;
   tr->cosf = 1.0;
   if (m->out_cosine) tr->cosf = tr->wi[2] > 0.0 ? tr->wi[2] : 0.0;
-  for (int c = 0; c < 3; ++c) tr->y[c] = tr->pre[lastl][c] * tr->cosf;
+  for (int c = 0; c < m->widths[m->n_layers]; ++c) tr->y[c] = tr->pre[lastl][c] * (c < 3 ? tr->cosf : 1.0);
 }
 
 static void forward(const orc_model* m, const orc_queries* q, int64_t i, trace* tr) {
@@ -622,13 +625,15 @@ static void* eval_worker(void* arg) {
   trace* tr = (trace*)malloc(sizeof(trace));
   for (int64_t i = j->begin; i < j->end; ++i) {
     forward(j->m, j->q, i, tr);
-    for (int c = 0; c < 3; ++c) j->out[i * 3 + c] = tr->y[c];
+    const int ow = j->m->widths[j->m->n_layers];
+    for (int c = 0; c < ow; ++c) j->out[i * ow + c] = tr->y[c];
   }
   free(tr);
   return NULL;
 }
 
-/* Full evaluation of n queries -> rgb [n][3], split over nthreads. */
+/* Full evaluation of n queries -> out [n][widths[n_layers]] (RGB, then the
+ * albedo RGB with the albedo head), split over nthreads. */
 void orc_eval(const orc_model* m, const orc_queries* q, int64_t n, double* rgb_out, int nthreads) {
   if (nthreads < 1) nthreads = 1;
   if (nthreads > 256) nthreads = 256;
@@ -689,6 +694,21 @@ double orc_loss(const double* g, const float* y, int64_t n, double* dldg_out) {
   return acc * inv;
 }
 
+/* Albedo loss (the paper's albedo inference: the extra RGB output is fitted
+ * with an L2 loss to one-sample Monte Carlo estimates of the directional
+ * albedo of Eq. 2).  Reading: L = mean (a - t)^2 over the n x 3 elements,
+ * added to the BRDF loss with weight 1; dL/da = 2 (a - t) / (3 n). */
+double orc_albedo_loss(const double* a, const float* t, int64_t n, double* dlda_out) {
+  double acc = 0.0;
+  double inv = 1.0 / (3.0 * (double)n);
+  for (int64_t i = 0; i < 3 * n; ++i) {
+    double d = a[i] - (double)t[i];
+    acc += d * d;
+    if (dlda_out) dlda_out[i] = 2.0 * d * inv;
+  }
+  return acc * inv;
+}
+
 /* ------------------------------------------------------------------------- */
 /* reverse mode                                                               */
 /* ------------------------------------------------------------------------- */
@@ -711,7 +731,8 @@ void orc_grad(const orc_model* m, const orc_queries* q, int64_t n, const double*
     forward(&mm, q, i, tr);
     int L = m->n_layers;
     /* output */
-    for (int j = 0; j < m->widths[L]; ++j) dpre[j] = (j < 3 ? dl_dy[i * 3 + j] : 0.0) * tr->cosf;
+    const int ow = m->widths[L];
+    for (int j = 0; j < ow; ++j) dpre[j] = dl_dy[i * ow + j] * (j < 3 ? tr->cosf : 1.0);
     /* decoder layers, last to first; parameter offsets */
     int64_t offs[ORC_MAXL];
     int64_t o = 0;
@@ -899,7 +920,7 @@ void orc_frame_condition(const orc_model* m, const orc_queries* q, int64_t n, do
  * the nominal result first, then the results with each subset of the three
  * ambiguous rounding decisions closest to their midpoints taken the other
  * way.  out is
- * [n][ORC_MAX_ALT][3], unused slots NaN; nalt[i] results, nsites[i]
+ * [n][ORC_MAX_ALT][widths[n_layers]], unused slots NaN; nalt[i] results, nsites[i]
  * ambiguous sites found.  gamma is the FP32 error band relative to each
  * sum's magnitude. */
 #define ORC_MAX_ALT 8
@@ -920,8 +941,9 @@ static void* alt_worker(void* arg) {
   orc_model plain = *m;
   plain.act_round = 0;
   for (int64_t i = j->begin; i < j->end; ++i) {
-    double* o = j->out + i * ORC_MAX_ALT * 3;
-    for (int k = 0; k < ORC_MAX_ALT * 3; ++k) o[k] = NAN;
+    const int ow = m->widths[m->n_layers];
+    double* o = j->out + i * ORC_MAX_ALT * ow;
+    for (int k = 0; k < ORC_MAX_ALT * ow; ++k) o[k] = NAN;
     double kappa = 1.0;
     if (m->frame_hidden > 0 || m->frame_form == 1) {
       forward(&plain, j->q, i, tr);
@@ -932,7 +954,7 @@ static void* alt_worker(void* arg) {
     rc.record = 1;
     rc.gamma = j->gamma;
     forward_rc(m, j->q, i, tr, &rc, kappa);
-    for (int c = 0; c < 3; ++c) o[c] = tr->y[c];
+    for (int c = 0; c < ow; ++c) o[c] = tr->y[c];
     int ns = rc.nsites, na = 1;
     j->nsites[i] = ns;
     /* the three sites closest to their rounding midpoints, all subsets */
@@ -956,7 +978,7 @@ static void* alt_worker(void* arg) {
         for (int k = 0; k < nk; ++k)
           if (mask & (1 << k)) fc.flip[fc.nflip++] = sites[k];
         forward_rc(m, j->q, i, tr, &fc, kappa);
-        for (int c = 0; c < 3; ++c) o[na * 3 + c] = tr->y[c];
+        for (int c = 0; c < ow; ++c) o[na * ow + c] = tr->y[c];
         ++na;
       }
     }

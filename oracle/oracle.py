@@ -79,6 +79,7 @@ def lib():
         _lib.orc_eval.argtypes = [p, p, i64, p, C.c_int]
         _lib.orc_decoder_input_absmax.argtypes = [p, p, i64, p]
         _lib.orc_loss.restype = d; _lib.orc_loss.argtypes = [p, p, i64, p]
+        _lib.orc_albedo_loss.restype = d; _lib.orc_albedo_loss.argtypes = [p, p, i64, p]
         _lib.orc_grad.argtypes = [p, p, i64, p, p, p, p, p]
         _lib.orc_relu_pattern.argtypes = [p, p, i64, p]
         _lib.orc_frame_condition.argtypes = [p, p, i64, p]
@@ -241,8 +242,10 @@ def _nq(q):
 
 
 def eval(model: Model, q, nthreads: int | None = None) -> np.ndarray:
+    """[n, 3] RGB, or [n, 6] (RGB, albedo RGB) for a decoder with the albedo
+    head (6 outputs; the cosine factor applies to the RGB only)."""
     n = _nq(q)
-    out = np.zeros((n, 3), dtype=np.float64)
+    out = np.zeros((n, model.widths[-1]), dtype=np.float64)
     if n == 0:
         return out
     qv = _QueryView(q, n)
@@ -308,10 +311,10 @@ MAX_ALT = 8
 
 def eval_alternatives(model: Model, q, gamma=2.0 ** -19, nthreads=None):
     """Every valid result of each query under the model's rounding emulation
-    (see orc_eval_alternatives): alts [n, 8, 3] (NaN-padded, nominal first),
-    nalt [n], nsites [n]."""
+    (see orc_eval_alternatives): alts [n, 8, outputs] (NaN-padded, nominal
+    first), nalt [n], nsites [n]."""
     n = _nq(q)
-    alts = np.full((n, MAX_ALT, 3), np.nan)
+    alts = np.full((n, MAX_ALT, model.widths[-1]), np.nan)
     nalt = np.zeros(n, dtype=np.int32)
     nsites = np.zeros(n, dtype=np.int32)
     if n:
@@ -372,15 +375,25 @@ def loss(g, y):
     return val, d
 
 
+def albedo_loss(a, t):
+    """(L, dL/da) of the albedo head's L2 loss over [n,3] outputs."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    n = a.shape[0]
+    d = np.zeros_like(a)
+    val = lib().orc_albedo_loss(_ptr(a), _ptr(t), n, _ptr(d))
+    return val, d
+
+
 def grad(model: Model, q, dl_dy, with_pyramid=True, with_z=False):
-    """Gradients of sum <dl_dy, y> w.r.t. frame params, decoder params, pyramid
+    """Gradients of sum <dl_dy, y> (dl_dy [n, outputs]) w.r.t. frame params, decoder params, pyramid
     and, with_z, the latent of each query ("z", [n][8]: what the encoder of
     Sec. 5.1 back-propagates; with q["z"] given the latents bypass the
     texture and the pyramid gradient stays zero)."""
     if model.frame_form == 1:
         raise NotImplementedError("reverse mode of the paper's frame form is not built")
     n = _nq(q)
-    dl = np.ascontiguousarray(dl_dy, dtype=np.float64).reshape(n, 3)
+    dl = np.ascontiguousarray(dl_dy, dtype=np.float64).reshape(n, model.widths[-1])
     gf = np.zeros(model.n_frame_params(), dtype=np.float64)
     gd = np.zeros(model.n_dec_params(), dtype=np.float64)
     gp = np.zeros((model.texel_count(), 8), dtype=np.float64) if with_pyramid else None

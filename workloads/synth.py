@@ -363,6 +363,19 @@ def target_rgb(target: ProceduralBRDF, q) -> np.ndarray:
     return target(q["u"].astype(np.float64), q["v"].astype(np.float64), wi, wo).astype(np.float32)
 
 
+def albedo_targets(rng, target: ProceduralBRDF, q) -> np.ndarray:
+    """[n, 3] float32 one-sample Monte Carlo estimates of the procedural
+    material's directional albedo (Eq. 2: the integral over the upper
+    hemisphere of f(x, wi, wo) cos(theta_i)) at each query's uv and wo: wi
+    drawn cosine-weighted (pdf cos(theta_i) / pi), so the estimate is
+    pi f(x, wi, wo).  The training data of the albedo head."""
+    n = q["u"].shape[0]
+    wi = cosine_hemisphere(rng, n)
+    wo = np.stack([q["wox"], q["woy"], q["woz"]]).astype(np.float64)
+    f = target(q["u"].astype(np.float64), q["v"].astype(np.float64), wi, wo)
+    return (np.pi * f).astype(np.float32)
+
+
 def material_attributes(target: ProceduralBRDF, q) -> np.ndarray:
     """[n, 4] float32 material parameters k(x) = (albedo RGB, roughness) of the
     procedural material at the queries' uv: the encoder's inputs."""
