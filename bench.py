@@ -453,6 +453,7 @@ def run_ours(args):
     if args.train_steps > 0 and rank == 0:
         training = run_training(ctx, dev, stream, args.train_steps)
         if args.train_steps >= 10:
+            training["albedo_head"] = run_albedo_head(ctx, dev, stream, min(1000, args.train_steps))
             training["encoder_bootstrap"] = run_encoder_bootstrap(ctx, dev, stream, args.train_steps // 2,
                                                                   args.train_steps - args.train_steps // 2)
 
@@ -887,6 +888,73 @@ def run_encoder_bootstrap(ctx, dev, stream, enc_steps, fine_steps, batch=131072,
                     "loss + reverse mode with latents from the encoder, encoder reverse mode, Adam on frame, "
                     "decoder and encoder; bake: the encoder over every texel; finetuning and direct: the "
                     "training step of the training leg"}
+
+
+def run_albedo_head(ctx, dev, stream, steps, batch=131072, pool=4, n_test=64):
+    """The optional albedo head (the paper's albedo inference) on the training
+    workload's material: its 1024^2 x 8 pyramid (11 levels) and frame MLP, a
+    14-64-64-6 decoder (RGB, then the albedo), trained with
+    nam_train_step_albedo (log-L1 on the RGB plus the L2 albedo term against
+    one-sample estimates pi f(x, wi, wo), wi cosine-weighted) on uniform
+    queries; reports the step time and the head's mean |albedo - Eq. 2| at
+    n_test points (lod 0), the integral by a 96 x 96 midpoint rule."""
+    import torch
+
+    import workloads as W
+    from paper_2305_02678_gb300 import binding as B
+    w = W.workload(4)
+    m = w["model"]
+    target = w["target"]
+    rng = W.rng_streams(W.SEEDS[4] + 31, 4)
+    dec = W.make_mlp(rng[0], (14, 64, 64, 6))
+    batches = []
+    for _ in range(pool):
+        q = W.uniform_queries(rng[1], batch, 10.0)
+        batches.append(({k: torch.from_numpy(v).to(dev) for k, v in q.items()},
+                        torch.from_numpy(W.target_rgb(target, q)).to(dev),
+                        torch.from_numpy(W.albedo_targets(rng[2], target, q)).to(dev)))
+    tq = W.uniform_queries(rng[3], n_test, 0.0)
+    k = 96
+    s_, p_ = np.meshgrid((np.arange(k) + 0.5) / k, (np.arange(k) + 0.5) / k * 2 * np.pi, indexing="ij")
+    ct, st = np.sqrt(s_.ravel()), np.sqrt(1 - s_.ravel())
+    wi = np.stack([st * np.cos(p_.ravel()), st * np.sin(p_.ravel()), ct])
+    ref = np.zeros((n_test, 3))
+    for j in range(n_test):
+        wo = np.repeat(np.array([[tq["wox"][j]], [tq["woy"][j]], [tq["woz"][j]]], np.float64), k * k, axis=1)
+        f = target(np.full(k * k, float(tq["u"][j])), np.full(k * k, float(tq["v"][j])), wi, wo)
+        ref[j] = np.pi * f.mean(axis=0)
+    dtq = {kk: torch.from_numpy(v).to(dev) for kk, v in tq.items()}
+    mat = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], dec, precision=B.NAM_PREC_F32,
+                       trainable=True)
+
+    def albedo_error():
+        _, a = mat.eval_albedo(dtq, stream=stream)
+        return float(np.mean(np.abs(a.cpu().numpy() - ref)))
+
+    e0 = albedo_error()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    losses = []
+    for s in range(1, steps + 1):
+        dq, y, ya = batches[s % pool]
+        if s == 4:
+            ev[0].record(stream)
+        l = B.nam_train_step_albedo(ctx.h, mat.h, dq, y, ya, batch, lr_params=1e-3, step=s, stream=stream,
+                                    want_loss=(s % 100 == 0 or s == 1 or s == steps))
+        if l is not None:
+            losses.append(l)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / (steps - 3)
+    e1 = albedo_error()
+    mat.destroy()
+    ctx.check()
+    return {"workload": "albedo-head-1024sq-131072", "decoder": "14-64-64-6", "batch": batch, "steps": steps,
+            "ms_per_step": round(ms, 4), "samples_per_s": round(batch * 1e3 / ms, 1),
+            "loss_every_100": [round(x, 5) for x in losses],
+            "albedo_mean_abs_error": {"before": round(e0, 4), "after": round(e1, 4),
+                                      "reference_mean": round(float(ref.mean()), 4), "points": n_test},
+            "note": "one fused kernel for forward, both losses and reverse mode (six outputs), then Adam; "
+                    "error against a 96 x 96 midpoint quadrature of Eq. 2 at lod 0"}
 
 
 def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_frames=None):

@@ -143,7 +143,10 @@ typedef struct {
                                  4 (three hidden layers, H = 64) */
   const float* frame_weights;
   /* decoder widths[0] = 14 (20 with NAM_FRAME_PAPER), widths[1..n_layers-1]
-   * = H (16, 32 or 64, all equal), widths[n_layers] = 3.  Weights FP32
+   * = H (16, 32 or 64, all equal), widths[n_layers] = 3, or 6 with the
+   * albedo head (the paper's albedo inference: outputs 3..5 approximate the
+   * directional albedo of Eq. 2, read with nam_eval_albedo; the cosine
+   * factor never applies to them; no encoder with the head).  Weights FP32
    * master values, per layer W (out x in) then b (out), layers in order. */
   int32_t widths[NAM_MAX_LAYERS + 1];
   const float* decoder_weights;
@@ -218,9 +221,18 @@ enum {
 };
 
 /* Evaluate n queries whose arrays are device memory; writes rgb_out (device,
- * [n][3]).  n = 0 is a no-op.  Asynchronous on `stream`. */
+ * [n][3]).  n = 0 is a no-op.  Asynchronous on `stream`.  A material with
+ * the albedo head gives its RGB here (its albedo: nam_eval_albedo). */
 nam_status nam_eval(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
                     float* rgb_out, void* stream, uint32_t flags);
+
+/* The albedo head (a material created with widths[n_layers] = 6): one pass
+ * writes the RGB of nam_eval to rgb_out and the directional albedo
+ * alpha(x, wo) the decoder infers (the paper's albedo inference; its extra
+ * RGB triplet, no cosine factor) to albedo_out, both device [n][3].  Every
+ * precision; NAM_ERR_UNSUPPORTED for a material without the head. */
+nam_status nam_eval_albedo(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
+                           float* rgb_out, float* albedo_out, void* stream, uint32_t flags);
 
 /* Same with HOST query and output arrays; synchronises the stream before it
  * returns.  Where the device reads host memory through the host's page
@@ -421,7 +433,8 @@ nam_status nam_scene_render_paths(nam_ctx* ctx, const nam_scene* scene, const na
 /* differentiation and training (Sec. 5.2)                                  */
 /* ------------------------------------------------------------------------ */
 /* Reverse mode of nam_eval for a trainable (F32) material: given grad_rgb
- * (device [n][3]) accumulates (adds, does not zero) the gradient of
+ * (device [n][3]; [n][6] for a material with the albedo head: dL/d(RGB),
+ * then dL/d(albedo)) accumulates (adds, does not zero) the gradient of
  * sum <grad_rgb, rgb> into grad_params (device [n_params], layout of the
  * masters) and grad_pyramid (device [texels][8], 16-byte aligned; may be
  * NULL; a misaligned pointer is refused with NAM_ERR_INVALID_ARG).  Weight
@@ -448,6 +461,17 @@ typedef struct {
  * allocates the material's 256-byte loss accumulator. */
 nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
                           int64_t n, const nam_adam* opt, float* loss_out, void* stream, uint32_t flags);
+
+/* nam_train_step for a material with the albedo head (the paper's albedo
+ * inference): the loss adds mean (a - t)^2 over the n x 3 albedo outputs,
+ * t the device [n][3] target_albedo, one-sample Monte Carlo estimates of the
+ * directional albedo (Eq. 2: e.g. pi f(x, wi, wo) for wi drawn
+ * cosine-weighted), so that the head converges to their mean.  *loss_out
+ * receives the sum of both terms.  nam_train_step (and its no-allocation
+ * form) refuses a material with the head, this call one without it. */
+nam_status nam_train_step_albedo(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
+                                 const float* target_albedo, int64_t n, const nam_adam* opt, float* loss_out,
+                                 void* stream, uint32_t flags);
 
 /* A training step that allocates no device memory.  The paper has no
  * counterpart: this is a library facility.  nam_train_step allocates a

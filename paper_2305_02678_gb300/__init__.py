@@ -142,6 +142,19 @@ class Material:
         B.nam_eval(self.ctx.h, self.h, q, n, out, stream, flags)
         return out
 
+    def eval_albedo(self, q, stream=None, flags=0):
+        """(rgb [n, 3], albedo [n, 3]) of a material with the albedo head."""
+        import torch
+
+        from . import binding as B
+        n = int(q["u"].shape[0])
+        rgb = torch.empty((n, 3), dtype=torch.float32, device=q["u"].device)
+        alb = torch.empty((n, 3), dtype=torch.float32, device=q["u"].device)
+        if stream is None:
+            stream = torch.cuda.current_stream(q["u"].device)
+        B.nam_eval_albedo(self.ctx.h, self.h, q, n, rgb, alb, stream, flags)
+        return rgb, alb
+
     def eval_host(self, q, out=None, stream=None, flags=0):
         """q: dict of host float32 arrays (numpy or pinned torch).  Synchronous."""
         from . import binding as B

@@ -48,7 +48,9 @@ class NeuralBRDFFunction(torch.autograd.Function):
     latent pyramid.  `params` and `pyramid` must be the tensors
     material_tensors() returned for `mat`: the kernels read the material's own
     storage, and the tensors are passed so that autograd routes gradients to
-    them (and notices in-place updates between forward and backward)."""
+    them (and notices in-place updates between forward and backward).  With
+    the albedo head (six decoder outputs) the result is [n, 6]: RGB, then the
+    directional albedo, and the gradient flowing back has that layout."""
 
     @staticmethod
     def forward(ctx, params, pyramid, mat, queries, flags):
@@ -56,8 +58,15 @@ class NeuralBRDFFunction(torch.autograd.Function):
         if params.data_ptr() != p or pyramid.data_ptr() != z:
             raise ValueError("params/pyramid must be the material's own tensors (material_tensors)")
         n = int(queries["u"].shape[0])
-        out = torch.empty((n, 3), dtype=torch.float32, device=params.device)
-        B.nam_eval(mat.ctx.h, mat.h, queries, n, out, torch.cuda.current_stream(params.device), flags)
+        stream = torch.cuda.current_stream(params.device)
+        if mat.widths[-1] == 6:
+            rgb = torch.empty((n, 3), dtype=torch.float32, device=params.device)
+            alb = torch.empty((n, 3), dtype=torch.float32, device=params.device)
+            B.nam_eval_albedo(mat.ctx.h, mat.h, queries, n, rgb, alb, stream, flags)
+            out = torch.cat([rgb, alb], dim=1)
+        else:
+            out = torch.empty((n, 3), dtype=torch.float32, device=params.device)
+            B.nam_eval(mat.ctx.h, mat.h, queries, n, out, stream, flags)
         ctx.save_for_backward(params, pyramid)
         ctx.mat, ctx.queries, ctx.flags, ctx.n = mat, queries, flags, n
         return out
@@ -68,6 +77,8 @@ class NeuralBRDFFunction(torch.autograd.Function):
         mat = ctx.mat
         gp = torch.zeros_like(params) if ctx.needs_input_grad[0] else None
         gz = torch.zeros_like(pyramid) if ctx.needs_input_grad[1] else None
+        if grad_rgb.shape != (ctx.n, mat.widths[-1]):
+            raise ValueError(f"output gradient of shape {tuple(grad_rgb.shape)}, expected ({ctx.n}, {mat.widths[-1]})")
         if gp is not None or gz is not None:
             B.nam_backward(mat.ctx.h, mat.h, ctx.queries, ctx.n, grad_rgb.contiguous().float(), gp, gz,
                            torch.cuda.current_stream(params.device), ctx.flags)

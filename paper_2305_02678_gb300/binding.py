@@ -121,7 +121,7 @@ class nam_stats(C.Structure):
 #: every symbol include/nam.h declares
 EXPORTS = ("nam_status_string", "nam_last_error_message", "nam_init", "nam_shutdown", "nam_check_device_error",
            "nam_create_material", "nam_destroy_material", "nam_material_get_info", "nam_material_params",
-           "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_eval_binned", "nam_eval_select", "nam_fp8_calibrate", "nam_sample", "nam_sample_pdf", "nam_backward", "nam_train_step",
+           "nam_eval", "nam_eval_host", "nam_eval_multi", "nam_eval_binned", "nam_eval_select", "nam_fp8_calibrate", "nam_sample", "nam_sample_pdf", "nam_backward", "nam_train_step", "nam_eval_albedo", "nam_train_step_albedo",
            "nam_train_step_noalloc", "nam_encode", "nam_encoder_bake", "nam_backward_encoded",
            "nam_train_step_encoded", "nam_material_encoder", "nam_scene_gbuffer", "nam_scene_render_direct",
            "nam_scene_render_paths",
@@ -158,6 +158,8 @@ def _load():
         "nam_eval_select": (i32, [p, p, i32, p, p, i64, p, p, u32]),
         "nam_backward": (i32, [p, p, p, i64, p, p, p, p, u32]),
         "nam_train_step": (i32, [p, p, p, p, i64, p, p, p, u32]),
+        "nam_eval_albedo": (i32, [p, p, p, i64, p, p, p, u32]),
+        "nam_train_step_albedo": (i32, [p, p, p, p, p, i64, p, p, p, u32]),
         "nam_train_step_noalloc": (i32, [p, p, p, p, i64, p, p, p, u32]),
         "nam_encode": (i32, [p, p, p, i64, p, p]),
         "nam_encoder_bake": (i32, [p, p, p, p]),
@@ -283,6 +285,13 @@ def nam_eval(ctx, mat, q, n, rgb_out, stream=None, flags=0):
     _check(_lib.nam_eval(ctx, mat, C.byref(qs), int(n), ptr(rgb_out), _stream(stream), flags), "nam_eval")
 
 
+def nam_eval_albedo(ctx, mat, q, n, rgb_out, albedo_out, stream=None, flags=0):
+    """RGB and the albedo head's directional albedo, both device [n][3]."""
+    qs = make_queries(q)
+    _check(_lib.nam_eval_albedo(ctx, mat, C.byref(qs), int(n), ptr(rgb_out), ptr(albedo_out), _stream(stream),
+                                flags), "nam_eval_albedo")
+
+
 def nam_fp8_calibrate(ctx, mat, q, n, stream=None):
     """Static per-layer FP8 activation scales (max |layer input| / 448) of
     material `mat` over n device queries; returns a float32 numpy array."""
@@ -356,6 +365,18 @@ def nam_train_step(ctx, mat, q, target_rgb, n, lr_params=1e-3, lr_pyramid=1e-2, 
     qs = make_queries(q)
     _check(_lib.nam_train_step(ctx, mat, C.byref(qs), ptr(target_rgb), int(n), C.byref(opt),
                                C.byref(loss) if want_loss else None, _stream(stream), flags), "nam_train_step")
+    return loss.value if want_loss else None
+
+
+def nam_train_step_albedo(ctx, mat, q, target_rgb, target_albedo, n, lr_params=1e-3, lr_pyramid=1e-2, beta1=0.9,
+                          beta2=0.999, eps=1e-8, step=1, stream=None, flags=0, want_loss=True):
+    """nam_train_step with the albedo head's L2 term; returns the summed loss."""
+    opt = nam_adam(lr_params, lr_pyramid, beta1, beta2, eps, step)
+    loss = C.c_float(0.0)
+    qs = make_queries(q)
+    _check(_lib.nam_train_step_albedo(ctx, mat, C.byref(qs), ptr(target_rgb), ptr(target_albedo), int(n),
+                                      C.byref(opt), C.byref(loss) if want_loss else None, _stream(stream), flags),
+           "nam_train_step_albedo")
     return loss.value if want_loss else None
 
 

@@ -246,8 +246,9 @@ nam_status nam::validate_desc(const nam_material_desc* d, Shape* shape, PyrDesc*
     return fail(NAM_ERR_UNSUPPORTED, "n_layers must be 3 or 4: two or three hidden layers (got %d)", d->n_layers);
   const int H = d->widths[1];
   const int in = paper ? 20 : 14;
-  if (d->widths[0] != in || d->widths[d->n_layers] != 3)
-    return fail(NAM_ERR_UNSUPPORTED, "decoder must map %d inputs to 3 outputs", in);
+  const int n_out = d->widths[d->n_layers];
+  if (d->widths[0] != in || (n_out != 3 && n_out != 6))
+    return fail(NAM_ERR_UNSUPPORTED, "decoder must map %d inputs to 3 outputs (6 with the albedo head)", in);
   for (int l = 1; l < d->n_layers; ++l)
     if (d->widths[l] != H) return fail(NAM_ERR_UNSUPPORTED, "hidden widths must be equal");
   if (H != 16 && H != 32 && H != 64) return fail(NAM_ERR_UNSUPPORTED, "hidden width %d not in {16, 32, 64}", H);
@@ -278,10 +279,13 @@ nam_status nam::validate_desc(const nam_material_desc* d, Shape* shape, PyrDesc*
   if (d->encoder_inputs && !d->trainable)
     return fail(NAM_ERR_UNSUPPORTED, "an encoder needs a trainable material (it exists only for training)");
   if (d->encoder_inputs && !d->encoder_weights) return fail(NAM_ERR_INVALID_ARG, "encoder_weights is NULL");
+  if (d->encoder_inputs && n_out != 3)
+    return fail(NAM_ERR_UNSUPPORTED, "the encoder phase trains the RGB decoder only (no albedo head)");
   shape->H = H;
   shape->NH = d->n_layers - 1;
   shape->frame = paper ? 2 : (d->frame_hidden ? 1 : 0);
   shape->in = in;
+  shape->out = n_out;
   std::memset(pyr, 0, sizeof *pyr);
   pyr->levels = d->levels;
   pyr->f16 = d->latent_dtype == NAM_LATENT_F16;
@@ -514,6 +518,25 @@ extern "C" nam_status nam_eval(nam_ctx* ctx, nam_material m, const nam_queries* 
   return NAM_OK;
 }
 
+extern "C" nam_status nam_eval_albedo(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
+                                      float* rgb_out, float* albedo_out, void* stream, uint32_t flags) {
+  if (!ctx || !m) return fail(NAM_ERR_INVALID_ARG, "nam_eval_albedo: NULL context or material");
+  if (n < 0) return fail(NAM_ERR_INVALID_ARG, "nam_eval_albedo: n < 0");
+  if (!owns(ctx, m)) return fail(NAM_ERR_NOT_FOUND, "nam_eval_albedo: unknown material");
+  if (m->shape.out != 6) return fail(NAM_ERR_UNSUPPORTED, "nam_eval_albedo: the material has no albedo head");
+  if (n == 0) return NAM_OK;
+  if (!rgb_out || !albedo_out) return fail(NAM_ERR_INVALID_ARG, "nam_eval_albedo: NULL output");
+  nam_status st = check_queries(m, q);
+  if (st) return st;
+  DeviceGuard g(ctx->device);
+  LaunchCommon L;
+  fill_launch(ctx, m, q, n, rgb_out, flags, &L);
+  L.albedo = albedo_out;
+  int e = launch_material(L, m->desc.precision, stream);
+  if (e) return cuda_fail(e, "nam_eval_albedo: launch");
+  return NAM_OK;
+}
+
 extern "C" nam_status nam_fp8_calibrate(nam_ctx* ctx, nam_material m, const nam_queries* q, int64_t n,
                                         float* act_scale_out, void* stream) {
   if (!ctx || !m || !act_scale_out) return fail(NAM_ERR_INVALID_ARG, "nam_fp8_calibrate: NULL argument");
@@ -685,7 +708,7 @@ nam_status nam::check_multi(nam_ctx* ctx, const nam_material* mats, int32_t nmat
     const nam_material m = mats[k];
     if (m->desc.precision == NAM_PREC_F32) return fail(NAM_ERR_UNSUPPORTED, "multi-material launches use the tensor-core path");
     if (m->desc.precision != m0->desc.precision || m->shape.H != m0->shape.H || m->shape.NH != m0->shape.NH ||
-        m->shape.frame != m0->shape.frame || m->shape.in != m0->shape.in)
+        m->shape.frame != m0->shape.frame || m->shape.in != m0->shape.in || m->shape.out != m0->shape.out)
       return fail(NAM_ERR_INVALID_ARG, "materials must share precision and MLP shape");
     if (std::memcmp(&m->pyr, &m0->pyr, sizeof(PyrDesc)) != 0)
       return fail(NAM_ERR_INVALID_ARG, "materials must share pyramid geometry, dtype, filter and addressing");

@@ -18,7 +18,10 @@
 //  Training step variant (LOSS): the decoder blocks also finish the forward
 //  (y = Wo h2 + bo, summed over the half-warp), evaluate the log-space L1
 //  loss against the target and start the backward from its gradient, so a
-//  training step needs no separate forward or loss pass.
+//  training step needs no separate forward or loss pass.  With the albedo
+//  head (ALB: six outputs, RGB then albedo) the fused loss adds the albedo's
+//  L2 error against one-sample albedo estimates (the paper's albedo
+//  inference), and the output layer's gradient blocks span eight rows.
 //  Phase B (thread = 4x4 block of one weight matrix): each owner sums the
 //  outer products delta[q][rows] * act[q][cols] over the tile in registers
 //  (two 16-byte shared loads per 16 FMAs), the column-0 owners also sum the
@@ -38,8 +41,10 @@ namespace nam {
 constexpr int kBwdQ = 128;             // queries per tile
 constexpr int kBwdThreads = 4 * kBwdQ;  // a quad per query
 
-template <int H>
+template <int H, bool ALB = false>
 struct BwdSmem {
+  static constexpr int NO = ALB ? 6 : 3;  // decoder outputs
+  static constexpr int DW = ALB ? 8 : 4;  // DY row length
   static constexpr int S = H + 4;  // padded row stride: rows l + 16 jj of a half-warp hit distinct banks
   // parameters
   float fW1[16 * 8], fb1[16], fW2[6 * 16], fb2[8];
@@ -47,7 +52,7 @@ struct BwdSmem {
   float b1[H];
   float W2[H][S];    // W2[j][k]
   float b2[H];
-  float Wo[3 * H], bo[4];
+  float Wo[NO * H], bo[8];
   float lred[16];  // per-warp loss partials
   // per-query vectors of the current tile (deltas at pre-activations)
   float Z[kBwdQ][8];     // frame MLP input (z)
@@ -61,8 +66,10 @@ struct BwdSmem {
   float H1[kBwdQ][S];    // decoder layer-1 activations
   float D2[kBwdQ][S];    // delta at layer-2 pre-activations
   float H2[kBwdQ][S];    // layer-2 activations
-  float DY[kBwdQ][4];    // delta at the output (after the cosine factor), zero padding;
-                         // with the fused loss first (target, cosine factor)
+  float DY[kBwdQ][DW];   // delta at the outputs (after the cosine factor), zero padding;
+                         // with the fused loss first the targets and the cosine
+                         // factor: (t_r, t_g, t_b, cf), or with ALB (t_r, t_g, t_b,
+                         // albedo t_r, t_g, t_b, 0, cf)
 };
 
 // Log-space L1 loss of one output element g against its target y (Sec. 5.2
@@ -94,10 +101,12 @@ __device__ __forceinline__ float dot4(const float4 a, const float4 b, float s) {
   return fmaf(a.w, b.w, s);
 }
 
-template <int H, bool FRAME, bool F16, bool LOSS>
+template <int H, bool FRAME, bool F16, bool LOSS, bool ALB>
 __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const BackwardArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  BwdSmem<H>& S = *reinterpret_cast<BwdSmem<H>*>(smem_raw);
+  using Sm = BwdSmem<H, ALB>;
+  Sm& S = *reinterpret_cast<Sm*>(smem_raw);
+  constexpr int NO = Sm::NO, DW = Sm::DW;
   constexpr int JB = H / 16;  // hidden units per lane in the decoder blocks
   const int t = threadIdx.x;
   // ---- parameters -> shared ---------------------------------------------------
@@ -121,20 +130,21 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
     p += H * H;
     for (int i = t; i < H; i += kBwdThreads) S.b2[i] = p[i];
     p += H;
-    for (int i = t; i < 3 * H; i += kBwdThreads) S.Wo[i] = p[i];
-    p += 3 * H;
-    if (t < 4) S.bo[t] = t < 3 ? p[t] : 0.0f;
+    for (int i = t; i < NO * H; i += kBwdThreads) S.Wo[i] = p[i];
+    p += NO * H;
+    if (t < 8) S.bo[t] = t < NO ? p[t] : 0.0f;
   }
   // coarse-level accumulators after the tile: [16 warps][tiny_n][8], [cta_n][8]
-  float* wacc = reinterpret_cast<float*>(smem_raw + sizeof(BwdSmem<H>));
+  float* wacc = reinterpret_cast<float*>(smem_raw + sizeof(Sm));
   float* cacc = wacc + 16 * 8 * A.tiny_n;
   for (int i = t; i < 8 * (16 * A.tiny_n + A.cta_n); i += kBwdThreads) wacc[i] = 0.0f;
   float* my_wacc = wacc + (t >> 5) * 8 * A.tiny_n;
 
   // ---- phase-B ownership: one 4x4 block of one gradient matrix ------------------
-  // blocks: dW2 (H/4)^2, dW1 H/4 x 4 (14 columns padded to 16), dWo 1 x H/4
-  // (3 rows padded to 4), dWf1 4 x 2, dWf2 2 x 4 (6 rows padded to 8)
-  constexpr int NB2 = (H / 4) * (H / 4), NB1 = H, NBO = H / 4;
+  // blocks: dW2 (H/4)^2, dW1 H/4 x 4 (14 columns padded to 16), dWo
+  // DW/4 x H/4 (3 rows padded to 4, or 6 padded to 8), dWf1 4 x 2, dWf2 2 x 4
+  // (6 rows padded to 8)
+  constexpr int NB2 = (H / 4) * (H / 4), NB1 = H, NBO = (DW / 4) * (H / 4);
   int role = -1, r0 = 0, c0 = 0;
   const float* dp = nullptr;
   const float* ap = nullptr;
@@ -143,13 +153,13 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
     int b = t;
     if (b < NB2) {
       role = 0; r0 = 4 * (b / (H / 4)); c0 = 4 * (b % (H / 4));
-      dp = &S.D2[0][r0]; dstride = BwdSmem<H>::S; ap = &S.H1[0][c0]; astride = BwdSmem<H>::S;
+      dp = &S.D2[0][r0]; dstride = Sm::S; ap = &S.H1[0][c0]; astride = Sm::S;
     } else if ((b -= NB2) < NB1) {
       role = 1; r0 = 4 * (b >> 2); c0 = 4 * (b & 3);
-      dp = &S.D1[0][r0]; dstride = BwdSmem<H>::S; ap = &S.X[0][c0]; astride = 16;
+      dp = &S.D1[0][r0]; dstride = Sm::S; ap = &S.X[0][c0]; astride = 16;
     } else if ((b -= NB1) < NBO) {
-      role = 2; r0 = 0; c0 = 4 * b;
-      dp = &S.DY[0][0]; dstride = 4; ap = &S.H2[0][c0]; astride = BwdSmem<H>::S;
+      role = 2; r0 = 4 * (b / (H / 4)); c0 = 4 * (b % (H / 4));
+      dp = &S.DY[0][r0]; dstride = DW; ap = &S.H2[0][c0]; astride = Sm::S;
     } else if (FRAME && (b -= NBO) < 8) {
       role = 3; r0 = 4 * (b >> 1); c0 = 4 * (b & 1);
       dp = &S.DHF[0][r0]; dstride = 16; ap = &S.Z[0][c0]; astride = 8;
@@ -235,15 +245,28 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
         reinterpret_cast<float4*>(&S.Z[ql][0])[0] = make_float4(z[0], z[1], z[2], z[3]);
         reinterpret_cast<float4*>(&S.Z[ql][0])[1] = make_float4(z[4], z[5], z[6], z[7]);
         const float cf = cosine ? fmaxf(wi[2], 0.0f) : 1.0f;
+        float4* dy4 = reinterpret_cast<float4*>(&S.DY[ql][0]);
         if (LOSS) {
           const float* tg = A.target + 3 * i;
-          reinterpret_cast<float4*>(&S.DY[ql][0])[0] =
-              valid ? make_float4(tg[0], tg[1], tg[2], cf) : make_float4(0.0f, 0.0f, 0.0f, cf);
+          if (ALB) {
+            const float* ta = A.target_albedo + 3 * i;
+            dy4[0] = valid ? make_float4(tg[0], tg[1], tg[2], ta[0]) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            dy4[1] = valid ? make_float4(ta[1], ta[2], 0.0f, cf) : make_float4(0.0f, 0.0f, 0.0f, cf);
+          } else {
+            dy4[0] = valid ? make_float4(tg[0], tg[1], tg[2], cf) : make_float4(0.0f, 0.0f, 0.0f, cf);
+          }
+        } else if constexpr (ALB) {
+          // dL/d(output) of the caller, [n][6]; the cosine factor scales the RGB only
+          float dy[6];
+#pragma unroll
+          for (int c = 0; c < 6; ++c) dy[c] = valid ? A.grad_rgb[6 * i + c] * (c < 3 ? cf : 1.0f) : 0.0f;
+          dy4[0] = make_float4(dy[0], dy[1], dy[2], dy[3]);
+          dy4[1] = make_float4(dy[4], dy[5], 0.0f, 0.0f);
         } else {
           float dy[3];
 #pragma unroll
           for (int c = 0; c < 3; ++c) dy[c] = valid ? A.grad_rgb[3 * i + c] * cf : 0.0f;
-          reinterpret_cast<float4*>(&S.DY[ql][0])[0] = make_float4(dy[0], dy[1], dy[2], 0.0f);
+          dy4[0] = make_float4(dy[0], dy[1], dy[2], 0.0f);
         }
       }
     }
@@ -298,51 +321,143 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
         // output y = Wo relu(a) + bo of the four queries, summed over the
         // half-warp; lane (mq, mc) = (hl / 4, hl % 4) takes element mc of
         // query qb + mq: loss and dL/dy (times the cosine factor) into DY
-        float y[4][3];
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) y[qq][c] = 0.0f;
-#pragma unroll
-        for (int jj = 0; jj < JB; ++jj) {
-          const int j = hl + 16 * jj;
-          const float o[3] = {S.Wo[j], S.Wo[H + j], S.Wo[2 * H + j]};
-#pragma unroll
-          for (int qq = 0; qq < 4; ++qq) {
-            const float h = fmaxf(a[qq][jj], 0.0f);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) y[qq][c] = fmaf(o[c], h, y[qq][c]);
-          }
-        }
-#pragma unroll
-        for (int off = 1; off < 16; off <<= 1)
+        if constexpr (ALB) {
+          float y[4][NO];
 #pragma unroll
           for (int qq = 0; qq < 4; ++qq)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) y[qq][c] += __shfl_xor_sync(0xffffffffu, y[qq][c], off);
-        const int mq = hl >> 2, mc = hl & 3;
-        float ym = 0.0f;
+            for (int c = 0; c < NO; ++c) y[qq][c] = 0.0f;
+#pragma unroll
+          for (int jj = 0; jj < JB; ++jj) {
+            const int j = hl + 16 * jj;
+            float o[NO];
+#pragma unroll
+            for (int c = 0; c < NO; ++c) o[c] = S.Wo[c * H + j];
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              const float h = fmaxf(a[qq][jj], 0.0f);
+#pragma unroll
+              for (int c = 0; c < NO; ++c) y[qq][c] = fmaf(o[c], h, y[qq][c]);
+            }
+          }
+#pragma unroll
+          for (int off = 1; off < 16; off <<= 1)
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+              for (int c = 0; c < NO; ++c) y[qq][c] += __shfl_xor_sync(0xffffffffu, y[qq][c], off);
+          // lane (mq, mc) takes output elements mc and, with ALB, mc + 4 of query qb + mq
+          const int mq = hl >> 2, mc = hl & 3;
+          float ym[2] = {0.0f, 0.0f};
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+            for (int c = 0; c < NO; ++c) {
+              if (qq == mq && c == mc) ym[0] = y[qq][c];
+              if (qq == mq && c == mc + 4) ym[1] = y[qq][c];
+            }
+          float tv[DW];  // targets; the cosine factor last
+#pragma unroll
+          for (int c4 = 0; c4 < DW / 4; ++c4) {
+            const float4 v = reinterpret_cast<const float4*>(&S.DY[qb + mq][0])[c4];
+            tv[4 * c4] = v.x; tv[4 * c4 + 1] = v.y; tv[4 * c4 + 2] = v.z; tv[4 * c4 + 3] = v.w;
+          }
+          const float cf = tv[DW - 1];
+          const bool vq = qb + mq < count;
+          __syncwarp();
+#pragma unroll
+          for (int h2 = 0; h2 < DW / 4; ++h2) {
+            const int e = mc + 4 * h2;  // output element of this lane
+            float tgt = 0.0f;
+#pragma unroll
+            for (int c = 0; c < NO; ++c)
+              if (c == e) tgt = tv[c];
+            float d = 0.0f;
+            if (e < 3) {
+              // BRDF: log-space L1 of the cosine-weighted output
+              const float g = (ym[h2] + S.bo[e]) * cf;
+              float gr;
+              const float l = log_l1(g, tgt, &gr);
+              if (vq) lsum += l;
+              d = gr * A.loss_inv * cf;
+            } else if (e < NO) {
+              // albedo head: L2 against the one-sample albedo estimate
+              const float r = ym[h2] + S.bo[e] - tgt;
+              if (vq) lsum += r * r;
+              d = 2.0f * r * A.loss_inv;
+            }
+            S.DY[qb + mq][e] = vq ? d : 0.0f;
+          }
+          __syncwarp();
+        } else {
+          float y[4][3];
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) y[qq][c] = 0.0f;
+#pragma unroll
+          for (int jj = 0; jj < JB; ++jj) {
+            const int j = hl + 16 * jj;
+            const float o[3] = {S.Wo[j], S.Wo[H + j], S.Wo[2 * H + j]};
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+              const float h = fmaxf(a[qq][jj], 0.0f);
+#pragma unroll
+              for (int c = 0; c < 3; ++c) y[qq][c] = fmaf(o[c], h, y[qq][c]);
+            }
+          }
+#pragma unroll
+          for (int off = 1; off < 16; off <<= 1)
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+              for (int c = 0; c < 3; ++c) y[qq][c] += __shfl_xor_sync(0xffffffffu, y[qq][c], off);
+          const int mq = hl >> 2, mc = hl & 3;
+          float ym = 0.0f;
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              if (qq == mq && c == mc) ym = y[qq][c];
+          const float4 tv = *reinterpret_cast<const float4*>(&S.DY[qb + mq][0]);
+          __syncwarp();
+          if (mc < 3) {
+            const float g = (ym + S.bo[mc]) * tv.w;
+            float gr;
+            const float l = log_l1(g, mc == 0 ? tv.x : mc == 1 ? tv.y : tv.z, &gr);
+            const bool vq = qb + mq < count;
+            if (vq) lsum += l;
+            S.DY[qb + mq][mc] = vq ? gr * A.loss_inv * tv.w : 0.0f;
+          } else {
+            S.DY[qb + mq][3] = 0.0f;
+          }
+          __syncwarp();
+        }
+      }
+      // layer-2 delta d2 = (Wo^T dy) where the unit is active
+      if constexpr (ALB) {
+        float dyv[4][NO];
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq)
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            if (qq == mq && c == mc) ym = y[qq][c];
-        const float4 tv = *reinterpret_cast<const float4*>(&S.DY[qb + mq][0]);
-        __syncwarp();
-        if (mc < 3) {
-          const float g = (ym + S.bo[mc]) * tv.w;
-          float gr;
-          const float l = log_l1(g, mc == 0 ? tv.x : mc == 1 ? tv.y : tv.z, &gr);
-          const bool vq = qb + mq < count;
-          if (vq) lsum += l;
-          S.DY[qb + mq][mc] = vq ? gr * A.loss_inv * tv.w : 0.0f;
-        } else {
-          S.DY[qb + mq][3] = 0.0f;
+          for (int c = 0; c < NO; ++c) dyv[qq][c] = S.DY[qb + qq][c];
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+          const int j = hl + 16 * jj;
+          float o[NO];
+#pragma unroll
+          for (int c = 0; c < NO; ++c) o[c] = S.Wo[c * H + j];
+#pragma unroll
+          for (int qq = 0; qq < 4; ++qq) {
+            const float s = a[qq][jj];
+            float d = o[NO - 1] * dyv[qq][NO - 1];
+#pragma unroll
+            for (int c = NO - 2; c >= 0; --c) d = fmaf(o[c], dyv[qq][c], d);
+            S.H2[qb + qq][j] = fmaxf(s, 0.0f);
+            S.D2[qb + qq][j] = s > 0.0f ? d : 0.0f;
+          }
         }
-        __syncwarp();
-      }
-      // layer-2 delta d2 = (Wo^T dy) where the unit is active
-      {
+      } else {
         float4 dyv[4];
 #pragma unroll
         for (int qq = 0; qq < 4; ++qq) dyv[qq] = *reinterpret_cast<const float4*>(&S.DY[qb + qq][0]);
@@ -613,13 +728,13 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
   if (role < 0) return;
   float* g = A.grad_params;
   const int o = FRAME ? 246 : 0;
-  const int oW1 = o, ob1 = o + 14 * H, oW2 = ob1 + H, ob2 = oW2 + H * H, oWo = ob2 + H, obo = oWo + 3 * H;
+  const int oW1 = o, ob1 = o + 14 * H, oW2 = ob1 + H, ob2 = oW2 + H * H, oWo = ob2 + H, obo = oWo + NO * H;
   // (weight offset, row stride, valid rows, valid columns, bias offset)
   int wo_ = 0, ws = 0, nr = 0, nc = 0, bo_ = 0;
   switch (role) {
     case 0: wo_ = oW2; ws = H; nr = H; nc = H; bo_ = ob2; break;
     case 1: wo_ = oW1; ws = 14; nr = H; nc = 14; bo_ = ob1; break;
-    case 2: wo_ = oWo; ws = H; nr = 3; nc = H; bo_ = obo; break;
+    case 2: wo_ = oWo; ws = H; nr = NO; nc = H; bo_ = obo; break;
     case 3: wo_ = 0; ws = 8; nr = 16; nc = 8; bo_ = 128; break;
     default: wo_ = 144; ws = 16; nr = 6; nc = 16; bo_ = 240; break;
   }
@@ -634,11 +749,11 @@ __global__ void __launch_bounds__(kBwdThreads, 1) backward_kernel(const Backward
   }
 }
 
-template <int H, bool FRAME, bool F16, bool LOSS>
+template <int H, bool FRAME, bool F16, bool LOSS, bool ALB>
 static int launch_bwd_one(const BackwardArgs& a, cudaStream_t s) {
-  auto k = backward_kernel<H, FRAME, F16, LOSS>;
+  auto k = backward_kernel<H, FRAME, F16, LOSS, ALB>;
   constexpr int kSmemMax = 227 * 1024;
-  constexpr int kBase = (int)sizeof(BwdSmem<H>);
+  constexpr int kBase = (int)sizeof(BwdSmem<H, ALB>);
   static_assert(kBase <= kSmemMax, "backward tile does not fit in shared memory");
   // coarse-level accumulators in what the tile leaves: per-warp copies of the
   // coarsest levels up to kTiny texels, then one copy of the next levels
@@ -671,12 +786,23 @@ static int launch_bwd_one(const BackwardArgs& a, cudaStream_t s) {
 }
 
 // Trainable materials keep FP32 latents (the pyramid is an Adam master).
+template <int H, bool ALB>
+static int bwd_dispatch_alb(const BackwardArgs& a, cudaStream_t s) {
+  if (a.target)
+    return a.shape.frame ? launch_bwd_one<H, true, false, true, ALB>(a, s)
+                         : launch_bwd_one<H, false, false, true, ALB>(a, s);
+  return a.shape.frame ? launch_bwd_one<H, true, false, false, ALB>(a, s)
+                       : launch_bwd_one<H, false, false, false, ALB>(a, s);
+}
+
 template <int H>
 static int bwd_dispatch(const BackwardArgs& a, cudaStream_t s) {
   if (a.pyr.f16) return (int)cudaErrorInvalidValue;
-  if (a.target)
-    return a.shape.frame ? launch_bwd_one<H, true, false, true>(a, s) : launch_bwd_one<H, false, false, true>(a, s);
-  return a.shape.frame ? launch_bwd_one<H, true, false, false>(a, s) : launch_bwd_one<H, false, false, false>(a, s);
+  if (a.shape.out == 6) {
+    if (a.target && !a.target_albedo) return (int)cudaErrorInvalidValue;
+    return bwd_dispatch_alb<H, true>(a, s);
+  }
+  return bwd_dispatch_alb<H, false>(a, s);
 }
 
 int launch_backward(const BackwardArgs& a, void* stream) {

@@ -85,8 +85,8 @@ struct TcLayout8 {
   static constexpr int B_SC = (B_LO + 16 * KP + 15) / 16 * 16;  // FP32: inv_s0, c0, c1, c2
   static constexpr int B_B1 = B_SC + 16;                  // FP32 b'_0 [H]
   static constexpr int B_B2 = B_B1 + H * 4;               // FP32 b'_1 [H]
-  static constexpr int B_B3 = B_B2 + H * 4;               // FP32 b_2 [4]
-  static constexpr int BLOB = B_B3 + 16;
+  static constexpr int B_B3 = B_B2 + H * 4;               // FP32 b_2 [8]: RGB, albedo head
+  static constexpr int BLOB = B_B3 + 32;
 };
 
 template <int H, int FK>
@@ -209,8 +209,8 @@ int pack_tc_blob(const Shape& s, int precision, const float* frame, const float*
   const float* b1 = W1 + IN * H;
   const float* W2 = b1 + H;              // [H][H] (then the third layer's, NH = 3)
   const float* b2 = W2 + H * H;
-  const float* W3 = b2 + H;              // [3][H] (NH = 2)
-  const float* b3 = W3 + 3 * H;
+  const float* W3 = b2 + H;              // [out][H] (NH = 2): RGB rows, then the albedo head's
+  const float* b3 = W3 + s.out * H;
   if (precision == NAM_PREC_FP8) {
     if (!act_scale) return -1;
     const int KP = H < 32 ? 32 : H;
@@ -219,7 +219,7 @@ int pack_tc_blob(const Shape& s, int precision, const float* frame, const float*
     float sw[3];
     quantize_layer_e4m3(W1, H, 14, out + b_l1, H, &sw[0]);
     quantize_layer_e4m3(W2, H, H, out + b_l2, H, &sw[1]);
-    quantize_layer_e4m3(W3, 3, H, out + b_lo, 16, &sw[2]);
+    quantize_layer_e4m3(W3, s.out, H, out + b_lo, 16, &sw[2]);
     const float inv0 = 1.0f / act_scale[0], inv1 = 1.0f / act_scale[1], inv2 = 1.0f / act_scale[2];
     put_f(out + b_sc, 0, inv0);
     put_f(out + b_sc, 1, (act_scale[0] * sw[0]) * inv1);
@@ -229,7 +229,7 @@ int pack_tc_blob(const Shape& s, int precision, const float* frame, const float*
       put_f(out + b_b1, n, b1[n] * inv1);
       put_f(out + b_b2, n, b2[n] * inv2);
     }
-    for (int n = 0; n < 3; ++n) put_f(out + b_b3, n, b3[n]);
+    for (int n = 0; n < s.out; ++n) put_f(out + b_b3, n, b3[n]);
     if (weight_scales_out)
       for (int l = 0; l < 3; ++l) weight_scales_out[l] = sw[l];
     return 0;
@@ -250,8 +250,8 @@ int pack_tc_blob(const Shape& s, int precision, const float* frame, const float*
     p = bh + H;
   }
   const float* Wo = p;
-  const float* bo = Wo + 3 * H;
-  for (int n = 0; n < 3; ++n) {
+  const float* bo = Wo + s.out * H;
+  for (int n = 0; n < s.out; ++n) {
     for (int k = 0; k < H; ++k) put_h(out + o.b_lo, 16, n, k, Wo[n * H + k]);
     put_h(out + o.b_lo, 16, n, H, bo[n]);
   }
@@ -723,6 +723,25 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
         y0 = fmaf(y0, c2, b3[0]);
         y1 = fmaf(y1, c2, b3[1]);
         y2 = fmaf(y2, c2, b3[2]);
+      }
+      if (L.albedo) {
+        // albedo head: output columns 3..5 (no cosine factor)
+        uint32_t acc2[4];
+        ptx::tmem_ld4(tDl + 4, acc2);
+        ptx::tmem_ld_wait();
+        float a0 = u2f(acc[3]), a1 = u2f(acc2[0]), a2 = u2f(acc2[1]);
+        if (P8) {
+          const float c2 = sc8[3];
+          const float* b3 = reinterpret_cast<const float*>(sW + Lay8::B_B3);
+          a0 = fmaf(a0, c2, b3[3]);
+          a1 = fmaf(a1, c2, b3[4]);
+          a2 = fmaf(a2, c2, b3[5]);
+        }
+        if (valid && row_mat == ci.mat) {
+          L.albedo[3 * i + 0] = a0;
+          L.albedo[3 * i + 1] = a1;
+          L.albedo[3 * i + 2] = a2;
+        }
       }
       if (cosine) {
         const float cz = fmaxf(qc.wiz, 0.0f);

@@ -41,6 +41,8 @@ struct Shape {
   int32_t frame;    // 0: none, 1: frame MLP 8 -> 16 -> 6 + Gram-Schmidt,
                     // 2: the paper's linear 8 -> 12, two frames
   int32_t in;       // decoder inputs: 14, or 20 with frame == 2
+  int32_t out;      // decoder outputs: 3 (RGB), or 6 with the albedo head
+                    // (RGB, then the directional albedo's RGB)
 };
 
 // Frame parameters per form: MLP 16*8 + 16 + 6*16 + 6, paper 12*8 + 12.
@@ -88,6 +90,8 @@ struct LaunchCommon {
   float* amax;           // FP32 kernel only: if set, max |input| of each decoder
                          // layer over the batch (atomic max, starts at 0);
                          // rgb may then be null
+  float* albedo;         // albedo head (shape.out == 6): if set, [n][3]
+                         // directional albedo of each query
 };
 
 // Resident blocks per SM of a kernel: the occupancy API, or (resources_only,
@@ -159,6 +163,11 @@ struct BackwardArgs {
   const float* target;
   float* loss_acc;
   float loss_inv;
+  // albedo head (shape.out == 6): with target set, target_albedo [n][3]
+  // holds one-sample estimates of the directional albedo and the loss adds
+  // loss_inv * sum of the squared albedo errors (L2); without target,
+  // grad_rgb is [n][6] (RGB, then albedo)
+  const float* target_albedo;
   // encoder phase (Sec. 5.1): when z_in is set the latent of query i is
   // z_in[8 i ..] (the texture is not read) and, when dz_out is set, dL/dz of
   // query i goes to dz_out[8 i ..] instead of the pyramid gradient

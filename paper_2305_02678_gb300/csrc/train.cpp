@@ -83,12 +83,17 @@ extern "C" nam_status nam_backward(nam_ctx* ctx, nam_material m, const nam_queri
   return NAM_OK;
 }
 
-extern "C" nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
-                                     int64_t n, const nam_adam* opt, float* loss_out, void* stream, uint32_t flags) {
+// The fused training step; target_albedo (albedo head only) [n][3].
+static nam_status train_step(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
+                             const float* target_albedo, int64_t n, const nam_adam* opt, float* loss_out,
+                             void* stream, uint32_t flags) {
   nam_status st = check_trainable(ctx, m);
   if (st) return st;
   if (n <= 0) return fail(NAM_ERR_INVALID_ARG, "n must be > 0");
   if (!target_rgb || !opt) return fail(NAM_ERR_INVALID_ARG, "NULL target or optimiser settings");
+  if (m->shape.out == 6 && !target_albedo)
+    return fail(NAM_ERR_UNSUPPORTED, "the material has the albedo head: nam_train_step_albedo trains it");
+  if (m->shape.out == 3 && target_albedo) return fail(NAM_ERR_UNSUPPORTED, "the material has no albedo head");
   if (opt->step < 1) return fail(NAM_ERR_INVALID_ARG, "Adam step is 1-based");
   st = check_queries(m, q);
   if (st) return st;
@@ -104,6 +109,7 @@ extern "C" nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_que
   const int64_t np = m->n_params, po = m->pyr_off, nt = m->pyr.texels * 8;
   fill_bwd(ctx, m, q, n, nullptr, m->grad, m->grad + po, flags, &a);
   a.target = target_rgb;
+  a.target_albedo = target_albedo;
   a.loss_acc = loss_acc;
   a.loss_inv = 1.0f / (float)(3 * n);
   if (!e) e = launch_backward(a, s);
@@ -120,6 +126,18 @@ extern "C" nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_que
     if (ce != cudaSuccess) return cuda_fail((int)ce, "nam_train_step: loss readback");
   }
   return NAM_OK;
+}
+
+extern "C" nam_status nam_train_step(nam_ctx* ctx, nam_material m, const nam_queries* q, const float* target_rgb,
+                                     int64_t n, const nam_adam* opt, float* loss_out, void* stream, uint32_t flags) {
+  return train_step(ctx, m, q, target_rgb, nullptr, n, opt, loss_out, stream, flags);
+}
+
+extern "C" nam_status nam_train_step_albedo(nam_ctx* ctx, nam_material m, const nam_queries* q,
+                                            const float* target_rgb, const float* target_albedo, int64_t n,
+                                            const nam_adam* opt, float* loss_out, void* stream, uint32_t flags) {
+  if (!target_albedo) return fail(NAM_ERR_INVALID_ARG, "nam_train_step_albedo: NULL albedo targets");
+  return train_step(ctx, m, q, target_rgb, target_albedo, n, opt, loss_out, stream, flags);
 }
 
 // ---------------------------------------------------------------------------

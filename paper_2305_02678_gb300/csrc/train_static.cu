@@ -59,6 +59,8 @@ extern "C" nam_status nam_train_step_noalloc(nam_ctx* ctx, nam_material m, const
   if (!m->desc.trainable) return fail(NAM_ERR_UNSUPPORTED, "nam_train_step_noalloc: material is not trainable");
   if (m->shape.NH != 2 || m->shape.frame == 2)
     return fail(NAM_ERR_UNSUPPORTED, "nam_train_step_noalloc: reverse mode supports the frame MLP form with two hidden layers");
+  if (m->shape.out != 3)
+    return fail(NAM_ERR_UNSUPPORTED, "nam_train_step_noalloc: the material has the albedo head (nam_train_step_albedo)");
   if (n <= 0) return fail(NAM_ERR_INVALID_ARG, "nam_train_step_noalloc: n must be > 0");
   if (n > kMaxQueries)
     return fail(NAM_ERR_INVALID_ARG, "nam_train_step_noalloc: batch of %lld queries exceeds the %lld the static buffer holds",
