@@ -890,26 +890,27 @@ def run_encoder_bootstrap(ctx, dev, stream, enc_steps, fine_steps, batch=131072,
                     "training step of the training leg"}
 
 
-def run_albedo_head(ctx, dev, stream, steps, batch=131072, pool=4, n_test=64):
+def run_albedo_head(ctx, dev, stream, steps, batch=131072, pool=4, n_test=64, W0=256, L=9):
     """The optional albedo head (the paper's albedo inference) on the training
-    workload's material: its 1024^2 x 8 pyramid (11 levels) and frame MLP, a
-    14-64-64-6 decoder (RGB, then the albedo), trained with
-    nam_train_step_albedo (log-L1 on the RGB plus the L2 albedo term against
-    one-sample estimates pi f(x, wi, wo), wi cosine-weighted) on uniform
-    queries; reports the step time and the head's mean |albedo - Eq. 2| at
-    n_test points (lod 0), the integral by a 96 x 96 midpoint rule."""
+    workload's procedural material: a W0^2 x 8 pyramid (L levels, N(0, 0.1)),
+    frame MLP 8-16-6 and a 14-64-64-6 decoder (RGB, then the albedo), trained
+    with nam_train_step_albedo (log-L1 on the RGB plus the L2 albedo term
+    against one-sample estimates pi f(x, wi, wo), wi cosine-weighted) on
+    uniform lod-0 queries, so that every finest texel sees some 2,000 noisy
+    albedo samples over 1,000 steps; reports the step time and the head's
+    mean |albedo - Eq. 2| at n_test lod-0 points, the integral by a 96 x 96
+    midpoint rule."""
     import torch
 
     import workloads as W
     from paper_2305_02678_gb300 import binding as B
-    w = W.workload(4)
-    m = w["model"]
-    target = w["target"]
+    target = W.workload(4, scale=1 / 262144)["target"]
     rng = W.rng_streams(W.SEEDS[4] + 31, 4)
-    dec = W.make_mlp(rng[0], (14, 64, 64, 6))
+    pyr = W.make_pyramid(rng[0], W0, W0, L, dtype=np.float32, std=0.1)
+    model = W.make_model(rng[0], (14, 64, 64, 6), (8, 16, 6))
     batches = []
     for _ in range(pool):
-        q = W.uniform_queries(rng[1], batch, 10.0)
+        q = W.uniform_queries(rng[1], batch, 0.0)
         batches.append(({k: torch.from_numpy(v).to(dev) for k, v in q.items()},
                         torch.from_numpy(W.target_rgb(target, q)).to(dev),
                         torch.from_numpy(W.albedo_targets(rng[2], target, q)).to(dev)))
@@ -924,8 +925,7 @@ def run_albedo_head(ctx, dev, stream, steps, batch=131072, pool=4, n_test=64):
         f = target(np.full(k * k, float(tq["u"][j])), np.full(k * k, float(tq["v"][j])), wi, wo)
         ref[j] = np.pi * f.mean(axis=0)
     dtq = {kk: torch.from_numpy(v).to(dev) for kk, v in tq.items()}
-    mat = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], dec, precision=B.NAM_PREC_F32,
-                       trainable=True)
+    mat = ctx.material(W0, W0, L, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_F32, trainable=True)
 
     def albedo_error():
         _, a = mat.eval_albedo(dtq, stream=stream)
@@ -938,8 +938,8 @@ def run_albedo_head(ctx, dev, stream, steps, batch=131072, pool=4, n_test=64):
         dq, y, ya = batches[s % pool]
         if s == 4:
             ev[0].record(stream)
-        l = B.nam_train_step_albedo(ctx.h, mat.h, dq, y, ya, batch, lr_params=1e-3, step=s, stream=stream,
-                                    want_loss=(s % 100 == 0 or s == 1 or s == steps))
+        l = B.nam_train_step_albedo(ctx.h, mat.h, dq, y, ya, batch, lr_params=3e-3, lr_pyramid=1e-2, step=s,
+                                    stream=stream, want_loss=(s % 100 == 0 or s == 1 or s == steps))
         if l is not None:
             losses.append(l)
     ev[1].record(stream)
@@ -948,7 +948,7 @@ def run_albedo_head(ctx, dev, stream, steps, batch=131072, pool=4, n_test=64):
     e1 = albedo_error()
     mat.destroy()
     ctx.check()
-    return {"workload": "albedo-head-1024sq-131072", "decoder": "14-64-64-6", "batch": batch, "steps": steps,
+    return {"workload": f"albedo-head-{W0}sq-{batch}-lod0", "decoder": "14-64-64-6", "batch": batch, "steps": steps,
             "ms_per_step": round(ms, 4), "samples_per_s": round(batch * 1e3 / ms, 1),
             "loss_every_100": [round(x, 5) for x in losses],
             "albedo_mean_abs_error": {"before": round(e0, 4), "after": round(e1, 4),
