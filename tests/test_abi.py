@@ -65,6 +65,9 @@ def test_struct_layouts_match_c(libnam, tmp_path):
         "nam_frame": libnam.nam_frame,
         "nam_frame_stats": libnam.nam_frame_stats,
         "nam_stats": libnam.nam_stats,
+        "nam_sphere": libnam.nam_sphere,
+        "nam_scene": libnam.nam_scene,
+        "nam_gbuffer": libnam.nam_gbuffer,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
     for name, cls in structs.items():
@@ -86,6 +89,35 @@ def test_struct_layouts_match_c(libnam, tmp_path):
         assert got[f"{name} size"] == C.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert got[f"{name}.{fname}"] == getattr(cls, fname).offset, f"{name}.{fname}"
+
+
+def _header_constants():
+    """Names of the #define and enum constants of nam.h (NAM_*)."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    names = set(re.findall(r"^#define\s+(NAM_[A-Z0-9_]+)\s+\S", src, flags=re.M))
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        names |= set(re.findall(r"\b(NAM_[A-Z0-9_]+)\s*=", body))
+    return sorted(names)
+
+
+def test_binding_constants_match_header(libnam, tmp_path):
+    """Every NAM_* constant the binding defines has the header's value (the
+    values printed by a C compiler, so that the header is read as C reads it)."""
+    names = [n for n in _header_constants() if hasattr(libnam, n)]
+    assert len(names) >= 30, names
+    lines = ["#include <stdio.h>", f'#include "{HEADER}"', "int main(void) {"]
+    for n in names:
+        lines.append(f'  printf("{n} %lld\\n", (long long)({n}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for line in out:
+        if line.strip():
+            k, v = line.rsplit(" ", 1)
+            assert getattr(libnam, k) == int(v), (k, getattr(libnam, k), v)
 
 
 def test_init_without_gpu_fails_cleanly(libnam):
