@@ -8,9 +8,10 @@
 //           chunk table of the tensor-core kernel (each material's range cut
 //           into 128-query chunks; empty slots have count 0);
 //   scatter each block reserves, per material, one run of slots for its
-//           segment (one global atomic per block and material) and writes
-//           each query's fields, read in the caller's order, to a slot of its
-//           run, with the slot's original index;
+//           segment (one global atomic per block and material), orders the
+//           indices of the segment's queries by material in shared memory
+//           and writes each run's fields, with the slots' original indices,
+//           to consecutive slots;
 //   unbin   the kernel's outputs, read in binned order, written back to the
 //           caller's order.
 // Inside a material's range, runs follow the order in which blocks reserve
@@ -120,12 +121,29 @@ struct Binned {
   float *u, *v, *lod, *xi, *wix, *wiy, *wiz, *wox, *woy, *woz;
 };
 
+// Scatter, ordered (segments of more than kDirectMaterials materials): the
+// indices of the segment's valid queries are first
+// placed in shared memory ordered by material (a local counting sort), then
+// each material's run is written to consecutive slots, its fields read from
+// the segment (consecutive for a segment of one material, L1-resident
+// otherwise), so that the global writes of a run are coalesced instead of
+// one sector per 4-byte field.
+// Shared memory: cnt, run, excl [nmat] each, then the query index and the
+// material of each local position [kSeg] each.
+constexpr int kStage = 1;
+constexpr int kDirectMaterials = 4;  // segments of at most this many materials skip the ordering
+
 __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, const int32_t* __restrict__ ids,
                                                                int64_t n, int nmat, uint32_t* __restrict__ cursors,
                                                                Binned out, int32_t* __restrict__ orig) {
   extern __shared__ uint32_t sh[];
-  uint32_t* cnt = sh;             // [nmat] this segment's queries per material
-  uint32_t* run = sh + nmat;      // [nmat] first slot of the segment's run
+  uint32_t* cnt = sh;               // [nmat] this segment's queries per material, then a bump counter
+  uint32_t* run = sh + nmat;        // [nmat] first slot of the segment's run
+  uint32_t* excl = sh + 2 * nmat;   // [nmat] first local position of each material
+  uint32_t* stage = sh + 3 * nmat;  // [kSeg] query index of each local position
+  int32_t* smat = reinterpret_cast<int32_t*>(stage + kStage * kSeg);  // [kSeg]
+  __shared__ uint32_t wsum[kThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t seg = (int64_t)blockIdx.x * kSeg;
   const int64_t end = seg + kSeg < n ? seg + kSeg : n;
   for (int m = threadIdx.x; m < nmat; m += blockDim.x) cnt[m] = 0;
@@ -138,18 +156,79 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, cons
     if (m >= 0) warp_bump(cnt, m, act);
   }
   __syncthreads();
+  // exclusive scan of cnt over the materials: each thread sums a contiguous
+  // block of entries, the block scans the thread sums
+  const int per = (nmat + kThreads - 1) / kThreads;
+  const int m0 = threadIdx.x * per, m1 = m0 + per < nmat ? m0 + per : nmat;
+  uint32_t mine = 0;
+  for (int m = m0; m < m1; ++m) mine += cnt[m];
+  uint32_t x = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  uint32_t before = x - mine;
+  for (int w = 0; w < warp; ++w) before += wsum[w];
+  for (int m = m0; m < m1; ++m) {
+    excl[m] = before;
+    before += cnt[m];
+  }
+  uint32_t total = 0;
+  for (int w = 0; w < kThreads / 32; ++w) total += wsum[w];
+  // a segment of a few materials is written directly below: each warp's
+  // lanes of one material already take consecutive slots; staging pays off
+  // only for many (threads whose materials are present, a lower bound on the
+  // segment's materials when a thread covers several)
+  bool present = false;
+  for (int m = m0; m < m1; ++m) present |= cnt[m] != 0;
+  const bool one = __syncthreads_count(present) <= kDirectMaterials;
   for (int m = threadIdx.x; m < nmat; m += blockDim.x) {
     run[m] = cnt[m] ? atomicAdd(cursors + m, cnt[m]) : 0u;
     cnt[m] = 0;
   }
   __syncthreads();
+  if (one) {
+    for (int64_t base = seg; base < end; base += blockDim.x) {
+      const int64_t i = base + threadIdx.x;
+      int m = i < end ? __ldg(ids + i) : -1;
+      if (m >= nmat) m = -1;
+      const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
+      if (m < 0) continue;
+      const uint32_t slot = run[m] + warp_bump(cnt, m, act);
+      out.u[slot] = __ldg(q.u + i);
+      out.v[slot] = __ldg(q.v + i);
+      out.lod[slot] = __ldg(q.lod + i);
+      if (q.xi) out.xi[slot] = __ldg(q.xi + i);
+      out.wix[slot] = __ldg(q.wix + i);
+      out.wiy[slot] = __ldg(q.wiy + i);
+      out.wiz[slot] = __ldg(q.wiz + i);
+      out.wox[slot] = __ldg(q.wox + i);
+      out.woy[slot] = __ldg(q.woy + i);
+      out.woz[slot] = __ldg(q.woz + i);
+      orig[slot] = (int32_t)i;
+    }
+    return;
+  }
+  // stage: local position = the material's first position + its bump
   for (int64_t base = seg; base < end; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;
     int m = i < end ? __ldg(ids + i) : -1;
     if (m >= nmat) m = -1;
     const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
     if (m < 0) continue;
-    const uint32_t slot = run[m] + warp_bump(cnt, m, act);
+    const uint32_t lp = excl[m] + warp_bump(cnt, m, act);
+    stage[lp] = (uint32_t)i;
+    smat[lp] = m;
+  }
+  __syncthreads();
+  // write: consecutive positions of one material go to consecutive slots
+  for (uint32_t p = threadIdx.x; p < total; p += blockDim.x) {
+    const int m = smat[p];
+    const int64_t i = stage[p];
+    const uint32_t slot = run[m] + (p - excl[m]);
     out.u[slot] = __ldg(q.u + i);
     out.v[slot] = __ldg(q.v + i);
     out.lod[slot] = __ldg(q.lod + i);
@@ -366,7 +445,13 @@ int launch_bin_eval(const BinArgs& a, void* stream) {
   const int gseg = (int)((n + kSeg - 1) / kSeg);
   bin_count_kernel<<<gseg, kThreads, a.nmat * sizeof(uint32_t), s>>>(a.ids, n, a.nmat, counts, a.L.err);
   bin_plan_kernel<<<1, 1024, 2 * (a.nmat + 1) * sizeof(uint32_t), s>>>(counts, a.nmat, cursors, chunks, maxc);
-  bin_scatter_kernel<<<gseg, kThreads, 2 * a.nmat * sizeof(uint32_t), s>>>(a.L.q, a.ids, n, a.nmat, cursors, b, orig);
+  const int scatter_smem = (3 * a.nmat + (kStage + 1) * kSeg) * (int)sizeof(uint32_t);
+  static std::atomic<uint64_t> scatter_attr{0};
+  once_per_device(scatter_attr, [] {
+    cudaFuncSetAttribute(bin_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (3 * NAM_MAX_BIN_MATERIALS + (kStage + 1) * kSeg) * (int)sizeof(uint32_t));
+  });
+  bin_scatter_kernel<<<gseg, kThreads, scatter_smem, s>>>(a.L.q, a.ids, n, a.nmat, cursors, b, orig);
   e = (int)cudaGetLastError();
   if (e) return e;
   LaunchCommon L = a.L;
