@@ -8,10 +8,12 @@
 //           chunk table of the tensor-core kernel (each material's range cut
 //           into 128-query chunks; empty slots have count 0);
 //   scatter each block reserves, per material, one run of slots for its
-//           segment (one global atomic per block and material), orders the
-//           indices of the segment's queries by material in shared memory
-//           and writes each run's fields, with the slots' original indices,
-//           to consecutive slots;
+//           segment (one global atomic per block and material) and writes
+//           each query's fields, with the slot's original index, to a slot
+//           of its run: directly at its warp's bump for a segment of a few
+//           materials, else after ordering the segment's query indices by
+//           material in shared memory, so that each run is written to
+//           consecutive slots;
 //   unbin   the kernel's outputs, read in binned order, written back to the
 //           caller's order.
 // Inside a material's range, runs follow the order in which blocks reserve
@@ -121,13 +123,13 @@ struct Binned {
   float *u, *v, *lod, *xi, *wix, *wiy, *wiz, *wox, *woy, *woz;
 };
 
-// Scatter, ordered (segments of more than kDirectMaterials materials): the
-// indices of the segment's valid queries are first
-// placed in shared memory ordered by material (a local counting sort), then
-// each material's run is written to consecutive slots, its fields read from
-// the segment (consecutive for a segment of one material, L1-resident
-// otherwise), so that the global writes of a run are coalesced instead of
-// one sector per 4-byte field.
+// Scatter.  A segment of at most kDirectMaterials materials writes each query
+// at its warp's bump (a warp's lanes of one material take consecutive
+// slots).  A segment of more is ordered first: the indices of its valid
+// queries are placed in shared memory by material (a local counting sort),
+// then each material's run is written to consecutive slots, its fields read
+// from the segment (L1-resident), so that the global writes of a run are
+// coalesced instead of one sector per 4-byte field.
 // Shared memory: cnt, run, excl [nmat] each, then the query index and the
 // material of each local position [kSeg] each.
 constexpr int kStage = 1;
