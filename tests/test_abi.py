@@ -127,3 +127,18 @@ def test_init_without_gpu_fails_cleanly(libnam):
     with pytest.raises(libnam.NamError) as e:
         libnam.nam_init(0)
     assert e.value.status in (libnam.NAM_ERR_CUDA, libnam.NAM_ERR_INVALID_ARG)
+
+
+def test_every_entry_point_refuses_null_arguments(libnam):
+    """Each entry point checks its context (and other pointers) before any
+    CUDA call: with every pointer NULL and every integer 0 it returns
+    NAM_ERR_INVALID_ARG and leaves a message, on a machine without a GPU."""
+    import ctypes as C
+    lib = libnam.lib()
+    for name in libnam.EXPORTS:
+        if name in ("nam_status_string", "nam_last_error_message", "nam_now"):
+            continue
+        f = getattr(lib, name)
+        st = f(*[None if t is C.c_void_p else 0 for t in f.argtypes])
+        assert st == libnam.NAM_ERR_INVALID_ARG, (name, st)
+        assert lib.nam_last_error_message().decode(), name
