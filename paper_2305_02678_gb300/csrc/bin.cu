@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(1024) select_scan_kernel(const int32_t* __rest
     __syncthreads();
     if (i < nb) block_offs[i] = carry + (warp ? wsum[warp - 1] : 0) + x - v;
     carry += wsum[31];
-    __syncthreads();  // wsum is rewritten by the next round
+    __syncthreads();  // wsum is rewritten by the next iteration
   }
   if (threadIdx.x == 0) {
     *total = carry;
