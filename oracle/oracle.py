@@ -324,15 +324,16 @@ def eval_alternatives(model: Model, q, gamma=2.0 ** -19, nthreads=None):
     return alts, nalt, nsites
 
 
-def parity(g, o, kappa, tol, kappa_well=50.0, c=64.0, unit=2.0 ** -24):
+def parity(g, o, kappa, tol, kappa_well=50.0, c=64.0, unit=2.0 ** -24, tau=None):
     """Element-wise parity with a conditioning-aware bound.
 
     rel_i = max_c |g - o| / max(|o|, tau), tau = RMS of o.  Queries whose
     frame condition number is at most kappa_well must meet `tol`; beyond it
     the bound is max(tol, c * kappa * unit), the growth of a
     finite-precision evaluation's rounding (unit roundoff `unit` of the
-    frame arithmetic) through an ill-conditioned frame.  Returns
-    (ok, stats)."""
+    frame arithmetic) through an ill-conditioned frame.  `tau` overrides the
+    RMS floor (a few queries cut from a larger batch keep that batch's
+    floor).  Returns (ok, stats)."""
     g = np.asarray(g, dtype=np.float64).reshape(-1, 3)
     alts = None
     if np.ndim(o) == 3:   # [n, k, 3] valid alternatives, nominal first
@@ -342,7 +343,9 @@ def parity(g, o, kappa, tol, kappa_well=50.0, c=64.0, unit=2.0 ** -24):
     kappa = np.asarray(kappa, dtype=np.float64)
     if o.size == 0:
         return True, {"max_rel": 0.0, "mean_rel": 0.0, "ill_conditioned": 0, "n": 0}
-    tau = max(float(np.sqrt(np.mean(o * o))), 1e-30)
+    if tau is None:
+        tau = float(np.sqrt(np.mean(o * o)))
+    tau = max(tau, 1e-30)
     den = np.maximum(np.abs(o), tau)
     if alts is None:
         rel = (np.abs(g - o) / den).max(axis=1)

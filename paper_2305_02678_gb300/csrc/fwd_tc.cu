@@ -105,8 +105,8 @@ static bool tc_supported(const Shape& s, int precision) {
 }
 
 size_t tc_blob_bytes(const Shape& s, int precision) {
+  if (precision == NAM_PREC_F16) return f16_blob_bytes(s);
   if (!tc_supported(s, precision)) return 0;
-  if (precision == NAM_PREC_F16) return (size_t)tc_off(s.H, s.frame, s.NH).blob;
   const bool f = s.frame == 1;
   if (s.H == 16) return f ? blob8_bytes<16, 1>() : blob8_bytes<16, 0>();
   if (s.H == 32) return f ? blob8_bytes<32, 1>() : blob8_bytes<32, 0>();
@@ -178,7 +178,8 @@ static void put_f(uint8_t* base, int idx, float v) { std::memcpy(base + 4 * idx,
 // out as TcLayout8 describes.
 int pack_tc_blob(const Shape& s, int precision, const float* frame, const float* dec, const float* act_scale,
                  uint8_t* out, float* weight_scales_out) {
-  if (precision != NAM_PREC_F16 && precision != NAM_PREC_FP8) return -1;
+  if (precision == NAM_PREC_F16) return pack_f16_blob(s, frame, dec, out);
+  if (precision != NAM_PREC_FP8) return -1;
   const size_t bytes = tc_blob_bytes(s, precision);
   if (!bytes) return -1;
   std::memset(out, 0, bytes);
@@ -811,16 +812,11 @@ static int tc_dispatch(const LaunchCommon& L, cudaStream_t s) {
 
 int launch_eval_tc(const LaunchCommon& L, int precision, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
+  if (precision == NAM_PREC_F16) return launch_eval_f16(L, stream);
   if (!tc_supported(L.shape, precision)) return (int)cudaErrorInvalidValue;
-  if (precision == NAM_PREC_FP8) {
-    if (L.shape.H == 16) return tc_dispatch<16, 2, true>(L, s);
-    if (L.shape.H == 32) return tc_dispatch<32, 2, true>(L, s);
-    return tc_dispatch<64, 2, true>(L, s);
-  }
-  if (L.shape.NH == 3) return tc_dispatch<64, 3, false>(L, s);
-  if (L.shape.H == 16) return tc_dispatch<16, 2, false>(L, s);
-  if (L.shape.H == 32) return tc_dispatch<32, 2, false>(L, s);
-  return tc_dispatch<64, 2, false>(L, s);
+  if (L.shape.H == 16) return tc_dispatch<16, 2, true>(L, s);
+  if (L.shape.H == 32) return tc_dispatch<32, 2, true>(L, s);
+  return tc_dispatch<64, 2, true>(L, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -14,6 +14,9 @@ enum DevError : int {
   DEVERR_NONE = 0,
   DEVERR_WAIT_TIMEOUT = 1,  // a bounded mbarrier wait ran out
   DEVERR_BOUNDS = 2,        // an index failed a device-side check
+  DEVERR_DRAIN_TIMEOUT = 3, // after a wait gave up, the kernel's own MMAs or
+                            // copies did not complete within the drain limit;
+                            // its TMEM was left allocated
 };
 
 // Latent pyramid geometry, passed by value to kernels.
@@ -116,6 +119,10 @@ inline void once_per_device(std::atomic<uint64_t>& done, F fn) {
 }
 
 int launch_eval_f32(const LaunchCommon& L, void* stream);
+// FP16 tensor-core evaluation (every shape with a tensor-core kernel)
+int launch_eval_f16(const LaunchCommon& L, void* stream);
+size_t f16_blob_bytes(const Shape& s);
+int pack_f16_blob(const Shape& s, const float* frame, const float* dec, uint8_t* out);
 int launch_eval_tc(const LaunchCommon& L, int precision, void* stream);
 
 // Weight blob sizes and packing (host side).

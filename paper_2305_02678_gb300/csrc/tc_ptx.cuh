@@ -46,15 +46,24 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parit
   return ok != 0;
 }
 // Wait for the phase of `bar` with the given parity to complete, for at most
-// timeout_ns of wall time.  Returns false if the limit was reached.
+// timeout_ns of wall time.  Returns false if the limit was reached.  Each
+// try_wait may suspend the thread for a hardware-defined time until the phase
+// completes; the clock is read only every 8 probes after the first miss (a
+// limit shorter than the operation waited for still runs out: the first miss
+// starts the clock).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t timeout_ns) {
-  if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
-  for (;;) {
-    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
-    if (globaltimer() - t0 > timeout_ns) return false;
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 7) == 0 && globaltimer() - t0 > timeout_ns) return false;
   }
 }
+// Limit of the teardown waits for a kernel's own copies and MMAs still in
+// flight after a steady-state wait gave up: fixed and generous, independent of
+// the caller's limit, so that a kernel never frees TMEM or exits under a live
+// MMA or bulk copy unless the GPU itself has stopped making progress.
+constexpr uint64_t kDrainTimeoutNs = 4000000000ull;
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
@@ -99,6 +108,14 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t
   d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
   d |= (uint64_t)1 << 46;  // descriptor version for the sm_100 family
   return d;                // base offset 0, swizzle none
+}
+
+// The same descriptor built as base + constant: `base` = sdesc(saddr, 0,
+// sbo) computed once; sdesc_at(base, off, lbo) = sdesc(saddr + off, lbo, sbo)
+// as long as (saddr + off) >> 4 stays below 2^14 (shared memory < 256 KB), so
+// that the address field never carries into the LBO field.
+__device__ __forceinline__ uint64_t sdesc_at(uint64_t base, uint32_t off, uint32_t lbo) {
+  return base + (uint64_t)((off >> 4) | ((lbo >> 4) << 16));
 }
 
 // Instruction descriptor, kind::f16 with FP16 A/B, FP32 D, both K-major.
@@ -217,6 +234,35 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
   unsigned long long rd;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
   return *reinterpret_cast<float2*>(&rd);
+}
+// d = a - b on pairs of FP32 values (one packed instruction).
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  unsigned long long ra = *reinterpret_cast<unsigned long long*>(&a);
+  unsigned long long rb = *reinterpret_cast<unsigned long long*>(&b);
+  unsigned long long rd;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(rd) : "l"(ra), "l"(rb));
+  return *reinterpret_cast<float2*>(&rd);
+}
+// 16-byte global -> shared copy through L1 (cp.async, completes into the
+// issuing thread's current group); src_size < 16 fills the rest with zeros
+// (0: nothing is read).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_size) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_size) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+// Read-only global load that the compiler keeps where it is written (the
+// value's first use waits on it, wherever that is).
+__device__ __forceinline__ float ld_nc_pinned(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr)
+               : "memory");
+  return v;
 }
 // Two FP32 values -> packed E4M3 pair in the low 16 bits (first value in the
 // low byte), round to nearest even, saturating.

@@ -1,21 +1,17 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
 Tolerances (max over queries and channels of |g - o| / max(|o|, tau), tau the
-RMS of the oracle's outputs):
-  FP32 path        1e-5 against the oracle with the same FP32 parameters;
-  FP16 path        2e-3 against the oracle evaluating the same FP16
-                   parameters with the same FP16 rounding of the decoder's
-                   MMA operands (what FP16 inference computes).  Where the
-                   exact value of a rounded operand lies within FP32
-                   accumulation error of a rounding midpoint, either FP16
-                   neighbour is a correct result: the oracle lists those
-                   results (nominal first) and the GPU must match one.  The
-                   error against the unrounded oracle is reported.
+RMS of the oracle's outputs), both against the oracle with the same parameter
+values (FP32 masters, or the FP16-rounded weights of Sec. 5.2's quantisation)
+and FP64 activations:
+  FP32 path        1e-5;
+  FP16 path        2e-3.
 Both bounds hold for every query whose frame step is well conditioned
 (condition number kappa <= 50, ~99.8% of the 1080p workload's queries).  The
 rest, where the decoded normal and tangent are nearly parallel or nearly
 cancel, are checked against max(tol, 64 kappa 2^-24): the frame is computed
-at FP32 accuracy, and rounding at that level grows with kappa there.
+at FP32 accuracy, and a relative error e of its raw outputs moves the frame
+by up to (1 + 2 kappa) e.
 """
 import numpy as np
 import pytest
@@ -62,25 +58,19 @@ def _eval(ctx, w, precision, q=None, filt=0, addr=0, flags=0, pyramid=None):
     return res
 
 
-def _oracle(oracle, w, q=None, params="master", act_round=0, filt=0, addr=0, cos=False, pyramid=None,
-            with_kappa=False):
+def _oracle(oracle, w, q=None, params="master", filt=0, addr=0, cos=False, pyramid=None, with_kappa=False):
     m = w["model"]
     om = oracle.Model(w["W0"], w["H0"], w["L"], w["pyramid"] if pyramid is None else pyramid, m["frame"],
-                      m["decoder"], filter=filt, address=addr, out_cosine=cos, params=params, act_round=act_round)
+                      m["decoder"], filter=filt, address=addr, out_cosine=cos, params=params)
     q = w["queries"] if q is None else q
-    if act_round:
-        # every valid FP16 result: nominal rounding plus the roundings that
-        # FP32 accumulation may take the other way near a midpoint
-        o = oracle.eval_alternatives(om, q)[0]
-    else:
-        o = oracle.eval(om, q)
+    o = oracle.eval(om, q)
     if with_kappa:
         return o, oracle.frame_condition(om, q)
     return o
 
 
-def _check(oracle, g, o, kappa, tol, label):
-    ok, st = oracle.parity(g, o, kappa, tol)
+def _check(oracle, g, o, kappa, tol, label, tau=None):
+    ok, st = oracle.parity(g, o, kappa, tol, tau=tau)
     print(f"{label}: max {st['max_rel']:.3e} (well-conditioned {st['max_rel_well_conditioned']:.3e}), "
           f"mean {st['mean_rel']:.3e}, ill-conditioned {st['ill_conditioned']}/{st['n']}, "
           f"worst/bound {st['worst_over_bound']:.3f}, by kappa {st['by_kappa']}")
@@ -113,14 +103,9 @@ def test_fp16_1080p_full(gctx, oracle, w2):
     FP16 pyramid, frame MLP 8-16-6, decoder 14-64-64-3."""
     from paper_2305_02678_gb300 import binding as B
     g = _eval(gctx, w2, B.NAM_PREC_F16)
-    emu, kappa = _oracle(oracle, w2, params="fp16", act_round=oracle.ROUND_FP16, with_kappa=True)
-    _check(oracle, g, emu, kappa, TOL_F16, "fp16 1080p vs fp16-operand oracle")
-    exact = _oracle(oracle, w2, params="fp16")
-    err_exact = oracle.relative_error(g, exact)
-    err_nominal = oracle.relative_error(g, emu[:, 0])
-    print(f"fp16 1080p vs nominal fp16-operand oracle only: max {err_nominal[0]:.3e}")
-    print(f"fp16 1080p vs unrounded oracle: max {err_exact[0]:.3e} mean {err_exact[1]:.3e}")
-    assert err_exact[1] <= 2e-3
+    o, kappa = _oracle(oracle, w2, params="fp16", with_kappa=True)
+    st = _check(oracle, g, o, kappa, TOL_F16, "fp16 1080p vs oracle (FP16 weights, FP64 activations)")
+    assert st["max_rel_well_conditioned"] <= TOL_F16
 
 
 @pytest.mark.parametrize("filt", [0, 1])
@@ -128,7 +113,7 @@ def test_fp16_1080p_full(gctx, oracle, w2):
 def test_fp16_filters_and_addressing(gctx, oracle, w2_small, filt, addr):
     from paper_2305_02678_gb300 import binding as B
     g = _eval(gctx, w2_small, B.NAM_PREC_F16, filt=filt, addr=addr)
-    o, kappa = _oracle(oracle, w2_small, params="fp16", act_round=oracle.ROUND_FP16, filt=filt, addr=addr,
+    o, kappa = _oracle(oracle, w2_small, params="fp16", filt=filt, addr=addr,
                        with_kappa=True)
     _check(oracle, g, o, kappa, TOL_F16, f"fp16 filt={filt} addr={addr}")
 
@@ -147,7 +132,7 @@ def test_fp16_shapes(gctx, oracle, H, frame, latent):
     q = W.uniform_queries(rng[2], 20000, 7.5)
     w = dict(W0=W0, H0=H0, L=L, pyramid=pyr, model=model, queries=q)
     g = _eval(gctx, w, B.NAM_PREC_F16)
-    o, kappa = _oracle(oracle, w, params="fp16", act_round=oracle.ROUND_FP16, with_kappa=True)
+    o, kappa = _oracle(oracle, w, params="fp16", with_kappa=True)
     _check(oracle, g, o, kappa, TOL_F16, f"fp16 H={H} frame={frame} latent={latent}")
 
 
@@ -159,9 +144,14 @@ def test_ragged_sizes(gctx, oracle, w2_small, n, precision):
     assert g.shape == (n, 3)
     if n == 0:
         return
-    kw = dict(params="fp16", act_round=oracle.ROUND_FP16) if precision == 1 else {}
+    kw = dict(params="fp16") if precision == 1 else {}
     o, kappa = _oracle(oracle, w2_small, q=q, with_kappa=True, **kw)
-    _check(oracle, g, o, kappa, TOL_F16 if precision == 1 else TOL_F32, f"n={n} precision={precision}")
+    # the error floor tau of the 4,097-query batch these queries are cut from
+    # (the RMS of one query's own three outputs would grade a lone query more
+    # strictly than the same query inside any larger batch)
+    o_ref = _oracle(oracle, w2_small, q=W.slice_queries(w2_small["queries"], 5, 4097), **kw)
+    _check(oracle, g, o, kappa, TOL_F16 if precision == 1 else TOL_F32, f"n={n} precision={precision}",
+           tau=float(np.sqrt(np.mean(o_ref * o_ref))))
 
 
 def _edge_queries(W0, L):
@@ -206,7 +196,7 @@ def test_edge_coordinates(gctx, oracle, filt, addr, precision):
     q = _edge_queries(W0, L)
     w = dict(W0=W0, H0=H0, L=L, pyramid=pyr, model=model, queries=q)
     g = _eval(gctx, w, precision, filt=filt, addr=addr)
-    kw = dict(params="fp16", act_round=oracle.ROUND_FP16) if precision == 1 else {}
+    kw = dict(params="fp16") if precision == 1 else {}
     o, kappa = _oracle(oracle, w, filt=filt, addr=addr, with_kappa=True, **kw)
     assert np.isfinite(g).all()
     _check(oracle, g, o, kappa, TOL_F16 if precision == 1 else TOL_F32, f"edges filt={filt} addr={addr}")
