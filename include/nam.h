@@ -606,21 +606,6 @@ enum {
 };
 nam_status nam_inject_fault(nam_ctx* ctx, int32_t fault);
 
-/* ------------------------------------------------------------------------ */
-/* diagnostics                                                              */
-/* ------------------------------------------------------------------------ */
-/* One tensor-core MMA in isolation: D[128][64] = A[128][32] B[64][32]^T with
- * binary16 operands given (host) in the kernels' canonical K-major layout
- * (element (r, k) of an R-row operand at byte (k/8)*R*16 + r*16 + (k%8)*2),
- * FP32 result (host, row-major).  Checks the descriptor and TMEM conventions
- * the evaluation kernels rely on.  Synchronous. */
-nam_status nam_debug_mma_selftest(nam_ctx* ctx, const uint16_t* A_host, const uint16_t* B_host, float* D_host);
-/* The same product with the A operand read from tensor memory: A_rows_host
- * is A row-major ([128][32] binary16), stored two elements per 32-bit TMEM
- * column by the kernel; B as above. */
-nam_status nam_debug_mma_selftest_ts(nam_ctx* ctx, const uint16_t* A_rows_host, const uint16_t* B_host,
-                                     float* D_host);
-
 #ifdef __cplusplus
 }
 #endif

@@ -126,8 +126,7 @@ EXPORTS = ("nam_status_string", "nam_last_error_message", "nam_init", "nam_shutd
            "nam_train_step_encoded", "nam_material_encoder", "nam_scene_gbuffer", "nam_scene_render_direct",
            "nam_scene_render_paths",
            "nam_now",
-           "nam_submit", "nam_poll", "nam_wait", "nam_cancel", "nam_get_stats", "nam_inject_fault",
-           "nam_debug_mma_selftest", "nam_debug_mma_selftest_ts")
+           "nam_submit", "nam_poll", "nam_wait", "nam_cancel", "nam_get_stats", "nam_inject_fault")
 
 
 class NamError(RuntimeError):
@@ -179,8 +178,6 @@ def _load():
         "nam_cancel": (i32, [p, u64]),
         "nam_get_stats": (i32, [p, p]),
         "nam_inject_fault": (i32, [p, i32]),
-        "nam_debug_mma_selftest": (i32, [p, p, p, p]),
-        "nam_debug_mma_selftest_ts": (i32, [p, p, p, p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -492,20 +489,3 @@ def nam_get_stats(ctx) -> nam_stats:
 def nam_inject_fault(ctx, fault):
     _check(_lib.nam_inject_fault(ctx, fault), "nam_inject_fault")
 
-
-def nam_debug_mma_selftest(ctx, A_bits: np.ndarray, B_bits: np.ndarray) -> np.ndarray:
-    A = np.ascontiguousarray(A_bits, dtype=np.uint16)
-    B = np.ascontiguousarray(B_bits, dtype=np.uint16)
-    assert A.nbytes == 8192 and B.nbytes == 4096
-    D = np.zeros((128, 64), dtype=np.float32)
-    _check(_lib.nam_debug_mma_selftest(ctx, ptr(A), ptr(B), ptr(D)), "nam_debug_mma_selftest")
-    return D
-
-
-def nam_debug_mma_selftest_ts(ctx, A_rows_bits: np.ndarray, B_bits: np.ndarray) -> np.ndarray:
-    A = np.ascontiguousarray(A_rows_bits, dtype=np.uint16)
-    B = np.ascontiguousarray(B_bits, dtype=np.uint16)
-    assert A.nbytes == 8192 and B.nbytes == 4096
-    D = np.zeros((128, 64), dtype=np.float32)
-    _check(_lib.nam_debug_mma_selftest_ts(ctx, ptr(A), ptr(B), ptr(D)), "nam_debug_mma_selftest_ts")
-    return D

@@ -19,9 +19,6 @@
 #include "nam_ctx.h"
 
 namespace nam {
-int launch_mma_selftest(const uint8_t* A, const uint8_t* B, float* D, uint64_t timeout_ns, int* err, void* stream);
-int launch_mma_selftest_ts(const uint16_t* A, const uint8_t* B, float* D, uint64_t timeout_ns, int* err,
-                           void* stream);
 }
 
 using namespace nam;
@@ -213,6 +210,8 @@ extern "C" nam_status nam_check_device_error(nam_ctx* ctx) {
   cudaMemcpy(&code, ctx->err_word, sizeof(int), cudaMemcpyDeviceToHost);
   cudaMemset(ctx->err_word, 0, sizeof(int));
   if (code == DEVERR_WAIT_TIMEOUT) return fail(NAM_ERR_TIMEOUT, "a device-side wait ran past its limit");
+  if (code == DEVERR_DRAIN_TIMEOUT)
+    return fail(NAM_ERR_TIMEOUT, "a kernel's own MMAs or copies did not complete within the drain limit");
   if (code) return fail(NAM_ERR_DEVICE_ASSERT, "device-side check failed (code %d)", code);
   return NAM_OK;
 }
@@ -866,48 +865,4 @@ extern "C" nam_status nam_eval_select(nam_ctx* ctx, const nam_material* mats, in
   return NAM_OK;
 }
 
-// ---------------------------------------------------------------------------
-// diagnostics
-// ---------------------------------------------------------------------------
-extern "C" nam_status nam_debug_mma_selftest_ts(nam_ctx* ctx, const uint16_t* A_rows_host,
-                                                const uint16_t* B_host, float* D_host) {
-  if (!ctx || !A_rows_host || !B_host || !D_host) return fail(NAM_ERR_INVALID_ARG, "NULL argument");
-  DeviceGuard g(ctx->device);
-  void *A = nullptr, *B = nullptr, *D = nullptr;
-  cudaMalloc(&A, 8192);
-  cudaMalloc(&B, 4096);
-  cudaMalloc(&D, 128 * 64 * 4);
-  cudaMemcpy(A, A_rows_host, 8192, cudaMemcpyHostToDevice);
-  cudaMemcpy(B, B_host, 4096, cudaMemcpyHostToDevice);
-  cudaMemset(D, 0, 128 * 64 * 4);
-  int e = launch_mma_selftest_ts((const uint16_t*)A, (const uint8_t*)B, (float*)D, ctx->timeout_ns, ctx->err_word,
-                                 nullptr);
-  if (!e) e = (int)cudaDeviceSynchronize();
-  if (!e) e = (int)cudaMemcpy(D_host, D, 128 * 64 * 4, cudaMemcpyDeviceToHost);
-  cudaFree(A);
-  cudaFree(B);
-  cudaFree(D);
-  if (e) return cuda_fail(e, "nam_debug_mma_selftest_ts");
-  return nam_check_device_error(ctx);
-}
 
-extern "C" nam_status nam_debug_mma_selftest(nam_ctx* ctx, const uint16_t* A_host, const uint16_t* B_host,
-                                             float* D_host) {
-  if (!ctx || !A_host || !B_host || !D_host) return fail(NAM_ERR_INVALID_ARG, "NULL argument");
-  DeviceGuard g(ctx->device);
-  void *A = nullptr, *B = nullptr, *D = nullptr;
-  cudaMalloc(&A, 8192);
-  cudaMalloc(&B, 4096);
-  cudaMalloc(&D, 128 * 64 * 4);
-  cudaMemcpy(A, A_host, 8192, cudaMemcpyHostToDevice);
-  cudaMemcpy(B, B_host, 4096, cudaMemcpyHostToDevice);
-  cudaMemset(D, 0, 128 * 64 * 4);
-  int e = launch_mma_selftest((const uint8_t*)A, (const uint8_t*)B, (float*)D, ctx->timeout_ns, ctx->err_word, nullptr);
-  if (!e) e = (int)cudaDeviceSynchronize();
-  if (!e) e = (int)cudaMemcpy(D_host, D, 128 * 64 * 4, cudaMemcpyDeviceToHost);
-  cudaFree(A);
-  cudaFree(B);
-  cudaFree(D);
-  if (e) return cuda_fail(e, "nam_debug_mma_selftest");
-  return nam_check_device_error(ctx);
-}

@@ -759,15 +759,20 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_tc_kernel(const LaunchCommo
     qc = qn;
   }
 
-  // ---- teardown: wait (bounded) for copies / MMAs still in flight ----------
+  // ---- teardown -------------------------------------------------------------
+  // MMAs and bulk copies still in flight after a wait gave up are waited for
+  // with the fixed drain limit (not the caller's), and TMEM is freed only if
+  // they all completed.
+  bool drained = true;
   if (r == 0) {
-    if (mma_pending) ptx::mbar_wait(bar_m, ph_m ^ 1, L.timeout_ns);
-    if (w_pending) ptx::mbar_wait(bar_w, ph_w ^ 1, L.timeout_ns);
+    if (mma_pending) drained &= ptx::mbar_wait(bar_m, ph_m ^ 1, ptx::kDrainTimeoutNs);
+    if (w_pending) drained &= ptx::mbar_wait(bar_w, ph_w ^ 1, ptx::kDrainTimeoutNs);
     if (bad) record_error(L.err, DEVERR_WAIT_TIMEOUT);
+    if (!drained) record_error(L.err, DEVERR_DRAIN_TIMEOUT);
   }
   ptx::tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
+  const bool all_drained = __syncthreads_and(drained ? 1 : 0) != 0;
+  if (warp == 0 && all_drained) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, 512);
   }
@@ -817,137 +822,6 @@ int launch_eval_tc(const LaunchCommon& L, int precision, void* stream) {
   if (L.shape.H == 16) return tc_dispatch<16, 2, true>(L, s);
   if (L.shape.H == 32) return tc_dispatch<32, 2, true>(L, s);
   return tc_dispatch<64, 2, true>(L, s);
-}
-
-// ---------------------------------------------------------------------------
-// single-MMA self test: D[128][N] = A[128][K] * B[N][K]^T with FP16 operands
-// given in the canonical K-major layout (K = 32: two K steps), used by the
-// tests to check descriptor and TMEM conventions in isolation.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) mma_selftest_kernel(const uint8_t* A, const uint8_t* B, float* D,
-                                                           uint64_t timeout_ns, int* err) {
-  // A: 128 x 32 fp16 = 8 KB, B: 64 x 32 fp16 = 4 KB; the regions are sized
-  // 32 KB and 16 KB so that every address a descriptor can form stays inside.
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + 32768;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 32768 + 16384);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  for (int k = tid; k < 8192 / 16; k += 128) reinterpret_cast<uint4*>(sA)[k] = reinterpret_cast<const uint4*>(A)[k];
-  for (int k = tid; k < 4096 / 16; k += 128) reinterpret_cast<uint4*>(sB)[k] = reinterpret_cast<const uint4*>(B)[k];
-  const uint32_t b = ptx::smem_u32(bar);
-  if (tid == 0) {
-    ptx::mbar_init(b, 1);
-    ptx::fence_mbar_init();
-  }
-  if (warp == 0) {
-    ptx::tmem_alloc(ptx::smem_u32(tslot), 64);
-    ptx::tmem_relinquish();
-  }
-  ptx::fence_proxy_async();
-  ptx::tc_fence_before();
-  __syncthreads();
-  ptx::tc_fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t aA = ptx::smem_u32(sA), aB = ptx::smem_u32(sB);
-  if (tid == 0) {
-    constexpr uint32_t id = ptx::idesc_f16(128, 64);
-    ptx::mma_f16(tmem, ptx::sdesc(aA, 2048, 128), ptx::sdesc(aB, 64 * 16, 128), id, 0);
-    ptx::mma_f16(tmem, ptx::sdesc(aA + 4096, 2048, 128), ptx::sdesc(aB + 2 * 64 * 16, 64 * 16, 128), id, 1);
-    ptx::mma_commit(b);
-  }
-  bool ok = ptx::mbar_wait(b, 0, timeout_ns);
-  if (!ok && tid == 0) record_error(err, DEVERR_WAIT_TIMEOUT);
-  ptx::tc_fence_after();
-  if (ok) {
-    uint32_t acc[32];
-    for (int c0 = 0; c0 < 64; c0 += 32) {
-      ptx::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, acc);
-      ptx::tmem_ld_wait();
-      for (int j = 0; j < 32; ++j) D[tid * 64 + c0 + j] = u2f(acc[j]);
-    }
-  }
-  ptx::tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, 64);
-  }
-}
-
-// Same product with A taken from TMEM: thread r stores row r of A (two fp16
-// per 32-bit column, element 2j in the low half of column j) with
-// tcgen05.st, and two K=16 MMAs read it at columns +0 and +8.
-__global__ void __launch_bounds__(128) mma_selftest_ts_kernel(const uint16_t* A, const uint8_t* B, float* D,
-                                                              uint64_t timeout_ns, int* err) {
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* sB = smem;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 16384);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  for (int k = tid; k < 4096 / 16; k += 128) reinterpret_cast<uint4*>(sB)[k] = reinterpret_cast<const uint4*>(B)[k];
-  const uint32_t b = ptx::smem_u32(bar);
-  if (tid == 0) {
-    ptx::mbar_init(b, 1);
-    ptx::fence_mbar_init();
-  }
-  if (warp == 0) {
-    ptx::tmem_alloc(ptx::smem_u32(tslot), 128);
-    ptx::tmem_relinquish();
-  }
-  ptx::fence_proxy_async();
-  ptx::tc_fence_before();
-  __syncthreads();
-  ptx::tc_fence_after();
-  const uint32_t tmem = *tslot;
-  const uint32_t lane = (uint32_t)(warp * 32) << 16;
-  uint32_t row[16];
-  for (int j = 0; j < 16; ++j) row[j] = (uint32_t)A[tid * 32 + 2 * j] | ((uint32_t)A[tid * 32 + 2 * j + 1] << 16);
-  ptx::tmem_st16(tmem + lane + 64, row);
-  ptx::tmem_st_wait();
-  ptx::tc_fence_before();
-  __syncthreads();
-  const uint32_t aB = ptx::smem_u32(sB);
-  if (tid == 0) {
-    ptx::tc_fence_after();
-    constexpr uint32_t id = ptx::idesc_f16(128, 64);
-    ptx::mma_f16_ts(tmem, tmem + 64, ptx::sdesc(aB, 64 * 16, 128), id, 0);
-    ptx::mma_f16_ts(tmem, tmem + 64 + 8, ptx::sdesc(aB + 2 * 64 * 16, 64 * 16, 128), id, 1);
-    ptx::mma_commit(b);
-  }
-  bool ok = ptx::mbar_wait(b, 0, timeout_ns);
-  if (!ok && tid == 0) record_error(err, DEVERR_WAIT_TIMEOUT);
-  ptx::tc_fence_after();
-  if (ok) {
-    uint32_t acc[32];
-    for (int c0 = 0; c0 < 64; c0 += 32) {
-      ptx::tmem_ld32(tmem + lane + c0, acc);
-      ptx::tmem_ld_wait();
-      for (int j = 0; j < 32; ++j) D[tid * 64 + c0 + j] = u2f(acc[j]);
-    }
-  }
-  ptx::tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, 128);
-  }
-}
-
-int launch_mma_selftest_ts(const uint16_t* A, const uint8_t* B, float* D, uint64_t timeout_ns, int* err,
-                           void* stream) {
-  const int smem = 16384 + 64;
-  mma_selftest_ts_kernel<<<1, 128, smem, (cudaStream_t)stream>>>(A, B, D, timeout_ns, err);
-  return (int)cudaGetLastError();
-}
-
-int launch_mma_selftest(const uint8_t* A, const uint8_t* B, float* D, uint64_t timeout_ns, int* err,
-                        void* stream) {
-  const int smem = 32768 + 16384 + 64;
-  cudaFuncSetAttribute(mma_selftest_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  mma_selftest_kernel<<<1, 128, smem, (cudaStream_t)stream>>>(A, B, D, timeout_ns, err);
-  return (int)cudaGetLastError();
 }
 
 }  // namespace nam

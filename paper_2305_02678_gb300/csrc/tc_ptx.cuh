@@ -46,14 +46,21 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parit
   return ok != 0;
 }
 // Wait for the phase of `bar` with the given parity to complete, for at most
-// timeout_ns of wall time.  Returns false if the limit was reached.  Each
+// timeout_ns of wall time.  Returns false if the limit was reached.  A plain
 // try_wait may suspend the thread for a hardware-defined time until the phase
-// completes; the clock is read only every 8 probes after the first miss (a
-// limit shorter than the operation waited for still runs out: the first miss
+// completes; with such waits the clock is read only every 8 probes.  A limit
+// below 100 us probes with a suspend hint no longer than the limit, so that a
+// limit shorter than the operation waited for does run out (the first miss
 // starts the clock).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t timeout_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
+  if (timeout_ns < 100000u) {
+    for (;;) {
+      if (mbar_try_wait_sleep(bar, parity, (uint32_t)timeout_ns)) return true;
+      if (globaltimer() - t0 > timeout_ns) return false;
+    }
+  }
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 7) == 0 && globaltimer() - t0 > timeout_ns) return false;

@@ -1,8 +1,8 @@
 """nam_train_step_noalloc: the training step for callers that may not
 allocate device memory (its per-batch buffers live in the library's static
 device array).  It must give what nam_train_step gives: two identical
-trainable materials, two steps in a row on the same batches, one through each
-entry point.  Collected last on purpose (file name), and independent of every
+trainable materials, steps in a row on the same batches (the last one at the
+largest batch the static array holds), one through each entry point.  Collected last on purpose (file name), and independent of every
 other test's state, so it passes alone in a fresh process and after the rest."""
 import numpy as np
 import pytest
@@ -33,8 +33,9 @@ def test_noalloc_training_step_matches_allocating_step():
         ref = ctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_F32, trainable=True)
         nal = ctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_F32, trainable=True)
         s = torch.cuda.current_stream()
-        n = 20000
-        for step in (1, 2):
+        # two ordinary steps, then one at the largest batch the static array
+        # holds (its last slot in use)
+        for step, n in ((1, 20000), (2, 20000), (3, B.NAM_NOALLOC_TRAIN_MAX_QUERIES)):
             q = W.uniform_queries(rng[3], n, 7.0)
             y = torch.from_numpy(W.target_rgb(target, q)).cuda()
             dq = to_device(q)
