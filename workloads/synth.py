@@ -280,24 +280,36 @@ class ProceduralBRDF:
         return self.from_params(*self.params(u, v), wi, wo)
 
     @staticmethod
+    def ggx_ndf(alpha, cos_h):
+        """Isotropic GGX (Trowbridge-Reitz) normal distribution D(h) for the
+        cosine of the half vector with the normal."""
+        a2 = alpha * alpha
+        return a2 / (np.pi * (cos_h * cos_h * (a2 - 1.0) + 1.0) ** 2)
+
+    @staticmethod
+    def smith_lambda(alpha, cos_t):
+        """Smith's Lambda of the GGX distribution for a direction at cos_t
+        from the normal: (-1 + sqrt(1 + alpha^2 tan^2)) / 2."""
+        c = np.clip(cos_t, 1e-12, 1.0)
+        tan2 = (1.0 - c * c) / (c * c)
+        return 0.5 * (-1.0 + np.sqrt(1.0 + alpha * alpha * tan2))
+
+    @staticmethod
+    def schlick(f0, cos_d):
+        """Schlick's Fresnel approximation."""
+        return f0 + (1.0 - f0) * (1.0 - cos_d) ** 5
+
+    @staticmethod
     def from_params(a, r, wi, wo):
         """The BRDF for albedo a [n, 3] and roughness r [n]."""
+        P = ProceduralBRDF
         alpha = r * r
         ci, co = wi[2], wo[2]
         h = wi + wo
         h = h / np.maximum(np.linalg.norm(h, axis=0), 1e-300)
-        ch = h[2]
-        a2 = alpha * alpha
-        D = a2 / (np.pi * (ch * ch * (a2 - 1.0) + 1.0) ** 2)
-
-        def lam(c):
-            c = np.clip(c, 1e-12, 1.0)
-            tan2 = (1.0 - c * c) / (c * c)
-            return 0.5 * (-1.0 + np.sqrt(1.0 + a2 * tan2))
-
-        G2 = 1.0 / (1.0 + lam(ci) + lam(co))
-        vh = np.clip(np.sum(wi * h, axis=0), 0.0, 1.0)
-        F = 0.04 + 0.96 * (1.0 - vh) ** 5
+        D = P.ggx_ndf(alpha, h[2])
+        G2 = 1.0 / (1.0 + P.smith_lambda(alpha, ci) + P.smith_lambda(alpha, co))  # height-correlated
+        F = P.schlick(0.04, np.clip(np.sum(wi * h, axis=0), 0.0, 1.0))
         denom = np.maximum(4.0 * ci * co, 1e-12)
         spec = D * G2 * F / denom
         f = a / np.pi + spec[:, None]
