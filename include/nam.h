@@ -100,15 +100,21 @@ nam_status nam_check_device_error(nam_ctx* ctx);
 typedef struct nam_material_s* nam_material;
 
 enum { NAM_LATENT_F32 = 0, NAM_LATENT_F16 = 1 };
-/* Arithmetic of the MLPs (FP8: NAM_FRAME_MLP and two hidden layers only).
- * F32: plain FP32 FMA on CUDA cores, one query per
- * thread.  F16: parameters quantised to binary16 at creation (post-training
- * quantisation, Sec. 5.2), decoder layers on tensor cores with FP16 operands
- * and FP32 accumulation; the frame MLP keeps FP32 accuracy by splitting its
- * FP16 operands in two.  FP8: as F16 but each decoder layer's weights and
- * input activations are E4M3 with a per-layer scale (weights: absmax/448 of
- * the FP32 master; activations: the static scale passed in fp8_act_scale),
- * FP32 accumulation, FP32 bias. */
+/* Arithmetic of the MLPs.
+ * F32: plain FP32 FMA on CUDA cores, one query per thread.
+ * F16: parameters quantised to binary16 at creation (post-training
+ * quantisation, Sec. 5.2), MLP layers on tensor cores with FP16 operands and
+ * FP32 accumulation.  The operands the result is most sensitive to (the
+ * latent, the transformed directions, the frame MLP's hidden layer, the last
+ * hidden layer; every hidden layer for hidden width < 64) enter as two FP16
+ * halves, so the error against FP16 weights with exact activations stays
+ * within 2e-3.
+ * FP8 (beyond the paper): as F16, except that the hidden -> hidden decoder
+ * layers have E4M3 weights with a power-of-two per-layer scale (the smallest
+ * s_w with max |W| / s_w <= 448) and take their input as two E4M3 code sets
+ * of x / s_a (s_a: the smallest power of two >= fp8_act_scale[l]), FP32
+ * accumulation and FP32 bias; needs a decoder with at least two hidden
+ * layers. */
 enum { NAM_PREC_F32 = 0, NAM_PREC_F16 = 1, NAM_PREC_FP8 = 2 };
 enum { NAM_FILTER_TRILINEAR = 0, NAM_FILTER_STOCHASTIC = 1 };
 enum { NAM_ADDRESS_WRAP = 0, NAM_ADDRESS_CLAMP = 1 };
@@ -157,8 +163,10 @@ typedef struct {
   int32_t trainable;          /* 1: keep FP32 masters on the device for
                                  nam_backward / nam_train_step (F32 only;
                                  NAM_FRAME_MLP, two hidden layers) */
-  const float* fp8_act_scale; /* NAM_PREC_FP8: host array, input scale of
-                                 each decoder layer (n_layers values > 0) */
+  const float* fp8_act_scale; /* NAM_PREC_FP8: host array, n_layers values
+                                 > 0: max |input| / 448 of each decoder layer
+                                 (nam_fp8_calibrate); the hidden -> hidden
+                                 layers' entries set their input scales */
   /* importance sampler (Sec. 4.3, Appendix A): an MLP from (z, wi) to the
    * nine parameters of the analytic proxy density.  sampler_hidden = 0: no
    * sampler; 32: widths 11 -> 32 -> 32 -> 32 -> 9 with ReLU hidden layers,
@@ -186,7 +194,9 @@ typedef struct {
   int64_t texels;             /* texels over all levels */
   int64_t n_params;           /* FP32 master parameters (frame + decoder) */
   int32_t precision, filter, address, levels;
-  float fp8_weight_scale[NAM_MAX_LAYERS]; /* NAM_PREC_FP8: per decoder layer */
+  float fp8_weight_scale[NAM_MAX_LAYERS]; /* NAM_PREC_FP8: weight scale s_w of
+                                             each hidden -> hidden decoder
+                                             layer, 0 for the others */
 } nam_material_info;
 
 /* Copy the pyramid and weights to the device in the layout the kernels read

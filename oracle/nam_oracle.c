@@ -117,21 +117,25 @@ uint8_t orc_f64_to_e4m3(double x) {
 double orc_round_e4m3(double x) { return orc_e4m3_to_f64(orc_f64_to_e4m3(x)); }
 
 /* Per-layer FP8 weight quantisation (beyond the paper, which names lower
- * precision as future work in Sec. 5.2): s = absmax(W) / 448 in FP32, each
- * code = E4M3(W / s) with the division done in FP32, the precision in which
- * the quantised code is decided.  Writes s and the dequantised weights. */
+ * precision as future work in Sec. 5.2).  Reading: the scale is the power of
+ * two s = 2^ceil(log2(absmax(W) / 448)) (1 for an all-zero layer), so that
+ * |W| / s <= 448 and dividing by s is exact; each code = E4M3(W / s), round to
+ * nearest even, saturating.  Writes s and the dequantised weights code * s. */
 void orc_quantize_e4m3_layer(const float* W, int64_t n, float* scale_out, double* deq_out) {
-  float amax = 0.0f;
+  double amax = 0.0;
   for (int64_t i = 0; i < n; ++i) {
-    float a = fabsf(W[i]);
+    double a = fabs((double)W[i]);
     if (a > amax) amax = a;
   }
-  float s = amax > 0.0f ? amax / 448.0f : 1.0f;
-  *scale_out = s;
-  for (int64_t i = 0; i < n; ++i) {
-    float q = W[i] / s;
-    deq_out[i] = orc_round_e4m3((double)q) * (double)s;
+  /* the smallest power of two s with amax / s <= 448, found by doubling and
+   * halving (exact in FP64) rather than through log2 */
+  double s = 1.0;
+  if (amax > 0.0) {
+    while (amax / s > 448.0) s *= 2.0;
+    while (amax / (s * 0.5) <= 448.0) s *= 0.5;
   }
+  *scale_out = (float)s;
+  for (int64_t i = 0; i < n; ++i) deq_out[i] = orc_round_e4m3((double)W[i] / s) * s;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -147,11 +151,9 @@ typedef struct {
   int32_t n_layers;         /* decoder linear layers */
   int32_t widths[ORC_MAXL + 1]; /* decoder widths, widths[0] = 14, widths[n_layers] = 3, or 6 with
                                    the albedo head (outputs 3..5: directional albedo) */
-  int32_t act_round;        /* decoder operand rounding: 0 none, 1 fp16, 2 fp8 */
   const void* pyramid;      /* levels packed finest first, [texel][C] */
   const double* frame_params; /* Wf1[h][8], bf1[h], Wf2[6][h], bf2[6] */
   const double* dec_params;   /* per layer W[out][in] then b[out] */
-  const double* act_scale;    /* act_round == 2: input scale s_l of each decoder layer */
   int32_t frame_form;         /* 0: frame MLP 8 -> h -> 6 with Gram-Schmidt (frame_hidden > 0);
                                  1: the paper's form, one linear layer 8 -> 12 giving two frames
                                  (frame_params = Wf[12][8], bf[12]; decoder widths[0] = 20) */
@@ -337,102 +339,6 @@ typedef struct {
 /* ------------------------------------------------------------------------- */
 /* valid alternative roundings                                                */
 /* ------------------------------------------------------------------------- */
-/* A reduced-precision evaluation rounds FP32 values that are themselves
- * rounded sums; when the exact value lies within that FP32 error of the
- * midpoint between two representable neighbours, either neighbour is a
- * correct result.  The rounding context records such ambiguous sites
- * (decoder layer input `layer`, element j) and, on request, rounds chosen
- * sites to the other neighbour, so that the oracle can list every valid
- * result of a query. */
-#define ORC_MAX_SITES 32
-typedef struct {
-  int record;                       /* record ambiguous sites */
-  int nsites;
-  int site[ORC_MAX_SITES];
-  double dist[ORC_MAX_SITES];       /* |x - midpoint| / (gamma A) */
-  int nflip;
-  int flip[ORC_MAX_SITES];          /* sites rounded to the other neighbour */
-  double gamma;                     /* ambiguity band, relative to the sum's magnitude */
-} round_ctx;
-
-static uint16_t f16_step(uint16_t b, int up) {
-  int neg = (b >> 15) & 1;
-  uint16_t mag = b & 0x7fff;
-  if (mag == 0) return up ? 0x0001 : 0x8001;
-  if (up != neg) return b + 1;   /* away from zero */
-  return b - 1;                  /* towards zero */
-}
-static uint8_t e4m3_step(uint8_t b, int up) {
-  int neg = (b >> 7) & 1;
-  uint8_t mag = b & 0x7f;
-  if (mag == 0) return up ? 0x01 : 0x81;
-  if (up != neg) return (uint8_t)(mag >= 0x7e ? b : b + 1);
-  return b - 1;
-}
-
-/* Rounding of the decoder's MMA operands, emulated in FP64 so that the oracle
- * can evaluate the reduced-precision forms of the method step by step:
- * act_round 1 rounds every decoder-layer input to binary16 (FP16 inference,
- * Sec. 5.2: FP16 parameters at load; the MMA operands are FP16, Sec. 7.2);
- * act_round 2 quantises decoder-layer l's input a to E4M3(a / s_l) s_l with a
- * static per-layer scale s_l, the code decided in FP32.  The frame path is
- * never rounded: it is evaluated at FP32 accuracy in every precision. */
-static double round_act(const orc_model* m, double x, int dec_layer) {
-  if (m->act_round == 1) return orc_round_f16(x);
-  if (m->act_round == 2) {
-    float s = (float)m->act_scale[dec_layer];
-    float inv = 1.0f / s;
-    float q = (float)x * inv;
-    return orc_round_e4m3((double)q) * (double)s;
-  }
-  return x;
-}
-
-/* round_act with ambiguity bookkeeping: A is the magnitude (sum of |terms|)
- * of the sum that produced x; `site` identifies the rounding point. */
-static double round_act_ctx(const orc_model* m, double x, double A, int dec_layer, int site, round_ctx* rc) {
-  if (!rc || m->act_round == 0) return round_act(m, x, dec_layer);
-  double lo, hi, scale = 1.0, xs = x, nominal;
-  if (m->act_round == 1) {
-    uint16_t b = orc_f64_to_f16(x);
-    nominal = orc_f16_to_f64(b);
-    if (nominal == x) return nominal;
-    if (nominal > x) { hi = nominal; lo = orc_f16_to_f64(f16_step(b, 0)); }
-    else { lo = nominal; hi = orc_f16_to_f64(f16_step(b, 1)); }
-  } else {
-    float sc = (float)m->act_scale[dec_layer];
-    float inv = 1.0f / sc;
-    scale = sc;
-    xs = (double)((float)x * inv);
-    A = A * (double)inv;
-    uint8_t b = orc_f64_to_e4m3(xs);
-    nominal = orc_e4m3_to_f64(b);
-    if (nominal == xs || fabs(xs) >= 448.0) return nominal * scale;
-    if (nominal > xs) { hi = nominal; lo = orc_e4m3_to_f64(e4m3_step(b, 0)); }
-    else { lo = nominal; hi = orc_e4m3_to_f64(e4m3_step(b, 1)); }
-  }
-  double mid = 0.5 * (lo + hi);
-  double d = fabs(xs - mid) / (rc->gamma * A);
-  if (d <= 1.0) {
-    if (rc->record) {
-      if (rc->nsites < ORC_MAX_SITES) {
-        rc->site[rc->nsites] = site;
-        rc->dist[rc->nsites] = d;
-        rc->nsites++;
-      } else {
-        /* keep the closest ones */
-        int worst = 0;
-        for (int k = 1; k < ORC_MAX_SITES; ++k)
-          if (rc->dist[k] > rc->dist[worst]) worst = k;
-        if (d < rc->dist[worst]) { rc->site[worst] = site; rc->dist[worst] = d; }
-      }
-    }
-    for (int k = 0; k < rc->nflip; ++k)
-      if (rc->flip[k] == site) return (nominal == lo ? hi : lo) * scale;
-  }
-  return nominal * scale;
-}
-
 /* The paper's frame form (Sec. 4.2, Eq. 4; Sec. 9): one linear layer maps z
  * to N = 2 (normal, tangent) pairs; each is normalised, not orthogonalised,
  * and b = n x t / |n x t|.  Readings for degenerate outputs: |n_raw| < 1e-20
@@ -472,8 +378,7 @@ static void paper_frames(const orc_model* m, trace* tr) {
   }
 }
 
-static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trace* tr, round_ctx* rc,
-                       double kappa) {
+static void forward(const orc_model* m, const orc_queries* q, int64_t i, trace* tr) {
   if (q->z) {
     /* the latent comes from the encoder, not from the texture */
     tr->ntaps = 0;
@@ -528,17 +433,10 @@ static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trac
   /* decoder input order: z0..z7, wi', wo' (paper form: T wi = (t1, b1, n1,
    * t2, b2, n2) . wi, then T wo) */
   double* x = tr->act[0];
-  for (int c = 0; c < ORC_C; ++c) {
-    double A = 0.0;
-    for (int k = 0; k < tr->ntaps; ++k) A += fabs(tr->w[k] * texel(m, tr->idx[k], c));
-    x[c] = round_act_ctx(m, tr->z[c], A, 0, c, rc);
-  }
-  /* directions: FP32 transform by an FP32 frame whose error grows with the
-   * frame's condition number */
-  const double Ad = 3.0 + 8.0 * kappa;
+  for (int c = 0; c < ORC_C; ++c) x[c] = tr->z[c];
   for (int k = 0; k < nd; ++k) {
-    x[ORC_C + k] = round_act_ctx(m, wi_l[k], Ad, 0, ORC_C + k, rc);
-    x[ORC_C + nd + k] = round_act_ctx(m, wo_l[k], Ad, 0, ORC_C + nd + k, rc);
+    x[ORC_C + k] = wi_l[k];
+    x[ORC_C + nd + k] = wo_l[k];
   }
 
   const double* p = m->dec_params;
@@ -549,15 +447,10 @@ static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trac
     p = b + out;
     int last = (l == m->n_layers - 1);
     for (int j = 0; j < out; ++j) {
-      double s = b[j], A = fabs(b[j]);
-      for (int k = 0; k < in; ++k) {
-        s += W[j * in + k] * tr->act[l][k];
-        A += fabs(W[j * in + k] * tr->act[l][k]);
-      }
+      double s = b[j];
+      for (int k = 0; k < in; ++k) s += W[j * in + k] * tr->act[l][k];
       tr->pre[l][j] = s;
-      if (!last) {
-        tr->act[l + 1][j] = round_act_ctx(m, s > 0.0 ? s : 0.0, A, l + 1, (l + 1) * 1024 + j, rc);
-      }
+      if (!last) tr->act[l + 1][j] = s > 0.0 ? s : 0.0;
     }
   }
   int lastl = m->n_layers - 1;
@@ -566,9 +459,6 @@ static void forward_rc(const orc_model* m, const orc_queries* q, int64_t i, trac
   for (int c = 0; c < m->widths[m->n_layers]; ++c) tr->y[c] = tr->pre[lastl][c] * (c < 3 ? tr->cosf : 1.0);
 }
 
-static void forward(const orc_model* m, const orc_queries* q, int64_t i, trace* tr) {
-  forward_rc(m, q, i, tr, NULL, 0.0);
-}
 
 /* ------------------------------------------------------------------------- */
 /* exported batch entry points                                                */
@@ -657,10 +547,8 @@ void orc_eval(const orc_model* m, const orc_queries* q, int64_t n, double* rgb_o
 void orc_decoder_input_absmax(const orc_model* m, const orc_queries* q, int64_t n, double* amax_out) {
   trace* tr = (trace*)malloc(sizeof(trace));
   for (int l = 0; l < m->n_layers; ++l) amax_out[l] = 0.0;
-  orc_model mm = *m;
-  mm.act_round = 0;
   for (int64_t i = 0; i < n; ++i) {
-    forward(&mm, q, i, tr);
+    forward(m, q, i, tr);
     for (int l = 0; l < m->n_layers; ++l)
       for (int k = 0; k < m->widths[l]; ++k) {
         double a = fabs(tr->act[l][k]);
@@ -724,11 +612,9 @@ void orc_grad(const orc_model* m, const orc_queries* q, int64_t n, const double*
               double* g_frame, double* g_dec, double* g_pyr, double* g_z) {
   if (m->frame_form == 1) return; /* reverse mode of the paper's frame form is not built */
   trace* tr = (trace*)malloc(sizeof(trace));
-  orc_model mm = *m;
-  mm.act_round = 0;
   double da[ORC_MAXW], dpre[ORC_MAXW];
   for (int64_t i = 0; i < n; ++i) {
-    forward(&mm, q, i, tr);
+    forward(m, q, i, tr);
     int L = m->n_layers;
     /* output */
     const int ow = m->widths[L];
@@ -838,10 +724,8 @@ void orc_grad(const orc_model* m, const orc_queries* q, int64_t n, const double*
  * difference checks use it to skip parameters whose step crosses a kink. */
 void orc_relu_pattern(const orc_model* m, const orc_queries* q, int64_t n, uint64_t* out) {
   trace* tr = (trace*)malloc(sizeof(trace));
-  orc_model mm = *m;
-  mm.act_round = 0;
   for (int64_t i = 0; i < n; ++i) {
-    forward(&mm, q, i, tr);
+    forward(m, q, i, tr);
     uint64_t h = 1469598103934665603ull;
     for (int j = 0; j < m->frame_hidden; ++j) h = (h ^ (uint64_t)(tr->hf_pre[j] > 0.0)) * 1099511628211ull;
     for (int l = 0; l + 1 < m->n_layers; ++l)
@@ -906,106 +790,12 @@ static double frame_kappa(const orc_model* m, const trace* tr) {
 
 void orc_frame_condition(const orc_model* m, const orc_queries* q, int64_t n, double* kappa_out) {
   trace* tr = (trace*)malloc(sizeof(trace));
-  orc_model mm = *m;
-  mm.act_round = 0;
   for (int64_t i = 0; i < n; ++i) {
     if (m->frame_hidden <= 0 && m->frame_form != 1) { kappa_out[i] = 1.0; continue; }
-    forward(&mm, q, i, tr);
+    forward(m, q, i, tr);
     kappa_out[i] = frame_kappa(m, tr);
   }
   free(tr);
-}
-
-/* Every valid result of each query under the model's rounding emulation:
- * the nominal result first, then the results with each subset of the three
- * ambiguous rounding decisions closest to their midpoints taken the other
- * way.  out is
- * [n][ORC_MAX_ALT][widths[n_layers]], unused slots NaN; nalt[i] results, nsites[i]
- * ambiguous sites found.  gamma is the FP32 error band relative to each
- * sum's magnitude. */
-#define ORC_MAX_ALT 8
-typedef struct {
-  const orc_model* m;
-  const orc_queries* q;
-  int64_t begin, end;
-  double gamma;
-  double* out;
-  int32_t* nalt;
-  int32_t* nsites;
-} alt_job;
-
-static void* alt_worker(void* arg) {
-  alt_job* j = (alt_job*)arg;
-  const orc_model* m = j->m;
-  trace* tr = (trace*)malloc(sizeof(trace));
-  orc_model plain = *m;
-  plain.act_round = 0;
-  for (int64_t i = j->begin; i < j->end; ++i) {
-    const int ow = m->widths[m->n_layers];
-    double* o = j->out + i * ORC_MAX_ALT * ow;
-    for (int k = 0; k < ORC_MAX_ALT * ow; ++k) o[k] = NAN;
-    double kappa = 1.0;
-    if (m->frame_hidden > 0 || m->frame_form == 1) {
-      forward(&plain, j->q, i, tr);
-      kappa = frame_kappa(m, tr);
-    }
-    round_ctx rc;
-    memset(&rc, 0, sizeof rc);
-    rc.record = 1;
-    rc.gamma = j->gamma;
-    forward_rc(m, j->q, i, tr, &rc, kappa);
-    for (int c = 0; c < ow; ++c) o[c] = tr->y[c];
-    int ns = rc.nsites, na = 1;
-    j->nsites[i] = ns;
-    /* the three sites closest to their rounding midpoints, all subsets */
-    int sites[3], nk = 0;
-    for (int pick = 0; pick < 3 && pick < ns; ++pick) {
-      int best = -1;
-      for (int k = 0; k < ns; ++k) {
-        int used = 0;
-        for (int u2 = 0; u2 < nk; ++u2) used |= sites[u2] == rc.site[k];
-        if (!used && (best < 0 || rc.dist[k] < rc.dist[best])) best = k;
-      }
-      sites[nk++] = rc.site[best];
-    }
-    if (nk > 0) {
-      int nsub = (1 << nk) - 1;
-      for (int t = 0; t < nsub && na < ORC_MAX_ALT; ++t) {
-        round_ctx fc;
-        memset(&fc, 0, sizeof fc);
-        fc.gamma = j->gamma;
-        int mask = t + 1;
-        for (int k = 0; k < nk; ++k)
-          if (mask & (1 << k)) fc.flip[fc.nflip++] = sites[k];
-        forward_rc(m, j->q, i, tr, &fc, kappa);
-        for (int c = 0; c < ow; ++c) o[na * ow + c] = tr->y[c];
-        ++na;
-      }
-    }
-    j->nalt[i] = na;
-  }
-  free(tr);
-  return NULL;
-}
-
-void orc_eval_alternatives(const orc_model* m, const orc_queries* q, int64_t n, double gamma, double* out,
-                           int32_t* nalt, int32_t* nsites, int nthreads) {
-  if (nthreads < 1) nthreads = 1;
-  if (nthreads > 256) nthreads = 256;
-  if (n < 4096) nthreads = 1;
-  pthread_t th[256];
-  alt_job jobs[256];
-  int64_t chunk = (n + nthreads - 1) / nthreads;
-  for (int t = 0; t < nthreads; ++t) {
-    jobs[t].m = m; jobs[t].q = q; jobs[t].gamma = gamma;
-    jobs[t].out = out; jobs[t].nalt = nalt; jobs[t].nsites = nsites;
-    jobs[t].begin = (int64_t)t * chunk;
-    if (jobs[t].begin > n) jobs[t].begin = n;
-    jobs[t].end = jobs[t].begin + chunk < n ? jobs[t].begin + chunk : n;
-  }
-  if (nthreads == 1) { alt_worker(&jobs[0]); return; }
-  for (int t = 0; t < nthreads; ++t) pthread_create(&th[t], NULL, alt_worker, &jobs[t]);
-  for (int t = 0; t < nthreads; ++t) pthread_join(th[t], NULL);
 }
 
 /* ------------------------------------------------------------------------- */

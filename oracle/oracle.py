@@ -20,7 +20,6 @@ _lib = None
 
 FILTER_TRILINEAR, FILTER_STOCHASTIC = 0, 1
 ADDRESS_WRAP, ADDRESS_CLAMP = 0, 1
-ROUND_NONE, ROUND_FP16, ROUND_FP8 = 0, 1, 2  # decoder MMA operands
 MAXL = 8
 
 
@@ -39,9 +38,9 @@ class _Model(C.Structure):
     _fields_ = [("W0", C.c_int32), ("H0", C.c_int32), ("L", C.c_int32), ("C", C.c_int32),
                 ("latent_f16", C.c_int32), ("address", C.c_int32), ("filter", C.c_int32),
                 ("out_cosine", C.c_int32), ("frame_hidden", C.c_int32), ("n_layers", C.c_int32),
-                ("widths", C.c_int32 * (MAXL + 1)), ("act_round", C.c_int32),
+                ("widths", C.c_int32 * (MAXL + 1)),
                 ("pyramid", C.c_void_p), ("frame_params", C.c_void_p),
-                ("dec_params", C.c_void_p), ("act_scale", C.c_void_p), ("frame_form", C.c_int32)]
+                ("dec_params", C.c_void_p), ("frame_form", C.c_int32)]
 
 
 class _Queries(C.Structure):
@@ -83,7 +82,6 @@ def lib():
         _lib.orc_grad.argtypes = [p, p, i64, p, p, p, p, p]
         _lib.orc_relu_pattern.argtypes = [p, p, i64, p]
         _lib.orc_frame_condition.argtypes = [p, p, i64, p]
-        _lib.orc_eval_alternatives.argtypes = [p, p, i64, d, p, p, p, C.c_int]
     return _lib
 
 
@@ -123,7 +121,8 @@ def f64_to_e4m3(x):
 
 
 def quantize_e4m3_layer(W):
-    """(scale, dequantised weights) of one layer, codes decided in FP32."""
+    """(scale, dequantised weights) of one layer: power-of-two scale, codes
+    E4M3(W / scale)."""
     W = np.ascontiguousarray(W, dtype=np.float32)
     s = np.zeros(1, dtype=np.float32)
     out = np.zeros(W.shape, dtype=np.float64)
@@ -140,13 +139,13 @@ class Model:
     pyramid: [texels, 8] float16 or float32; frame: None or [(Wf1,bf1),(Wf2,bf2)];
     decoder: [(W,b), ...] with W [out][in].  `params` selects the parameter
     values: "master" (as given), "fp16" (each rounded to binary16 by the
-    oracle's own rounding), "fp8" (frame in fp16, decoder weights E4M3 with a
-    per-layer absmax scale, decoder biases in FP32).
+    oracle's own rounding), "fp8" (as "fp16", except the weights of the
+    hidden -> hidden decoder layers: E4M3 with a power-of-two per-layer scale).
+    Activations are always evaluated in FP64.
     """
 
     def __init__(self, W0, H0, L, pyramid, frame, decoder, *, filter=FILTER_TRILINEAR,
-                 address=ADDRESS_WRAP, out_cosine=False, params="master", act_round=ROUND_NONE,
-                 act_scale=None):
+                 address=ADDRESS_WRAP, out_cosine=False, params="master"):
         self.W0, self.H0, self.L = W0, H0, L
         self.pyramid = np.ascontiguousarray(pyramid)
         assert self.pyramid.shape[1] == 8
@@ -172,20 +171,21 @@ class Model:
             fp = None
         chunks = []
         scales = []
-        for W, b in decoder:
-            if params == "fp16":
-                chunks += [round_f16(W.astype(np.float64)).ravel(), round_f16(b.astype(np.float64))]
-            elif params == "fp8":
+        for l, (W, b) in enumerate(decoder):
+            hidden_to_hidden = 0 < l < len(decoder) - 1
+            if params == "fp8" and hidden_to_hidden:
                 s, Wd = quantize_e4m3_layer(W)
                 scales.append(s)
-                chunks += [Wd.ravel(), b.astype(np.float64)]
+                chunks += [Wd.ravel(), round_f16(b.astype(np.float64))]
+            elif params in ("fp16", "fp8"):
+                scales.append(None)
+                chunks += [round_f16(W.astype(np.float64)).ravel(), round_f16(b.astype(np.float64))]
             else:
                 chunks += [W.astype(np.float64).ravel(), b.astype(np.float64)]
         if params == "fp8":
             self.weight_scales = scales
         self.frame_params = fp
         self.dec_params = np.ascontiguousarray(np.concatenate(chunks))
-        self.act_scale = None if act_scale is None else np.ascontiguousarray(act_scale, dtype=np.float64)
         s = _Model()
         s.W0, s.H0, s.L, s.C = W0, H0, L, 8
         s.latent_f16 = int(f16)
@@ -197,11 +197,9 @@ class Model:
         s.n_layers = len(decoder)
         for i, w in enumerate(self.widths):
             s.widths[i] = w
-        s.act_round = act_round
         s.pyramid = self._pyr.ctypes.data
         s.frame_params = None if fp is None else fp.ctypes.data
         s.dec_params = self.dec_params.ctypes.data
-        s.act_scale = None if self.act_scale is None else self.act_scale.ctypes.data
         self._s = s
 
     @classmethod
@@ -306,39 +304,18 @@ def frame_condition(model: Model, q) -> np.ndarray:
     return out
 
 
-MAX_ALT = 8
-
-
-def eval_alternatives(model: Model, q, gamma=2.0 ** -19, nthreads=None):
-    """Every valid result of each query under the model's rounding emulation
-    (see orc_eval_alternatives): alts [n, 8, outputs] (NaN-padded, nominal
-    first), nalt [n], nsites [n]."""
-    n = _nq(q)
-    alts = np.full((n, MAX_ALT, model.widths[-1]), np.nan)
-    nalt = np.zeros(n, dtype=np.int32)
-    nsites = np.zeros(n, dtype=np.int32)
-    if n:
-        qv = _QueryView(q, n)
-        lib().orc_eval_alternatives(C.byref(model._s), C.byref(qv.s), n, gamma, _ptr(alts), _ptr(nalt),
-                                    _ptr(nsites), nthreads or os.cpu_count() or 1)
-    return alts, nalt, nsites
-
-
 def parity(g, o, kappa, tol, kappa_well=50.0, c=64.0, unit=2.0 ** -24, tau=None):
     """Element-wise parity with a conditioning-aware bound.
 
     rel_i = max_c |g - o| / max(|o|, tau), tau = RMS of o.  Queries whose
     frame condition number is at most kappa_well must meet `tol`; beyond it
-    the bound is max(tol, c * kappa * unit), the growth of a
-    finite-precision evaluation's rounding (unit roundoff `unit` of the
-    frame arithmetic) through an ill-conditioned frame.  `tau` overrides the
+    the bound is tol + c * kappa * unit: the evaluation's own error budget
+    plus the growth of the frame arithmetic's rounding (unit roundoff
+    `unit`) through an ill-conditioned frame, a relative error e of the raw
+    frame outputs moving the frame by up to (1 + 2 kappa) e.  `tau` overrides the
     RMS floor (a few queries cut from a larger batch keep that batch's
     floor).  Returns (ok, stats)."""
     g = np.asarray(g, dtype=np.float64).reshape(-1, 3)
-    alts = None
-    if np.ndim(o) == 3:   # [n, k, 3] valid alternatives, nominal first
-        alts = np.asarray(o, dtype=np.float64)
-        o = alts[:, 0, :]
     o = np.asarray(o, dtype=np.float64).reshape(-1, 3)
     kappa = np.asarray(kappa, dtype=np.float64)
     if o.size == 0:
@@ -347,13 +324,9 @@ def parity(g, o, kappa, tol, kappa_well=50.0, c=64.0, unit=2.0 ** -24, tau=None)
         tau = float(np.sqrt(np.mean(o * o)))
     tau = max(tau, 1e-30)
     den = np.maximum(np.abs(o), tau)
-    if alts is None:
-        rel = (np.abs(g - o) / den).max(axis=1)
-    else:
-        r = (np.abs(g[:, None, :] - alts) / den[:, None, :]).max(axis=2)
-        rel = np.nanmin(r, axis=1)
+    rel = (np.abs(g - o) / den).max(axis=1)
     well = kappa <= kappa_well
-    bound = np.where(well, tol, np.maximum(tol, c * kappa * unit))
+    bound = np.where(well, tol, tol + c * kappa * unit)
     ok = bool(np.all(rel <= bound)) and bool(np.all(np.isfinite(g)))
     bins = {}
     for lo, hi in ((0, 10), (10, 50), (50, 300), (300, 3000), (3000, np.inf)):
@@ -363,6 +336,7 @@ def parity(g, o, kappa, tol, kappa_well=50.0, c=64.0, unit=2.0 ** -24, tau=None)
                                    "max_rel_over_kappa_u": float((rel[sel] / (kappa[sel] * unit)).max())}
     st = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
           "max_rel_well_conditioned": float(rel[well].max()) if well.any() else 0.0,
+          "max_rel_ill_conditioned": float(rel[~well].max()) if (~well).any() else 0.0,
           "ill_conditioned": int((~well).sum()), "n": int(len(rel)),
           "worst_over_bound": float((rel / bound).max()), "by_kappa": bins}
     return ok, st

@@ -252,8 +252,6 @@ nam_status nam::validate_desc(const nam_material_desc* d, Shape* shape, PyrDesc*
     if (d->widths[l] != H) return fail(NAM_ERR_UNSUPPORTED, "hidden widths must be equal");
   if (H != 16 && H != 32 && H != 64) return fail(NAM_ERR_UNSUPPORTED, "hidden width %d not in {16, 32, 64}", H);
   if (d->n_layers == 4 && H != 64) return fail(NAM_ERR_UNSUPPORTED, "three hidden layers need H = 64");
-  if (d->precision == NAM_PREC_FP8 && (paper || d->n_layers != 3))
-    return fail(NAM_ERR_UNSUPPORTED, "FP8 needs the frame MLP form and two hidden layers");
   if (d->trainable && (paper || d->n_layers != 3))
     return fail(NAM_ERR_UNSUPPORTED, "training needs the frame MLP form and two hidden layers");
   if (d->precision < NAM_PREC_F32 || d->precision > NAM_PREC_FP8)

@@ -95,9 +95,11 @@ static void pack_image(const float* frame, const float* dec, int in, int n_out, 
   std::memset(out, 0, sizeof(Img));
   Img& S = *reinterpret_cast<Img*>(out);
   auto h = [](float v) { return __half2float(__float2half_rn(v)); };
+  // FP8: E4M3 weights (times their layer scale) on the hidden -> hidden
+  // layers only; every other parameter binary16, as in the tensor-core blob
   const bool p8 = precision == NAM_PREC_FP8;
-  auto wq = [&](float v, int layer) { return p8 ? e4m3_dequant(v, sw[layer]) : h(v); };
-  auto bq = [&](float v) { return p8 ? v : h(v); };
+  auto wq = [&](float v, int layer) { return p8 && layer >= 1 && layer < NH ? e4m3_dequant(v, sw[layer]) : h(v); };
+  auto bq = [&](float v) { return h(v); };
   if (FK == 1) {
     for (int i = 0; i < 128; ++i) S.fW1[i] = h(frame[i]);
     for (int i = 0; i < 16; ++i) S.fb1[i] = h(frame[128 + i]);

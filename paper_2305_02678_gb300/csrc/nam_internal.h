@@ -119,10 +119,13 @@ inline void once_per_device(std::atomic<uint64_t>& done, F fn) {
 }
 
 int launch_eval_f32(const LaunchCommon& L, void* stream);
-// FP16 tensor-core evaluation (every shape with a tensor-core kernel)
+// tensor-core evaluation (every shape with a tensor-core kernel): FP16, and
+// FP8 (E4M3 hidden -> hidden layers)
 int launch_eval_f16(const LaunchCommon& L, void* stream);
+int launch_eval_fp8(const LaunchCommon& L, void* stream);
 size_t f16_blob_bytes(const Shape& s);
-int pack_f16_blob(const Shape& s, const float* frame, const float* dec, uint8_t* out);
+int pack_f16_blob(const Shape& s, int precision, const float* frame, const float* dec, const float* act_scale,
+                  uint8_t* out, float* weight_scales_out);
 int launch_eval_tc(const LaunchCommon& L, int precision, void* stream);
 
 // Weight blob sizes and packing (host side).

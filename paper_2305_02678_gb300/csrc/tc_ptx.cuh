@@ -1,6 +1,7 @@
 // Thin wrappers over the sm_100-family PTX used by the tensor-core kernels:
 // mbarriers, bulk (TMA) copies, tcgen05 MMA / TMEM and their fences.
 #pragma once
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 namespace nam {
@@ -21,6 +22,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Non-blocking probe: true if the phase with the given parity has completed.
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}\n"
       : "=r"(ok)
       : "r"(bar), "r"(parity)
@@ -49,18 +62,18 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parit
 // timeout_ns of wall time.  Returns false if the limit was reached.  A plain
 // try_wait may suspend the thread for a hardware-defined time until the phase
 // completes; with such waits the clock is read only every 8 probes.  A limit
-// below 100 us probes with a suspend hint no longer than the limit, so that a
-// limit shorter than the operation waited for does run out (the first miss
-// starts the clock).
+// below 100 us spins on probes that never suspend and reads the clock after
+// each, so that a limit shorter than the operation waited for does run out.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t timeout_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const uint64_t t0 = globaltimer();
   if (timeout_ns < 100000u) {
+    const uint64_t t0 = globaltimer();
     for (;;) {
-      if (mbar_try_wait_sleep(bar, parity, (uint32_t)timeout_ns)) return true;
+      if (mbar_test_wait(bar, parity)) return true;
       if (globaltimer() - t0 > timeout_ns) return false;
     }
   }
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 7) == 0 && globaltimer() - t0 > timeout_ns) return false;
@@ -160,6 +173,16 @@ __device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uin
       "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// E4M3 operands with A in TMEM (four codes per 32-bit column, K = 32 per MMA).
+__device__ __forceinline__ void mma_f8_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                          uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
 // Arrive on `bar` once every tcgen05 op this thread issued so far is complete.
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
@@ -198,7 +221,12 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
 }
-// registers -> TMEM, 32 lanes x 32 bit, 8 / 16 consecutive columns.
+// registers -> TMEM, 32 lanes x 32 bit, 4 / 8 / 16 consecutive columns.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t (&v)[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]), "r"(v[1]),
+               "r"(v[2]), "r"(v[3])
+               : "memory");
+}
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
                "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
@@ -277,6 +305,14 @@ __device__ __forceinline__ uint32_t pack_e4m3x2(float lo, float hi) {
   uint16_t d;
   asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(d) : "f"(hi), "f"(lo));
   return (uint32_t)d;
+}
+// Packed E4M3 pair (low 16 bits; first value in the low byte) -> the two
+// values as FP32 (exact: every E4M3 value is a binary16 value).
+__device__ __forceinline__ float2 unpack_e4m3x2(uint32_t codes) {
+  uint32_t h;
+  asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h) : "h"((uint16_t)codes));
+  const __half2 hh = *reinterpret_cast<const __half2*>(&h);
+  return __half22float2(hh);
 }
 // Same with ReLU applied by the conversion.
 __device__ __forceinline__ uint32_t pack_e4m3x2_relu(float lo, float hi) {

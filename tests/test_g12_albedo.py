@@ -2,9 +2,9 @@
 decoder's extra RGB triplet approximates the directional albedo of Eq. 2 and
 is trained with an L2 loss against one-sample estimates).  Evaluation in
 FP32, FP16 and FP8 against the oracle's six-output decoder with the
-tolerances of the RGB path (1e-5 FP32 and 2e-3 FP16 against the oracle
-with the same parameter values and FP64 activations; 3e-2 FP8 against the
-operand-rounding oracle); the RGB of a material
+tolerances of the RGB path (1e-5 FP32, 2e-3 FP16 and 3e-2 FP8 against the
+oracle with the same parameter values and FP64 activations); the RGB of a
+material
 with the head is nam_eval's; reverse mode with [n][6] output gradients; the
 fused training step's loss and update direction against the oracle; a fit
 of the head to the procedural material's albedo; refused combinations."""
@@ -80,10 +80,8 @@ def test_albedo_fp8(gctx, oracle):
     scales = np.where(amax > 0, amax / 448.0, 1.0).astype(np.float32)
     mat = gctx.material(W0, W0, L, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_FP8, act_scale=scales)
     got = _eval_both(mat, q)
-    om = oracle.Model(W0, W0, L, pyr, model["frame"], model["decoder"], params="fp8", act_round=oracle.ROUND_FP8,
-                      act_scale=scales)
-    alts = oracle.eval_alternatives(om, q)[0]
-    _parity(oracle, got, alts, oracle.frame_condition(om, q), TOL_F8, "fp8")
+    om = oracle.Model(W0, W0, L, pyr, model["frame"], model["decoder"], params="fp8")
+    _parity(oracle, got, oracle.eval(om, q), oracle.frame_condition(om, q), TOL_F8, "fp8")
     mat.destroy()
     gctx.check()
 

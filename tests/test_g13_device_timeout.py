@@ -41,11 +41,12 @@ def test_short_wait_limit_reports_timeout_and_gpu_stays_usable(oracle, precision
         kw["act_scale"] = np.where(amax > 0, amax / 448.0, 1.0).astype(np.float32)
     with Context(0, wait_timeout_ns=1) as short:
         mat = short.material(W0, H0, L, pyr, model["frame"], model["decoder"], precision=precision, **kw)
-        mat.eval(dq)
+        for _ in range(3):
+            mat.eval(dq)
         with pytest.raises(B.NamError) as e:
             short.check()
         assert e.value.status == B.NAM_ERR_TIMEOUT
-        short.check()  # the error word was cleared
+        short.check()  # the error word was cleared (no launch since)
         mat.destroy()
     with Context(0) as ok:
         mat = ok.material(W0, H0, L, pyr, model["frame"], model["decoder"], precision=precision, **kw)
@@ -58,4 +59,4 @@ def test_short_wait_limit_reports_timeout_and_gpu_stays_usable(oracle, precision
     o = oracle.eval(om, W.slice_queries(q, 0, n))
     err = oracle.relative_error(g[:n], o)[0]
     assert np.isfinite(g).all()
-    assert err <= (2e-3 if precision == B.NAM_PREC_F16 else 0.5)
+    assert err <= (2e-3 if precision == B.NAM_PREC_F16 else 3e-2)

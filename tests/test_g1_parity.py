@@ -9,9 +9,9 @@ and FP64 activations:
 Both bounds hold for every query whose frame step is well conditioned
 (condition number kappa <= 50, ~99.8% of the 1080p workload's queries).  The
 rest, where the decoded normal and tangent are nearly parallel or nearly
-cancel, are checked against max(tol, 64 kappa 2^-24): the frame is computed
-at FP32 accuracy, and a relative error e of its raw outputs moves the frame
-by up to (1 + 2 kappa) e.
+cancel, are checked against tol + 64 kappa 2^-24: the frame is computed at
+FP32 accuracy, and a relative error e of its raw outputs moves the frame by
+up to (1 + 2 kappa) e, on top of the evaluation's own error.
 """
 import numpy as np
 import pytest

@@ -1,14 +1,14 @@
-"""FP8 (E4M3) decoder path: per-layer weight scales absmax/448, static
-per-layer activation scales from a calibration batch, FP32 accumulation and
-FP32 biases (beyond the paper, which stops at FP16 parameters).
+"""FP8 (E4M3) decoder path (beyond the paper, which stops at FP16 parameters,
+Sec. 5.2): the hidden -> hidden layers -- most of the decoder's MACs -- have
+E4M3 weights with a power-of-two per-layer scale; their input activations
+enter as two E4M3 code sets (hi = E4M3(x / s_a), lo = E4M3(x / s_a - hi), s_a
+the power of two above the calibrated max |input| / 448), FP32 accumulation;
+the frame MLP and the first and last decoder layers as in the FP16 path.
 
-Parity: against the oracle evaluating the same E4M3 weights (quantised by the
-oracle's own encoder from the FP32 masters) with the same E4M3 rounding of
-every decoder input, codes decided in FP32 -- what FP8 inference computes --
-within 3e-2 (the stated FP8 bound), with the error spread checked far tighter.
-Where an activation lies within FP32 accumulation error of an E4M3 rounding
-midpoint, either neighbour is a correct result (oracle alternatives).  The
-error against the oracle with unrounded activations is reported."""
+Parity: against the oracle evaluating the same parameter values (params=
+"fp8": those E4M3 weights, binary16 elsewhere) with FP64 activations, within
+the stated FP8 bound 3e-2 at the maximum (kappa <= 50; conditioning-aware
+beyond).  The error against the FP32 masters is reported."""
 import numpy as np
 import pytest
 
@@ -57,20 +57,17 @@ def _fp8_material(ctx, w, scales, **kw):
 def _check_fp8(oracle, w, scales, g, filt=0, addr=0, label="fp8", q=None):
     m = w["model"]
     q = w["queries"] if q is None else q
-    emu = oracle.Model(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"], filter=filt, address=addr,
-                       params="fp8", act_round=oracle.ROUND_FP8, act_scale=scales)
-    alts = oracle.eval_alternatives(emu, q)[0]
-    kappa = oracle.frame_condition(emu, q)
-    ok, st = oracle.parity(g, alts, kappa, TOL_F8)
-    nominal = oracle.relative_error(g, alts[:, 0])
-    print(f"{label}: vs E4M3-operand oracle max {st['max_rel']:.3e} mean {st['mean_rel']:.3e} "
-          f"(nominal only: max {nominal[0]:.3e}), ill-conditioned {st['ill_conditioned']}/{st['n']}")
+    om = oracle.Model(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"], filter=filt, address=addr,
+                      params="fp8")
+    o = oracle.eval(om, q)
+    kappa = oracle.frame_condition(om, q)
+    ok, st = oracle.parity(g, o, kappa, TOL_F8)
+    print(f"{label}: vs oracle (E4M3 hidden weights, FP64 activations) max {st['max_rel']:.3e} "
+          f"(well-conditioned {st['max_rel_well_conditioned']:.3e}) mean {st['mean_rel']:.3e}, "
+          f"ill-conditioned {st['ill_conditioned']}/{st['n']}")
     assert ok, st
-    # the spread: all but a handful of queries agree to FP32-accumulation level
-    tau = np.sqrt(np.mean(alts[:, 0] ** 2))
-    r = np.nanmin((np.abs(g[:, None, :] - alts) / np.maximum(np.abs(alts[:, :1, :]), tau)).max(axis=2), axis=1)
-    assert np.quantile(r, 0.999) <= 1e-4, np.quantile(r, 0.999)
-    return emu
+    assert st["max_rel_well_conditioned"] <= TOL_F8
+    return om
 
 
 def test_fp8_sweep_workload(gctx, oracle, w3s, calib):
@@ -82,18 +79,16 @@ def test_fp8_sweep_workload(gctx, oracle, w3s, calib):
     gctx.check()
     _check_fp8(oracle, w3s, calib, g, label="fp8 3840x68")
     m = w3s["model"]
-    exact = oracle.eval(oracle.Model(w3s["W0"], w3s["H0"], w3s["L"], w3s["pyramid"], m["frame"], m["decoder"],
-                                     params="fp8"), w3s["queries"])
     master = oracle.eval(oracle.Model(w3s["W0"], w3s["H0"], w3s["L"], w3s["pyramid"], m["frame"], m["decoder"]),
                          w3s["queries"])
-    e1 = oracle.relative_error(g, exact)
     e2 = oracle.relative_error(g, master)
-    print(f"fp8 vs unrounded-activation oracle (E4M3 weights): max {e1[0]:.3e} mean {e1[1]:.3e}")
     print(f"fp8 vs FP32-master oracle: max {e2[0]:.3e} mean {e2[1]:.3e}")
     print("weight scales", list(info.fp8_weight_scale)[:3])
-    # the weight scales the library reports are the oracle's
-    for (Wl, _), s in zip(m["decoder"], list(info.fp8_weight_scale)[:3]):
-        assert s == oracle.quantize_e4m3_layer(Wl)[0]
+    # the weight scale the library reports for the E4M3 layer is the oracle's;
+    # the FP16 layers report none
+    sc = list(info.fp8_weight_scale)[:3]
+    assert sc[1] == oracle.quantize_e4m3_layer(m["decoder"][1][0])[0]
+    assert sc[0] == 0.0 and sc[2] == 0.0
 
 
 @pytest.mark.parametrize("filt", [0, 1])
@@ -106,16 +101,17 @@ def test_fp8_filters_and_addressing(gctx, oracle, w3s, calib, filt, addr):
     _check_fp8(oracle, w3s, calib, g, filt=filt, addr=addr, label=f"fp8 filt={filt} addr={addr}", q=q)
 
 
-@pytest.mark.parametrize("H", [16, 32, 64])
-@pytest.mark.parametrize("frame", [False, True])
+@pytest.mark.parametrize("H,NH", [(16, 2), (32, 2), (64, 2), (64, 3)])
+@pytest.mark.parametrize("frame", ["none", "mlp", "paper"])
 @pytest.mark.parametrize("latent", ["f16", "f32"])
-def test_fp8_shapes(gctx, oracle, H, frame, latent):
+def test_fp8_shapes(gctx, oracle, H, NH, frame, latent):
     from paper_2305_02678_gb300 import binding as B
-    rng = W.rng_streams(500 + H + 2 * frame, 3)
+    rng = W.rng_streams(500 + H + 7 * NH + 2 * len(frame), 3)
     W0 = H0 = 256
     L = 9
     pyr = W.make_pyramid(rng[0], W0, H0, L, dtype=np.float16 if latent == "f16" else np.float32)
-    model = W.make_model(rng[1], (14, H, H, 3), (8, 16, 6) if frame else None)
+    fw = {"none": None, "mlp": (8, 16, 6), "paper": (8, 12)}[frame]
+    model = W.make_model(rng[1], (20 if frame == "paper" else 14,) + (H,) * NH + (3,), fw)
     q = W.uniform_queries(rng[2], 20000, 8.0)
     w = dict(W0=W0, H0=H0, L=L, pyramid=pyr, model=model, queries=q)
     om = oracle.Model(W0, H0, L, pyr, model["frame"], model["decoder"])
@@ -124,7 +120,7 @@ def test_fp8_shapes(gctx, oracle, H, frame, latent):
     mat = gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_FP8, act_scale=scales)
     g = mat.eval(to_device(q)).cpu().numpy()
     mat.destroy()
-    _check_fp8(oracle, w, scales, g, label=f"fp8 H={H} frame={frame} {latent}")
+    _check_fp8(oracle, w, scales, g, label=f"fp8 {NH}x{H} frame={frame} {latent}")
 
 
 def test_fp8_ragged_and_multi(gctx, oracle, w3s, calib):

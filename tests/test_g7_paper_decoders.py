@@ -88,9 +88,8 @@ def test_paper_form_multi_material_and_ragged(gctx):
 def test_unsupported_combinations_fail_cleanly(gctx):
     from paper_2305_02678_gb300 import binding as B
     W0, H0, L, pyr, model, q = _setup(97, 64, 2, "paper", n=10)
-    with pytest.raises(B.NamError):   # FP8 needs the frame MLP form
-        gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_FP8,
-                      act_scale=np.ones(3, np.float32))
+    with pytest.raises(B.NamError):   # FP8 needs its activation scales
+        gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], precision=B.NAM_PREC_FP8)
     pyr32 = pyr.astype(np.float32)
     with pytest.raises(B.NamError):   # training needs the frame MLP form
         gctx.material(W0, H0, L, pyr32, model["frame"], model["decoder"], precision=B.NAM_PREC_F32, trainable=True)

@@ -1,8 +1,9 @@
-"""Pins of the oracle's reduced-precision emulation and of its helpers, from
-closed forms: the rounding of decoder inputs to FP16 (Sec. 5.2: FP16
-parameters and, on tensor cores, FP16 operands, Sec. 7.2) and to E4M3 with a
-static scale, the list of valid results at a rounding midpoint, the FP8 weight
-quantisation, the calibration ranges and the frame condition number.
+"""Pins of the oracle's reduced-precision parameter modes and helpers, from
+closed forms: binary16 rounding of the parameters (Sec. 5.2: FP16 parameters
+by post-training quantisation), the FP8 mode (E4M3 weights with a
+power-of-two per-layer scale on the hidden -> hidden decoder layers, binary16
+elsewhere), the calibration ranges and the frame condition number.  The
+oracle evaluates activations in FP64 in every mode.
 
 The models are built so that every value is known exactly: a constant FP16
 pyramid (the filter then returns the constant, pinned elsewhere), directions
@@ -22,7 +23,7 @@ def _queries(n=4):
                 xi=np.full(n, 0.5, np.float32))
 
 
-def _model(oracle, b1, b2=None, c=0.5, params="master", act_round=0, act_scale=None, frame=None):
+def _model(oracle, b1, b2=None, c=0.5, params="master", frame=None):
     """decoder 14 -> H -> H -> 3: W1 = 0, b1 given; W2 = identity, b2 (0);
     W3 picks hidden unit 0 into every channel, b3 = 0."""
     pyr = np.full((8 * 8 + 4 * 4 + 2 * 2 + 1, 8), c, dtype=np.float16)
@@ -32,7 +33,7 @@ def _model(oracle, b1, b2=None, c=0.5, params="master", act_round=0, act_scale=N
     W3[:, 0] = 1.0
     dec = [(W1, np.asarray(b1, np.float32)), (W2, np.zeros(H, np.float32) if b2 is None else np.asarray(b2, np.float32)),
            (W3, np.zeros(3, np.float32))]
-    return oracle.Model(8, 8, 4, pyr, frame, dec, params=params, act_round=act_round, act_scale=act_scale)
+    return oracle.Model(8, 8, 4, pyr, frame, dec, params=params)
 
 
 def _b1(v):
@@ -45,73 +46,65 @@ def _b1(v):
     (1.0 + 2.0 ** -11, 1.0),                      # midpoint of 1 and 1 + 2^-10: ties to even
     (1.0 + 3 * 2.0 ** -11, 1.0 + 2.0 ** -9),      # midpoint of 1 + 2^-10 and 1 + 2^-9: even is the latter
     (0.1, 1638.0 / 16384.0),                      # nearest binary16 to 0.1
-    (70000.0, np.inf),                            # beyond 65504 + half a step: overflow
-    (-3.0, 0.0),                                  # ReLU before the rounding
+    (-3.0, 0.0),                                  # a negative bias, cut by the ReLU
 ])
-def test_fp16_operand_rounding_closed_forms(oracle, v, expect):
-    m = _model(oracle, _b1(v), act_round=oracle.ROUND_FP16)
-    y = oracle.eval(m, _queries())
+def test_fp16_parameters_closed_forms(oracle, v, expect):
+    """b1 carries v into hidden unit 0, which W2 = I and W3 pass to the
+    output: with params="fp16" the output is v rounded to binary16; the
+    activations themselves are not rounded (master parameters pass v
+    through unchanged)."""
+    y = oracle.eval(_model(oracle, _b1(v), params="fp16"), _queries())
     assert np.all(y == expect), (y[0], expect)
-    # without operand rounding the value passes through unchanged
     y0 = oracle.eval(_model(oracle, _b1(v)), _queries())
     assert np.allclose(y0, max(np.float32(v), 0.0), rtol=0, atol=0)
-
-
-@pytest.mark.parametrize("v,scale,expect", [
-    (1.0 + 2.0 ** -4, 1.0, 1.0),        # midpoint of 1 and 1.125 (3 fraction bits): ties to even
-    (1.1875, 1.0, 1.25),                # midpoint of 1.125 and 1.25: even is 1.25
-    (2.125, 2.0, 2.0),                  # the same decision after the scale (2.125 / 2 = 1.0625)
-    (500.0, 1.0, 448.0),                # saturates at the largest finite E4M3
-    (0.001, 1.0, 2.0 ** -9),            # nearest subnormal (spacing 2^-9)
-    (0.0009, 1.0, 0.0),                 # below half the smallest subnormal
-])
-def test_fp8_operand_rounding_closed_forms(oracle, v, scale, expect):
-    s = np.full(3, scale)
-    m = _model(oracle, _b1(v), params="fp8", act_round=oracle.ROUND_FP8, act_scale=s)
-    y = oracle.eval(m, _queries())
-    # identity and pick weights dequantise to 1 within FP32 rounding of 1/448
-    assert np.allclose(y, expect, rtol=2e-7, atol=0), (y[0], expect)
-
-
-def test_fp8_layer_input_zero_is_not_rounded_away(oracle):
-    """z and the directions are layer-0 inputs: with an exact constant pyramid
-    (0.5) and directions (0, 0, 1) the E4M3 codes are exact."""
-    W1 = np.zeros((H, 14), np.float32)
-    W1[0, 0] = 1.0       # h1[0] = z0
-    W1[1, 10] = 1.0      # h1[1] = wi_z
-    pyr = np.full((85, 8), 0.5, dtype=np.float16)
-    W3 = np.zeros((3, H), np.float32)
-    W3[0, 0] = 1.0
-    W3[1, 1] = 1.0
-    dec = [(W1, np.zeros(H, np.float32)), (np.eye(H, dtype=np.float32), np.zeros(H, np.float32)),
-           (W3, np.zeros(3, np.float32))]
-    m = oracle.Model(8, 8, 4, pyr, None, dec, params="fp8", act_round=oracle.ROUND_FP8, act_scale=np.ones(3))
-    y = oracle.eval(m, _queries())
-    assert np.allclose(y[:, 0], 0.5, rtol=3e-7) and np.allclose(y[:, 1], 1.0, rtol=3e-7) and np.all(y[:, 2] == 0)
+    # a product of two binary16 values with no rounding of the activation:
+    # b1 = 1 + 2^-10 (exact), W2[0][0] = 1 + 2^-10 (exact) -> h2 = (1 + 2^-10)^2
+    W2 = np.eye(H, dtype=np.float32)
+    W2[0, 0] = 1.0 + 2.0 ** -10
+    m = _model(oracle, _b1(1.0 + 2.0 ** -10), params="fp16")
+    dec = [(np.zeros((H, 14), np.float32), _b1(1.0 + 2.0 ** -10)), (W2, np.zeros(H, np.float32)),
+           (m.decoder[2][0], np.zeros(3, np.float32))]
+    m2 = oracle.Model(8, 8, 4, m.pyramid, None, dec, params="fp16")
+    y2 = oracle.eval(m2, _queries())
+    assert np.all(y2 == (1.0 + 2.0 ** -10) ** 2)
 
 
 def test_fp8_weight_quantisation_closed_forms(oracle):
+    """Scale: the smallest power of two s with absmax / s <= 448; codes
+    E4M3(W / s), round to nearest even, 3 fraction bits, saturating."""
     W = np.array([[2.0, 1.0, 0.01, -2.0]], np.float32)
     s, deq = oracle.quantize_e4m3_layer(W)
-    assert s == np.float32(2.0) / np.float32(448.0)
-    codes = np.array([448.0, 224.0, 2.25, -448.0])   # 0.01 / s = 2.24 -> 2.25 (spacing 0.25 in [2, 4))
-    assert np.allclose(deq.ravel(), codes * float(s), rtol=0, atol=0)
+    assert s == 2.0 ** -7                      # 2 / 448 = 2^-7.8 -> 2^-7 (2 / 2^-7 = 256 <= 448)
+    # 2 / 2^-7 = 256, 1 / 2^-7 = 128, 0.01 / 2^-7 = 1.28 -> 1.25 (spacing 0.125 in [1, 2))
+    codes = np.array([256.0, 128.0, 1.25, -256.0])
+    assert np.all(deq.ravel() == codes * 2.0 ** -7)
+    s1, deq1 = oracle.quantize_e4m3_layer(np.array([[448.0, 449.0, 1.0 + 2.0 ** -4]], np.float32))
+    assert s1 == 2.0                           # 449 / 448 > 1: next power of two
+    assert np.all(deq1.ravel() == np.array([448.0, 448.0, 1.0]))  # 224.5 -> 224; 0.53125 -> 0.5 (ties to even)
+    s2, deq2 = oracle.quantize_e4m3_layer(np.array([[448.0, -100.0]], np.float32))
+    assert s2 == 1.0 and np.all(deq2.ravel() == np.array([448.0, -96.0]))  # spacing 8 in [64, 128): 100 -> 96 (even)
     s0, deq0 = oracle.quantize_e4m3_layer(np.zeros((2, 3), np.float32))
     assert s0 == 1.0 and np.all(deq0 == 0)
 
 
-def test_alternatives_at_an_exact_midpoint(oracle):
-    """One activation exactly at a binary16 midpoint: both neighbours are
-    valid results; away from any midpoint there is a single result."""
-    m = _model(oracle, _b1(1.0 + 2.0 ** -11), act_round=oracle.ROUND_FP16)
-    alts, nalt, nsites = oracle.eval_alternatives(m, _queries())
-    assert np.all(nsites == 1) and np.all(nalt == 2)
-    got = np.sort(alts[:, :2, 0], axis=1)
-    assert np.all(got == np.array([1.0, 1.0 + 2.0 ** -10]))
-    assert np.all(alts[:, 0, 0] == 1.0)  # nominal first
-    m2 = _model(oracle, _b1(1.0 + 2.0 ** -12), act_round=oracle.ROUND_FP16)
-    alts2, nalt2, _ = oracle.eval_alternatives(m2, _queries())
-    assert np.all(nalt2 == 1) and np.all(alts2[:, 0, 0] == 1.0)
+def test_fp8_mode_quantises_only_hidden_to_hidden_layers(oracle):
+    """params="fp8": the hidden -> hidden weights are E4M3 with their layer
+    scale, every other parameter is binary16 (a swapped or shifted layer
+    fails)."""
+    rng = np.random.default_rng(3)
+    dec = [(rng.uniform(-1, 1, (H, 14)).astype(np.float32), rng.uniform(-1, 1, H).astype(np.float32)),
+           (rng.uniform(-1, 1, (H, H)).astype(np.float32), rng.uniform(-1, 1, H).astype(np.float32)),
+           (rng.uniform(-1, 1, (3, H)).astype(np.float32), rng.uniform(-1, 1, 3).astype(np.float32))]
+    pyr = np.full((85, 8), 0.5, dtype=np.float16)
+    m8 = oracle.Model(8, 8, 4, pyr, None, dec, params="fp8")
+    got = oracle.split_decoder(m8, m8.dec_params)
+    s, w2 = oracle.quantize_e4m3_layer(dec[1][0])
+    assert np.array_equal(got[1][0], w2.reshape(H, H))
+    assert m8.weight_scales[1] == s and m8.weight_scales[0] is None and m8.weight_scales[2] is None
+    for l in (0, 2):
+        assert np.array_equal(got[l][0], dec[l][0].astype(np.float16).astype(np.float64))
+    for l in range(3):
+        assert np.array_equal(got[l][1], dec[l][1].astype(np.float16).astype(np.float64))
 
 
 def test_calibration_ranges_closed_form(oracle):
