@@ -16,7 +16,7 @@ stream's p50/p99 frame latency, the FP64 oracle on the host cores
 (cpu_baseline) and the clocks seen while timing.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--no-serve] [--serve-frames F] [--no-sweep]
+                  [--no-serve] [--serve-frames F] [--serve-repeats R] [--no-sweep]
 """
 from __future__ import annotations
 
@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-frames", type=int, default=720)
+    ap.add_argument("--serve-repeats", type=int, default=4)
+    ap.add_argument("--serve-trace", default=None, help="write every served frame's timeline (.npz) here")
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-sweep4k", action="store_true")
@@ -524,7 +526,7 @@ def run_ours(args):
     # host and device allocations behind in this process) --------------------
     serving = None
     if not args.no_serve and rank == 0:
-        serving = run_serving(local, args.serve_frames)
+        serving = run_serving(local, args.serve_frames, repeats=args.serve_repeats, trace=args.serve_trace)
     # ---- precision sweep at 3840x2160 ---------------------------------------
     sweep4k, outs4k = None, None
     if not args.no_sweep4k:
@@ -689,9 +691,9 @@ def run_binned(ctx, dev, stream, flush, w, dq, n, args, n_mat=16):
                                         max(3, args.steps // 2), 2, flush, stream))
     reps = max(3, args.steps // 2)
     # per-tile selection on the same per-pixel ids: every tile holds more
-    # than 8 of the 16 materials, so every query takes the divergent path
+    # than 8 of the 16 materials, so every query goes through binning
     t_sel_pp = statistics.fmean(time_launches(lambda: B.nam_eval_select(ctx.h, handles, dq, ids, n, o, stream, 0),
-                                              3, 1, flush, stream))
+                                              reps, 2, flush, stream))
     # screen regions: the pixels of the 1920x1080 frame (queries in row-major
     # pixel order) take the material of the nearest of 16 random sites, so a
     # 128-pixel run is mixed only where a region boundary crosses it
@@ -723,15 +725,15 @@ def run_binned(ctx, dev, stream, flush, w, dq, n, args, n_mat=16):
                     "plus the chunked tensor-core launch, whose CTAs restage weights when a chunk's material "
                     "changes",
             "select": {
-                "per_pixel_ms": round(t_sel_pp, 4),
+                "per_pixel_ms": round(t_sel_pp, 4), "per_pixel_vs_binned": round(t_sel_pp / t, 3),
                 "regions_workload": f"{n_mat} screen regions (nearest of {n_mat} random sites), "
                                     f"{coherent:.3f} of the 128-query tiles coherent, "
                                     f"{passes:.3f} tensor-core passes per tile",
                 "regions_select_ms": round(t_sel, 4), "regions_binned_ms": round(t_bin_reg, 4),
                 "note": "nam_eval_select, in place: a 128-query tile with k <= 8 materials runs as k masked "
-                        "tensor-core passes (one per material), a tile with more on the divergent path (one query "
-                        "per thread, FP32, each thread's own material weights); three small passes build the "
-                        "pass table"}}
+                        "tensor-core passes (one per material); the queries of tiles with more are binned by "
+                        "material (the binning passes limited to those tiles) and run in coherent chunks; three "
+                        "small passes build the pass table"}}
 
 
 def run_scene(ctx, dev, stream, args, width=1920, height=1080):
@@ -1054,13 +1056,39 @@ def run_albedo_head(ctx, dev, stream, steps, batch=131072, pool=4, n_test=64, W0
                     "error against a 96 x 96 midpoint quadrature of Eq. 2 at lod 0"}
 
 
-def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_frames=None):
+def _host_cpu_counters():
+    """Process context switches and, where the container exposes them, the
+    cgroup's CPU-quota throttling counters (cgroup v2 cpu.stat)."""
+    import resource
+    ru = resource.getrusage(resource.RUSAGE_SELF)
+    out = {"voluntary_csw": ru.ru_nvcsw, "involuntary_csw": ru.ru_nivcsw}
+    try:
+        with open("/sys/fs/cgroup/cpu.stat") as f:
+            for line in f:
+                k, v = line.split()
+                if k in ("nr_periods", "nr_throttled", "throttled_usec"):
+                    out[k] = int(v)
+        with open("/sys/fs/cgroup/cpu.max") as f:
+            out["cpu_max"] = f.read().strip()
+    except OSError:
+        pass
+    return out
+
+
+def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_frames=None, repeats=4,
+                lead_s=0.1, trace=None):
     """Serving stream: Poisson frame arrivals at `rate`/s, resolutions drawn
     from 720p/1080p/1440p/2160p, 16 FP16 materials (own 2048^2 x 8 pyramid
     and 14-64-64-3 decoder each), one material per 64x64 tile drawn
-    uniformly, frames admitted under a 40 GB budget.  Frames go through
-    nam_submit with pinned host inputs; latency = finish - arrival.  The first
-    `warmup_frames` (default 10%) are excluded from the percentiles."""
+    uniformly, frames admitted under a 40 GB budget, `repeats` streams back to
+    back in one context.  Frames go through nam_submit with pinned host inputs
+    up to `lead_s` ahead of their arrival times; the library holds each until
+    it arrives, so the driver's own timing does not enter the latency
+    (finish - arrival).  The first `warmup_frames` (default 10%) of each
+    stream are excluded from its percentiles.  Every frame's timeline is
+    split into: release (arrival -> admission), gpu_wait (start of enqueue ->
+    first copy on the device), h2d, kernel, d2h and observe (RGB in host
+    memory -> completion seen by the serving thread)."""
     import ctypes as C
 
     import torch
@@ -1072,7 +1100,7 @@ def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_
     if warmup_frames is None:
         warmup_frames = max(1, n_frames // 10)
     total = n_frames + warmup_frames
-    rngs = W.rng_streams(W.SEEDS[5], 2 * n_mat + 3)
+    rngs = W.rng_streams(W.SEEDS[5], 2 * n_mat + 3 + repeats)
     ctx = Context(device, hbm_budget_bytes=budget, serve_streams=4, serve_queue_depth=4096)
     mats = []
     for k in range(n_mat):
@@ -1088,24 +1116,45 @@ def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_
         out = torch.empty((wd * ht, 3), dtype=torch.float32).pin_memory()
         tiles = W.tile_ranges(wd, ht)
         frames.append((wd * ht, pinned, out, tiles))
-    rng = rngs[2 * n_mat + 1]
+    runs = [_serving_stream(B, C, ctx, mats, mat_arr, frames, rngs[2 * n_mat + 1 + r], total, warmup_frames, rate,
+                            n_mat, lead_s) for r in range(repeats)]
+    for m in mats:
+        m.destroy()
+    ctx.close()
+    if trace:
+        # columns: resolution index, arrival, submit, admit, start, enqueued, gpu begin, kernel begin, kernel end,
+        # gpu end, finish (s), queries, slot, in flight at admission; one array per stream
+        np.savez(trace, **{f"run{r}": x.pop("_rows") for r, x in enumerate(runs)})
+    for x in runs:
+        x.pop("_rows", None)
+    out = dict(runs[0])
+    out.update({"frames": n_frames, "warmup_frames": warmup_frames, "rate_fps": rate, "materials": n_mat,
+                "budget_bytes": budget, "repeats": repeats, "submit_lead_ms": lead_s * 1e3,
+                "resident_bytes_materials": int(sum(m.info.resident_bytes for m in mats)),
+                "p50_frame_ms_runs": [r["p50_frame_ms"] for r in runs],
+                "p99_frame_ms_runs": [r["p99_frame_ms"] for r in runs],
+                "p99_spread": round(max(r["p99_frame_ms"] for r in runs) / min(r["p99_frame_ms"] for r in runs), 3),
+                "runs": runs[1:],
+                "latency": "finish - scheduled Poisson arrival on the nam_now() clock; host->device copy of the "
+                           "frame's inputs, kernel and device->host copy of its RGB included"})
+    return out
+
+def _serving_stream(B, C, ctx, mats, mat_arr, frames, rng, total, warmup_frames, rate, n_mat, lead_s):
+    """One Poisson stream of `total` frames through nam_submit; see run_serving."""
     arrivals = np.cumsum(rng.exponential(1.0 / rate, total))
-    which = rng.integers(0, len(res), total)
-    # every frame's tile -> material table, built before the stream starts so
-    # that submission keeps up with the arrival times
+    which = rng.integers(0, len(frames), total)
+    # every frame's tile -> material table, built before the stream starts
     tables = []
     for i in range(total):
-        tiles = frames[which[i]][3]
-        st = np.array(tiles, dtype=np.int64)
-        arr = np.zeros(len(tiles), dtype=[("start", "<i8"), ("count", "<i4"), ("material", "<i4")])
-        arr["start"], arr["count"], arr["material"] = st[:, 0], st[:, 1], rng.integers(0, n_mat, len(tiles))
+        st = np.array(frames[which[i]][3], dtype=np.int64)
+        arr = np.zeros(len(st), dtype=[("start", "<i8"), ("count", "<i4"), ("material", "<i4")])
+        arr["start"], arr["count"], arr["material"] = st[:, 0], st[:, 1], rng.integers(0, n_mat, len(st))
         tables.append(arr)
-    keep = []
+    cpu0 = _host_cpu_counters()
     tickets = []
-    submitted = []
-    t0 = B.nam_now() + 0.05
+    t0 = B.nam_now() + lead_s + 0.02
     for i in range(total):
-        n, pinned, out, tiles = frames[which[i]]
+        n, pinned, out, _ = frames[which[i]]
         items = tables[i]
         f = B.nam_frame()
         f.n_queries = n
@@ -1117,48 +1166,51 @@ def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_
         f.rgb_out = out.data_ptr()
         f.flags = 0
         f.arrival_s = t0 + arrivals[i]
-        keep.append(items)
-        now = B.nam_now()
-        if f.arrival_s > now:
-            time.sleep(f.arrival_s - now)
+        ahead = f.arrival_s - lead_s - B.nam_now()
+        if ahead > 0:
+            time.sleep(ahead)
         tickets.append(B.nam_submit(ctx.h, f))
-        submitted.append(B.nam_now())
     failed = 0
     rows = []
     for i, t in enumerate(tickets):
         st, fs = B.nam_wait(ctx.h, t, 60_000_000_000)
         failed += st != 0
         if i >= warmup_frames and st == 0:
-            rows.append((which[i], fs.arrival_s, fs.admit_s, fs.start_s, fs.finish_s, fs.n_queries, submitted[i]))
+            rows.append((which[i], fs.arrival_s, fs.submit_s, fs.admit_s, fs.start_s, fs.enqueued_s, fs.gpu_begin_s,
+                         fs.gpu_kernel_begin_s, fs.gpu_kernel_end_s, fs.gpu_end_s, fs.finish_s, fs.n_queries,
+                         fs.slot, fs.in_flight_at_admit))
+    cpu1 = _host_cpu_counters()
     a = np.array(rows, dtype=np.float64)
-    lat = (a[:, 4] - a[:, 1]) * 1e3
-    span = a[:, 4].max() - a[:, 1].min()
+    arr_s, sub_s, adm_s, sta_s, enq_s, gb_s, kb_s, ke_s, ge_s, fin_s = (a[:, k] for k in range(1, 11))
+    lat = (fin_s - arr_s) * 1e3
+    span = fin_s.max() - arr_s.min()
+    timed = gb_s > 0
+    parts = {"release": adm_s - arr_s, "enqueue": enq_s - sta_s, "gpu_wait": gb_s - sta_s, "h2d": kb_s - gb_s,
+             "kernel": ke_s - kb_s, "d2h": ge_s - ke_s, "observe": fin_s - ge_s}
 
     def pct(x, p):
         return round(float(np.percentile(x, p)), 3) if len(x) else None
 
+    breakdown = {k: {"p50_ms": pct(v[timed] * 1e3, 50), "p99_ms": pct(v[timed] * 1e3, 99),
+                     "max_ms": round(float(v[timed].max() * 1e3), 3) if timed.any() else None}
+                 for k, v in parts.items()}
+    slow = np.argsort(lat)[-5:]
     by_res = {}
-    for k, (wd, ht) in enumerate(res):
+    for k, (n, *_rest) in enumerate(frames):
         sel = a[:, 0] == k
-        by_res[f"{wd}x{ht}"] = {"frames": int(sel.sum()), "p50_ms": pct(lat[sel], 50), "p99_ms": pct(lat[sel], 99)}
-    out = {"frames": n_frames, "warmup_frames": warmup_frames, "failed": int(failed), "rate_fps": rate,
-           "p50_frame_ms": pct(lat, 50), "p99_frame_ms": pct(lat, 99),
-           "queue_ms_p99": pct((a[:, 2] - a[:, 1]) * 1e3, 99), "run_ms_p50": pct((a[:, 4] - a[:, 3]) * 1e3, 50),
-           "run_ms_p99": pct((a[:, 4] - a[:, 3]) * 1e3, 99),
-           "submit_late_ms_p99": pct((a[:, 6] - a[:, 1]) * 1e3, 99),
-           "slowest_frames_ms": [[round(float(x), 3) for x in ((r[6] - r[1]) * 1e3, (r[2] - r[6]) * 1e3,
-                                                            (r[4] - r[3]) * 1e3, (r[4] - r[1]) * 1e3)]
-                                 for r in a[np.argsort(a[:, 4] - a[:, 1])[-5:]]],
-           "evals_per_s": round(float(a[:, 5].sum() / span), 1),
-           "offered_evals_per_s": round(rate * float(np.mean([r[0] * r[1] for r in res])), 1),
-           "by_resolution": by_res, "materials": n_mat, "budget_bytes": budget,
-           "resident_bytes_materials": int(sum(m.info.resident_bytes for m in mats)),
-           "latency": "finish - scheduled Poisson arrival on the nam_now() clock; host->device copy of the frame's "
-                      "inputs, kernel and device->host copy of its RGB included"}
-    for m in mats:
-        m.destroy()
-    ctx.close()
-    return out
+        by_res[str(n)] = {"frames": int(sel.sum()), "p50_ms": pct(lat[sel], 50), "p99_ms": pct(lat[sel], 99)}
+    return {"failed": int(failed), "p50_frame_ms": pct(lat, 50), "p99_frame_ms": pct(lat, 99),
+            "max_frame_ms": round(float(lat.max()), 3),
+            "breakdown": breakdown,
+            "slowest_frames": [{"queries": int(a[j, 11]), "slot": int(a[j, 12]), "in_flight_at_admit": int(a[j, 13]),
+                                "submit_ahead_ms": round(float((arr_s[j] - sub_s[j]) * 1e3), 3),
+                                **{k: round(float(v[j] * 1e3), 3) for k, v in parts.items()},
+                                "total_ms": round(float(lat[j]), 3)} for j in slow],
+            "submit_ahead_ms_min": round(float((arr_s - sub_s).min() * 1e3), 3),
+            "evals_per_s": round(float(a[:, 11].sum() / span), 1),
+            "offered_evals_per_s": round(rate * float(np.mean([f[0] for f in frames])), 1),
+            "by_queries": by_res, "_rows": a,
+            "host_cpu": {k: (cpu1[k] - cpu0[k]) if isinstance(cpu0.get(k), int) else cpu1[k] for k in cpu1}}
 
 
 def _oracle_rate(O, om, q, nthreads, seconds, k0=16384):

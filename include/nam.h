@@ -341,20 +341,21 @@ nam_status nam_eval_binned(nam_ctx* ctx, const nam_material* mats, int32_t n_mat
  *       SIMT divergence runs a warp once per branch target, at tensor-core
  *       speed); every such query's result is bitwise that of nam_eval on its
  *       material;
- *   more  the divergent path: one query per thread, each thread reading its
- *       own material's weights from an FP32 image of the values the
- *       material's tensor-core blob holds (binary16-rounded weights and
- *       biases; FP8: E4M3 codes times their layer scale, FP32 decoder
- *       biases) and computing in FP32, so those results differ from
- *       nam_eval's by the tensor-core path's activation rounding only.
- * No query is moved: suited to ids that are coherent over runs of 128
- * queries (screen tiles of a few surfaces); nam_eval_binned suits incoherent
- * ids.  Arguments, id checks (an id outside [0, n_materials) leaves that
- * query's rgb_out untouched and makes nam_check_device_error report
- * NAM_ERR_DEVICE_ASSERT) and material requirements as nam_eval_binned.
- * Temporary device memory (≈ 40 bytes per tile plus at most 16 bytes per
- * query, and 24 bytes per material) comes from the context's stream-ordered
- * pool. */
+ *   more  the queries of all such tiles are binned by material (the
+ *       passes of nam_eval_binned, limited to those tiles: the reordering
+ *       the paper's renderer gets from SER, Sec. 7.3) and run in
+ *       material-coherent 128-query chunks, then written back in place;
+ *       every such query's result is likewise bitwise that of nam_eval on
+ *       its material.
+ * So every result equals nam_eval's on the query's material; only the cost
+ * differs: coherent ids (screen tiles of a few surfaces) move no query,
+ * incoherent ones cost about what nam_eval_binned does.  Arguments, id
+ * checks (an id outside [0, n_materials) leaves that query's rgb_out
+ * untouched and makes nam_check_device_error report NAM_ERR_DEVICE_ASSERT)
+ * and material requirements as nam_eval_binned.  Temporary device memory
+ * (≈ 40 bytes per tile plus at most 16 bytes per query for the pass table,
+ * the binning scratch of nam_eval_binned, and 16 bytes per material) comes
+ * from the context's stream-ordered pool. */
 #define NAM_SELECT_MAX_PASSES 8
 nam_status nam_eval_select(nam_ctx* ctx, const nam_material* mats, int32_t n_materials, const nam_queries* q,
                            const int32_t* material_ids, int64_t n, float* rgb_out, void* stream, uint32_t flags);
@@ -568,14 +569,32 @@ typedef struct {
   float* rgb_out;             /* HOST [n_queries][3], written before the ticket completes */
   uint32_t flags;             /* NAM_OUT_* */
   int32_t reserved0;
-  double arrival_s;           /* arrival time on the nam_now() clock; <= 0 -> now */
+  double arrival_s;           /* arrival time on the nam_now() clock; <= 0 -> now.  A frame
+                                 whose arrival lies in the future is held in the queue
+                                 until then (a paced stream), so a caller may submit ahead
+                                 of the arrival times without its own timing mattering. */
 } nam_frame;
 
+/* Times of one frame, all in seconds on the nam_now() clock.  The gpu_* times
+ * are device timestamps (CUDA events on the frame's stream) mapped onto that
+ * clock through an anchor event the serving thread takes while the GPU is
+ * idle (error: a few microseconds); 0 where the frame never reached the GPU. */
 typedef struct {
-  double arrival_s, admit_s, start_s, finish_s;  /* nam_now() clock */
+  double arrival_s;           /* the frame's arrival (nam_frame.arrival_s) */
+  double admit_s;             /* the serving thread took it off the queue */
+  double start_s;             /* it began enqueuing the frame's work */
+  double finish_s;            /* the serving thread observed its completion */
   int64_t n_queries;
   nam_status status;          /* NAM_OK once done; an error if it failed */
-  int32_t reserved0;
+  int32_t slot;               /* stream slot that ran it (-1: none) */
+  double submit_s;            /* nam_submit was called */
+  double enqueued_s;          /* all of the frame's work was on its stream */
+  double gpu_begin_s;         /* its first copy began on the device */
+  double gpu_kernel_begin_s;  /* its kernel began (inputs resident) */
+  double gpu_kernel_end_s;    /* its kernel ended */
+  double gpu_end_s;           /* its RGB was back in host memory */
+  int32_t in_flight_at_admit; /* frames already on the GPU when it was admitted */
+  int32_t reserved1;
 } nam_frame_stats;
 
 typedef struct {
@@ -590,10 +609,10 @@ typedef struct {
 /* Seconds on a monotonic host clock shared by the serving calls. */
 double nam_now(void);
 /* Queue a frame (non-blocking).  A serving thread admits queued frames in
- * arrival order as soon as their device buffers fit in the budget and a
- * stream slot is free, so frames that arrive while others run start at once
- * and overlap with them on the GPU.  NAM_ERR_BUSY if the queue is full;
- * NAM_ERR_BUDGET if the frame alone can never fit. */
+ * submission order, each once its arrival time has come, its device buffers
+ * fit in the budget and a stream slot is free, so frames that arrive while
+ * others run start at once and overlap with them on the GPU.  NAM_ERR_BUSY
+ * if the queue is full; NAM_ERR_BUDGET if the frame alone can never fit. */
 nam_status nam_submit(nam_ctx* ctx, const nam_frame* f, nam_ticket* out);
 /* Non-blocking: *done = 1 once the frame's output is in rgb_out (or it
  * failed); fills *st if not NULL. */

@@ -108,7 +108,10 @@ class nam_frame(C.Structure):
 
 class nam_frame_stats(C.Structure):
     _fields_ = [("arrival_s", C.c_double), ("admit_s", C.c_double), ("start_s", C.c_double),
-                ("finish_s", C.c_double), ("n_queries", C.c_int64), ("status", C.c_int32), ("reserved0", C.c_int32)]
+                ("finish_s", C.c_double), ("n_queries", C.c_int64), ("status", C.c_int32), ("slot", C.c_int32),
+                ("submit_s", C.c_double), ("enqueued_s", C.c_double), ("gpu_begin_s", C.c_double),
+                ("gpu_kernel_begin_s", C.c_double), ("gpu_kernel_end_s", C.c_double), ("gpu_end_s", C.c_double),
+                ("in_flight_at_admit", C.c_int32), ("reserved1", C.c_int32)]
 
 
 class nam_stats(C.Structure):

@@ -170,7 +170,6 @@ static void free_material(nam_ctx* ctx, nam_material m) {
   DeviceGuard g(ctx->device);
   cudaFree(m->pyramid);
   cudaFree(m->blob);
-  cudaFree(m->simt);
   cudaFree(m->params);
   cudaFree(m->sampler);
   cudaFree(m->adam_m);
@@ -341,7 +340,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   m->shape = sh;
   m->pyr = pd;
   m->n_params = np;
-  size_t blob_bytes = 0, simt_bytes = 0;
+  size_t blob_bytes = 0;
   if (d->precision == NAM_PREC_F32) {
     blob_bytes = 0;  // the FP32 kernels read the master layout directly
   } else {
@@ -350,9 +349,8 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
       delete m;
       return fail(NAM_ERR_UNSUPPORTED, "no tensor-core kernel for this shape/precision");
     }
-    simt_bytes = simt_image_floats(sh) * 4;
   }
-  uint64_t resident = pyr_bytes + blob_bytes + simt_bytes + (uint64_t)np * 4 + (uint64_t)smp.size() * 4 +
+  uint64_t resident = pyr_bytes + blob_bytes + (uint64_t)np * 4 + (uint64_t)smp.size() * 4 +
                       4ull * encw.size() * 4;
   m->enc_in = d->encoder_inputs;
   m->enc_n = (int64_t)encw.size();
@@ -371,7 +369,6 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   int e = dev_alloc(ctx, &m->pyramid, pyr_bytes);
   if (!e) e = dev_alloc(ctx, (void**)&m->params, np * 4);
   if (!e && blob_bytes) e = dev_alloc(ctx, &m->blob, blob_bytes);
-  if (!e && simt_bytes) e = dev_alloc(ctx, (void**)&m->simt, simt_bytes);
   if (!e && !smp.empty()) e = dev_alloc(ctx, (void**)&m->sampler, smp.size() * 4);
   if (!e && !encw.empty()) e = dev_alloc(ctx, (void**)&m->enc, 4 * encw.size() * 4);
   if (!e && d->trainable) {
@@ -400,12 +397,6 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
       return fail(NAM_ERR_UNSUPPORTED, "weight packing failed");
     }
     e = (int)cudaMemcpy(m->blob, blob.data(), blob_bytes, cudaMemcpyHostToDevice);
-  }
-  if (!e && simt_bytes) {
-    std::vector<float> img(simt_bytes / 4);
-    pack_simt_image(sh, d->precision, nframe ? master.data() : nullptr, master.data() + nframe,
-                    m->info.fp8_weight_scale, img.data());
-    e = (int)cudaMemcpy(m->simt, img.data(), simt_bytes, cudaMemcpyHostToDevice);
   }
   if (!e && d->trainable) {
     size_t nb = (m->pyr_off + pd.texels * 8) * 4;
@@ -831,13 +822,14 @@ extern "C" nam_status nam_eval_select(nam_ctx* ctx, const nam_material* mats, in
   if (st) return st;
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  // one stream-ordered allocation: tile table, then pyramid, blob and image pointers
-  const size_t tb = (select_scratch_bytes(n) + 255) / 256 * 256;
+  // one stream-ordered allocation: tile tables and binning scratch, then
+  // pyramid and weight pointers
+  const size_t tb = (select_scratch_bytes(n, nmat, q->xi != nullptr) + 255) / 256 * 256;
   const size_t pb = (size_t)nmat * sizeof(void*);
-  std::vector<uint8_t> host(3 * pb);
+  std::vector<uint8_t> host(2 * pb);
   for (int32_t k = 0; k < nmat; ++k) {
-    const void* ptrs[3] = {mats[k]->pyramid, mats[k]->blob, mats[k]->simt};
-    for (int j = 0; j < 3; ++j) std::memcpy(host.data() + j * pb + k * sizeof(void*), &ptrs[j], sizeof(void*));
+    const void* ptrs[2] = {mats[k]->pyramid, mats[k]->blob};
+    for (int j = 0; j < 2; ++j) std::memcpy(host.data() + j * pb + k * sizeof(void*), &ptrs[j], sizeof(void*));
   }
   void* dev = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync(&dev, tb + host.size(), ctx->pool, s);
@@ -854,7 +846,6 @@ extern "C" nam_status nam_eval_select(nam_ctx* ctx, const nam_material* mats, in
   a.L.mats.weights = (const void* const*)(tab + pb);
   a.L.mats.nmat = nmat;
   a.ids = material_ids;
-  a.images = (const float* const*)(tab + 2 * pb);
   a.precision = mats[0]->desc.precision;
   a.scratch = dev;
   int le = launch_select_eval(a, s);

@@ -49,7 +49,14 @@ __device__ __forceinline__ uint32_t warp_bump(uint32_t* cnt, int m, uint32_t act
   return __shfl_sync(same, base, leader) + __popc(same & lanemask_lt());
 }
 
+// A query takes part in binning unless `tile_k` is given and its 128-query
+// tile's entry there is non-negative (a tile the selection passes handle).
+__device__ __forceinline__ bool binned_query(const int32_t* tile_k, int64_t i) {
+  return tile_k == nullptr || __ldg(tile_k + (i >> 7)) < 0;
+}
+
 __global__ void __launch_bounds__(kThreads) bin_count_kernel(const int32_t* __restrict__ ids, int64_t n, int nmat,
+                                                             const int32_t* __restrict__ tile_k,
                                                              uint32_t* __restrict__ counts, int* err) {
   extern __shared__ uint32_t cnt[];  // [nmat]
   for (int m = threadIdx.x; m < nmat; m += blockDim.x) cnt[m] = 0;
@@ -59,7 +66,7 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const int32_t* __re
   for (int64_t base = seg; base < end; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;
     int m = -1;
-    if (i < end) {
+    if (i < end && binned_query(tile_k, i)) {
       m = __ldg(ids + i);
       if (m < 0 || m >= nmat) {
         record_error(err, DEVERR_BOUNDS);
@@ -75,10 +82,11 @@ __global__ void __launch_bounds__(kThreads) bin_count_kernel(const int32_t* __re
 }
 
 // One block: cursors[m] = sum of counts before m; chunks[c] for every slot
-// c < max_chunks (a material with k queries owns ceil(k / 128) chunks).
+// c < max_chunks (a material with k queries owns ceil(k / 128) chunks);
+// *n_used = the chunks in use (the tensor-core kernel's table length).
 __global__ void __launch_bounds__(1024) bin_plan_kernel(const uint32_t* __restrict__ counts, int nmat,
                                                         uint32_t* __restrict__ cursors, Chunk* __restrict__ chunks,
-                                                        int32_t max_chunks) {
+                                                        int32_t max_chunks, int32_t* __restrict__ n_used) {
   extern __shared__ uint32_t sh[];
   uint32_t* qoff = sh;             // [nmat + 1] first query of each material
   uint32_t* coff = sh + nmat + 1;  // [nmat + 1] first chunk of each material
@@ -96,6 +104,7 @@ __global__ void __launch_bounds__(1024) bin_plan_kernel(const uint32_t* __restri
   __syncthreads();
   for (int m = threadIdx.x; m < nmat; m += blockDim.x) cursors[m] = qoff[m];
   const uint32_t used = coff[nmat];
+  if (threadIdx.x == 0) *n_used = (int32_t)used;
   for (int32_t c = threadIdx.x; c < max_chunks; c += blockDim.x) {
     Chunk ch;
     if ((uint32_t)c < used) {
@@ -136,8 +145,9 @@ constexpr int kStage = 1;
 constexpr int kDirectMaterials = 4;  // segments of at most this many materials skip the ordering
 
 __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, const int32_t* __restrict__ ids,
-                                                               int64_t n, int nmat, uint32_t* __restrict__ cursors,
-                                                               Binned out, int32_t* __restrict__ orig) {
+                                                               int64_t n, int nmat, const int32_t* __restrict__ tile_k,
+                                                               uint32_t* __restrict__ cursors, Binned out,
+                                                               int32_t* __restrict__ orig) {
   extern __shared__ uint32_t sh[];
   uint32_t* cnt = sh;               // [nmat] this segment's queries per material, then a bump counter
   uint32_t* run = sh + nmat;        // [nmat] first slot of the segment's run
@@ -152,7 +162,7 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, cons
   __syncthreads();
   for (int64_t base = seg; base < end; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;
-    int m = i < end ? __ldg(ids + i) : -1;
+    int m = i < end && binned_query(tile_k, i) ? __ldg(ids + i) : -1;
     if (m >= nmat) m = -1;
     const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
     if (m >= 0) warp_bump(cnt, m, act);
@@ -195,7 +205,7 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, cons
   if (one) {
     for (int64_t base = seg; base < end; base += blockDim.x) {
       const int64_t i = base + threadIdx.x;
-      int m = i < end ? __ldg(ids + i) : -1;
+      int m = i < end && binned_query(tile_k, i) ? __ldg(ids + i) : -1;
       if (m >= nmat) m = -1;
       const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
       if (m < 0) continue;
@@ -217,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, cons
   // stage: local position = the material's first position + its bump
   for (int64_t base = seg; base < end; base += blockDim.x) {
     const int64_t i = base + threadIdx.x;
-    int m = i < end ? __ldg(ids + i) : -1;
+    int m = i < end && binned_query(tile_k, i) ? __ldg(ids + i) : -1;
     if (m >= nmat) m = -1;
     const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
     if (m < 0) continue;
@@ -266,12 +276,16 @@ __global__ void __launch_bounds__(kThreads) unbin_kernel(const float* __restrict
 //                    SIMT divergence serialises a warp over its branch
 //                    targets, and these passes serialise a tile over its
 //                    materials the same way, at tensor-core speed;
-//   k > 8            the divergent FP32 path, one query per thread.
+//   k > 8            the tile's queries are binned by material with those of
+//                    the other such tiles (the binning passes above, limited
+//                    to them) and run in material-coherent chunks: the
+//                    reordering the paper gets from SER (Sec. 7.3), which
+//                    here costs less than any per-thread path.
 // Three passes build the pass table in tile order: per-tile material lists
 // and per-group pass counts (one warp per tile, a group = one block's eight
 // tiles), an exclusive scan of the group counts (one block, which also
 // writes the table's length for the tensor-core kernel), and the table
-// itself with the list of the tiles left to the divergent path.
+// itself; tile_k = -1 marks the tiles left to binning.
 constexpr int kTilesPerBlock = kThreads / 32;  // one tile per warp in the list pass
 constexpr int kWriteThreads = 256;             // one tile per thread in the write pass
 
@@ -339,11 +353,10 @@ __device__ __forceinline__ int32_t warp_scan(int32_t x) {
   return x;
 }
 
-// One block of 1024: block_offs = exclusive scan of block_sums; *total = sum;
-// *n_over = 0 (the write pass counts the divergent tiles there).
+// One block of 1024: block_offs = exclusive scan of block_sums; *total = sum.
 __global__ void __launch_bounds__(1024) select_scan_kernel(const int32_t* __restrict__ block_sums, int64_t nb,
                                                            int32_t* __restrict__ block_offs,
-                                                           int32_t* __restrict__ total, int32_t* __restrict__ n_over) {
+                                                           int32_t* __restrict__ total) {
   __shared__ int32_t wsum[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int32_t carry = 0;
@@ -359,21 +372,16 @@ __global__ void __launch_bounds__(1024) select_scan_kernel(const int32_t* __rest
     carry += wsum[31];
     __syncthreads();  // wsum is rewritten by the next iteration
   }
-  if (threadIdx.x == 0) {
-    *total = carry;
-    *n_over = 0;
-  }
+  if (threadIdx.x == 0) *total = carry;
 }
 
 // One thread per tile: the tile's passes at its offset (the group's offset
-// plus the passes of the group's earlier tiles), or, for a tile with more
-// materials than passes, an entry in the divergent path's tile list.
+// plus the passes of the group's earlier tiles); a tile left to binning has
+// none.
 __global__ void __launch_bounds__(kWriteThreads) select_write_kernel(const int32_t* __restrict__ tile_k,
                                                                      const int32_t* __restrict__ tile_mats,
                                                                      int64_t n, const int32_t* __restrict__ block_offs,
-                                                                     Chunk* __restrict__ passes,
-                                                                     int32_t* __restrict__ over_list,
-                                                                     int32_t* __restrict__ n_over) {
+                                                                     Chunk* __restrict__ passes) {
   const int lane = threadIdx.x & 31;
   const int64_t ntiles = (n + 127) / 128;
   const int64_t t = (int64_t)blockIdx.x * kWriteThreads + threadIdx.x;
@@ -385,12 +393,7 @@ __global__ void __launch_bounds__(kWriteThreads) select_write_kernel(const int32
     const int32_t y = __shfl_up_sync(0xffffffffu, x, o, kTilesPerBlock);
     if ((lane % kTilesPerBlock) >= o) x += y;
   }
-  if (t >= ntiles) return;
-  if (kraw < 0) {
-    over_list[atomicAdd(n_over, 1)] = (int32_t)t;
-    return;
-  }
-  if (k == 0) return;
+  if (t >= ntiles || k == 0) return;
   const int32_t o = block_offs[t / kTilesPerBlock] + x - k;
   const int64_t base = t * 128;
   const int cnt = (int)(n - base < 128 ? n - base : 128);
@@ -408,13 +411,15 @@ __global__ void __launch_bounds__(kWriteThreads) select_write_kernel(const int32
 size_t bin_scratch_bytes(int64_t n, int nmat, bool xi) {
   const size_t f = ((size_t)n * 4 + 255) / 256 * 256;
   return (xi ? 10 : 9) * f + f /* orig */ + 3 * f /* binned rgb */ + 2 * (((size_t)nmat * 4 + 255) / 256 * 256) +
-         ((size_t)max_bin_chunks(n, nmat) * sizeof(Chunk) + 255) / 256 * 256;
+         256 /* chunks in use */ + ((size_t)max_bin_chunks(n, nmat) * sizeof(Chunk) + 255) / 256 * 256;
 }
 
 int32_t max_bin_chunks(int64_t n, int nmat) { return (int32_t)((n + 127) / 128 + nmat); }
 
-int launch_bin_eval(const BinArgs& a, void* stream) {
-  cudaStream_t s = (cudaStream_t)stream;
+// The binning passes over the queries of `a` (with `tile_k`, only those of
+// the tiles whose entry is negative), the tensor-core launch over the
+// binned ranges (as many chunks as the plan fills) and the write-back.
+static int bin_eval(const BinArgs& a, const int32_t* tile_k, cudaStream_t s) {
   const int64_t n = a.n;
   const size_t f = ((size_t)n * 4 + 255) / 256 * 256;
   uint8_t* p = (uint8_t*)a.scratch;
@@ -438,6 +443,7 @@ int launch_bin_eval(const BinArgs& a, void* stream) {
   const size_t mb = ((size_t)a.nmat * 4 + 255) / 256 * 256;
   uint32_t* counts = (uint32_t*)p; p += mb;
   uint32_t* cursors = (uint32_t*)p; p += mb;
+  int32_t* n_used = (int32_t*)p; p += 256;
   Chunk* chunks = (Chunk*)p;
   const int32_t maxc = max_bin_chunks(n, a.nmat);
 
@@ -445,15 +451,15 @@ int launch_bin_eval(const BinArgs& a, void* stream) {
   if (!e) e = (int)cudaMemsetAsync(orig, 0xff, (size_t)n * 4, s);
   if (e) return e;
   const int gseg = (int)((n + kSeg - 1) / kSeg);
-  bin_count_kernel<<<gseg, kThreads, a.nmat * sizeof(uint32_t), s>>>(a.ids, n, a.nmat, counts, a.L.err);
-  bin_plan_kernel<<<1, 1024, 2 * (a.nmat + 1) * sizeof(uint32_t), s>>>(counts, a.nmat, cursors, chunks, maxc);
+  bin_count_kernel<<<gseg, kThreads, a.nmat * sizeof(uint32_t), s>>>(a.ids, n, a.nmat, tile_k, counts, a.L.err);
+  bin_plan_kernel<<<1, 1024, 2 * (a.nmat + 1) * sizeof(uint32_t), s>>>(counts, a.nmat, cursors, chunks, maxc, n_used);
   const int scatter_smem = (3 * a.nmat + (kStage + 1) * kSeg) * (int)sizeof(uint32_t);
   static std::atomic<uint64_t> scatter_attr{0};
   once_per_device(scatter_attr, [] {
     cudaFuncSetAttribute(bin_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (3 * NAM_MAX_BIN_MATERIALS + (kStage + 1) * kSeg) * (int)sizeof(uint32_t));
   });
-  bin_scatter_kernel<<<gseg, kThreads, scatter_smem, s>>>(a.L.q, a.ids, n, a.nmat, cursors, b, orig);
+  bin_scatter_kernel<<<gseg, kThreads, scatter_smem, s>>>(a.L.q, a.ids, n, a.nmat, tile_k, cursors, b, orig);
   e = (int)cudaGetLastError();
   if (e) return e;
   LaunchCommon L = a.L;
@@ -461,23 +467,27 @@ int launch_bin_eval(const BinArgs& a, void* stream) {
   L.rgb = brgb;
   L.chunks = chunks;
   L.n_chunks = maxc;
-  e = launch_material(L, a.precision, stream);
+  L.n_chunks_dev = n_used;
+  L.row_ids = nullptr;
+  e = launch_material(L, a.precision, s);
   if (e) return e;
   // one thread per slot: the scattered 12-byte writes want many in flight
   unbin_kernel<<<(int)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(brgb, orig, n, a.rgb_out);
   return (int)cudaGetLastError();
 }
 
+int launch_bin_eval(const BinArgs& a, void* stream) { return bin_eval(a, nullptr, (cudaStream_t)stream); }
+
 // Scratch of a selection launch: tile_k [ntiles], tile_mats [ntiles][8],
-// group sums and offsets [nb] each, the divergent tile list [ntiles], the
-// pass and divergent-tile counts, the pass table (at most one pass per query
-// and kSelectPasses per tile).
+// group sums and offsets [nb] each, the pass count, the pass table (at most
+// one pass per query and kSelectPasses per tile), then the binning scratch
+// of the tiles left to binning (bin_scratch_bytes).
 namespace {
 struct SelectLayout {
-  size_t tile_k, tile_mats, sums, offs, over, total, passes, bytes;
+  size_t tile_k, tile_mats, sums, offs, total, passes, bin, bytes;
   int64_t ntiles, nb, cap;
 };
-SelectLayout select_layout(int64_t n) {
+SelectLayout select_layout(int64_t n, int nmat, bool xi) {
   auto r = [](size_t b) { return (b + 255) / 256 * 256; };
   SelectLayout l;
   l.ntiles = (n + 127) / 128;
@@ -487,34 +497,33 @@ SelectLayout select_layout(int64_t n) {
   l.tile_mats = l.tile_k + r((size_t)l.ntiles * 4);
   l.sums = l.tile_mats + r((size_t)l.ntiles * kSelectPasses * 4);
   l.offs = l.sums + r((size_t)l.nb * 4);
-  l.over = l.offs + r((size_t)l.nb * 4);
-  l.total = l.over + r((size_t)l.ntiles * 4);  // [0] pass count, [1] divergent tiles
+  l.total = l.offs + r((size_t)l.nb * 4);
   l.passes = l.total + 256;
-  l.bytes = l.passes + r((size_t)l.cap * sizeof(Chunk));
+  l.bin = l.passes + r((size_t)l.cap * sizeof(Chunk));
+  l.bytes = l.bin + bin_scratch_bytes(n, nmat, xi);
   return l;
 }
 }  // namespace
 
-size_t select_scratch_bytes(int64_t n) { return select_layout(n).bytes; }
+size_t select_scratch_bytes(int64_t n, int nmat, bool xi) { return select_layout(n, nmat, xi).bytes; }
 
 int launch_select_eval(const SelectArgs& a, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = a.L.n;
   if (n == 0) return 0;
-  const SelectLayout l = select_layout(n);
+  const int nmat = a.L.mats.nmat;
+  const SelectLayout l = select_layout(n, nmat, a.L.q.xi != nullptr);
   uint8_t* p = (uint8_t*)a.scratch;
   int32_t* tile_k = (int32_t*)(p + l.tile_k);
   int32_t* tile_mats = (int32_t*)(p + l.tile_mats);
   int32_t* sums = (int32_t*)(p + l.sums);
   int32_t* offs = (int32_t*)(p + l.offs);
-  int32_t* over = (int32_t*)(p + l.over);
   int32_t* total = (int32_t*)(p + l.total);
-  int32_t* n_over = total + 1;
   Chunk* passes = (Chunk*)(p + l.passes);
-  select_tiles_kernel<<<(int)l.nb, kThreads, 0, s>>>(a.ids, n, a.L.mats.nmat, tile_k, tile_mats, sums, a.L.err);
-  select_scan_kernel<<<1, 1024, 0, s>>>(sums, l.nb, offs, total, n_over);
+  select_tiles_kernel<<<(int)l.nb, kThreads, 0, s>>>(a.ids, n, nmat, tile_k, tile_mats, sums, a.L.err);
+  select_scan_kernel<<<1, 1024, 0, s>>>(sums, l.nb, offs, total);
   select_write_kernel<<<(int)((l.ntiles + kWriteThreads - 1) / kWriteThreads), kWriteThreads, 0, s>>>(
-      tile_k, tile_mats, n, offs, passes, over, n_over);
+      tile_k, tile_mats, n, offs, passes);
   int e = (int)cudaGetLastError();
   if (e) return e;
   LaunchCommon L = a.L;
@@ -524,7 +533,16 @@ int launch_select_eval(const SelectArgs& a, void* stream) {
   L.row_ids = a.ids;
   e = launch_material(L, a.precision, stream);
   if (e) return e;
-  return launch_eval_divergent(a.L, a.images, a.ids, over, n_over, stream);
+  BinArgs b;
+  b.L = a.L;
+  b.ids = a.ids;
+  b.nmat = nmat;
+  b.n = n;
+  b.rgb_out = a.L.rgb;
+  b.precision = a.precision;
+  b.num_sms = a.L.num_sms;
+  b.scratch = p + l.bin;
+  return bin_eval(b, tile_k, s);
 }
 
 }  // namespace nam

@@ -49,16 +49,6 @@ static uint8_t e4m3_of(float x) {
   return sign | (uint8_t)(((E + 7) << 3) | m);
 }
 
-// The value of an E4M3 code: sign bit, exponent field E (bias 7), mantissa
-// m; E = 0 holds the subnormals m 2^-9.
-static float e4m3_value(uint8_t c) {
-  const int E = (c >> 3) & 15, m = c & 7;
-  const float a = E == 0 ? std::ldexp((float)m, -9) : std::ldexp(1.0f + (float)m / 8.0f, E - 7);
-  return (c & 0x80) ? -a : a;
-}
-
-float e4m3_dequant(float w, float sw) { return e4m3_value(e4m3_of(w / sw)) * sw; }
-
 // The smallest power of two s with amax / s <= 448 (1 for amax = 0): the
 // scale under which the largest value maps into the E4M3 range and dividing
 // by s is exact.

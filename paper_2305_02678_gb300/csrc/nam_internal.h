@@ -135,22 +135,6 @@ size_t tc_blob_bytes(const Shape& s, int precision);
 int pack_tc_blob(const Shape& s, int precision, const float* frame, const float* dec,
                  const float* act_scale, uint8_t* out, float* weight_scales_out);
 
-// Per-material FP32 image of the weights for the divergent path: the layout
-// the FP32 kernel stages in shared memory, holding the values the material's
-// tensor-core blob encodes (binary16-rounded weights and biases; FP8: the
-// decoder's E4M3 codes times their layer scale, FP32 decoder biases).
-size_t simt_image_floats(const Shape& s);
-void pack_simt_image(const Shape& s, int precision, const float* frame, const float* dec,
-                     const float* fp8_weight_scales, float* out);
-// E4M3(w / sw) times sw: an FP8 weight as the tensor cores see it
-float e4m3_dequant(float w, float sw);
-// Divergent path of per-tile selection: for each of the *n_tiles tiles in
-// tiles[] (written by an earlier launch: tiles with more materials than
-// tensor-core passes), one thread per query evaluates it with the image and
-// pyramid of its own material ids[i] (L.n queries, 128-query tiles, L.mats
-// for the pyramids).
-int launch_eval_divergent(const LaunchCommon& L, const float* const* images, const int32_t* ids,
-                          const int32_t* tiles, const int32_t* n_tiles, void* stream);
 
 // Importance sampler (11 -> 32 -> 32 -> 32 -> 9 FP32 MLP + proxy density).
 constexpr int kSamplerFloats = (11 * 32 + 32) + 2 * (32 * 32 + 32) + (32 * 9 + 9);
@@ -216,17 +200,17 @@ int launch_bin_eval(const BinArgs& a, void* stream);
 
 // Per-tile selection (per-query material ids), in place: a tile of 128
 // queries with k <= kSelectPasses distinct materials runs as k tensor-core
-// passes (one per material, each storing its own material's rows); a tile
-// with more runs on the divergent FP32 path.
+// passes (one per material, each storing its own material's rows); the
+// queries of tiles with more are binned by material and run in
+// material-coherent chunks.
 constexpr int kSelectPasses = 8;
 struct SelectArgs {
   LaunchCommon L;              // caller's queries, rgb, n, flags, materials table
   const int32_t* ids;          // [n] material of each query
-  const float* const* images;  // device array [nmat] of divergent-path images
   int precision;
-  void* scratch;               // select_scratch_bytes(n), 256-byte aligned
+  void* scratch;               // select_scratch_bytes(n, nmat, xi), 256-byte aligned
 };
-size_t select_scratch_bytes(int64_t n);
+size_t select_scratch_bytes(int64_t n, int nmat, bool xi);
 int launch_select_eval(const SelectArgs& a, void* stream);
 
 // encoder (Sec. 5.1): K -> 32 -> 32 -> 8, ReLU hidden layers, linear output;

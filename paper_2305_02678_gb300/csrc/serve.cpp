@@ -10,8 +10,16 @@
 // RGB.  Frames on different slots run concurrently on the GPU, so a frame
 // that arrives while others are in flight starts as soon as a slot frees up.
 // Completion is observed with CUDA events; per-frame latency is
-// finish - arrival on the nam_now() clock.
+// finish - arrival on the nam_now() clock.  A frame whose arrival time lies
+// in the future waits in the queue until then, so that a paced stream does
+// not depend on when its caller gets to run.  Each frame's device timeline
+// (copies begin, kernel begins and ends, copies end) is taken with timing
+// events on its stream and mapped onto the nam_now() clock through an
+// anchor event recorded while no frame is on the GPU.
 #include <cuda_runtime.h>
+#ifdef __linux__
+#include <sys/prctl.h>
+#endif
 
 #include <algorithm>
 #include <chrono>
@@ -38,7 +46,10 @@ struct Job {
 
 struct Slot {
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t done = nullptr;      // after the RGB copy: the frame is complete
+  cudaEvent_t begin = nullptr;     // before the frame's first copy
+  cudaEvent_t k_begin = nullptr;   // before its kernel
+  cudaEvent_t k_end = nullptr;     // after its kernel
   Job* job = nullptr;
   // pinned staging for the frame's work table: an upload from pageable
   // memory could make the scheduler thread wait for the slot's stream.
@@ -76,6 +87,11 @@ struct ServeState {
   uint64_t primed_bytes = 0;
   std::deque<double> latencies_ms;
   double first_arrival = -1.0, last_finish = 0.0;
+  // device-time anchor: anchor_ev completed at anchor_host_s (nam_now())
+  cudaStream_t anchor_stream = nullptr;
+  cudaEvent_t anchor_ev = nullptr;
+  double anchor_host_s = 0.0;
+  bool anchored = false;
 };
 
 }  // namespace nam
@@ -83,6 +99,29 @@ struct ServeState {
 extern "C" double nam_now(void) {
   using namespace std::chrono;
   return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// Record the anchor event on its own (idle) stream and wait for it: the
+// host time right after the wait is the anchor's time on the nam_now()
+// clock, to within the wait's wake-up latency.  Called with no frame on the
+// GPU, so that every frame's events come after the anchor.
+static void take_anchor(ServeState* S) {
+  S->anchored = false;
+  if (cudaEventRecord(S->anchor_ev, S->anchor_stream) != cudaSuccess) return;
+  if (cudaEventSynchronize(S->anchor_ev) != cudaSuccess) return;
+  S->anchor_host_s = nam_now();
+  S->anchored = true;
+}
+
+// A completed timing event's time on the nam_now() clock (0 if unknown).
+static double device_time(const ServeState* S, cudaEvent_t ev) {
+  if (!S->anchored) return 0.0;
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, S->anchor_ev, ev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0.0;
+  }
+  return S->anchor_host_s + 1e-3 * (double)ms;
 }
 
 static void finish_job(ServeState* S, Job* j, nam_status status) {
@@ -123,6 +162,8 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
   if (e != cudaSuccess) return cuda_fail((int)e, "serving: frame buffers");
   uint8_t* base = (uint8_t*)j->dev;
   const int64_t nfield = j->nf;
+  e = cudaEventRecord(slot.begin, s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "serving: event");
   float* rgb = (float*)(base + (size_t)nfield * n * 4);
   // work table (int64 fields) at the next 16-byte boundary after the RGB;
   // uploaded first, from the slot's pinned buffer (free: the slot's previous
@@ -167,8 +208,12 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
   L.mats.weights = (const void* const*)(tab + cb + pb);
   L.mats.nmat = (int32_t)j->mats.size();
   if (ctx->fault_launch.exchange(false)) return fail(NAM_ERR_CUDA, "injected launch failure");
+  e = cudaEventRecord(slot.k_begin, s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "serving: event");
   int le = launch_material(L, j->mats[0]->desc.precision, s);
   if (le) return cuda_fail(le, "serving: launch");
+  e = cudaEventRecord(slot.k_end, s);
+  if (e != cudaSuccess) return cuda_fail((int)e, "serving: event");
   e = cudaMemcpyAsync(j->frame.rgb_out, rgb, (size_t)n * 12, cudaMemcpyDeviceToHost, s);
   if (e != cudaSuccess) return cuda_fail((int)e, "serving: D2H");
   cudaFreeAsync(j->dev, s);
@@ -181,6 +226,11 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
 static void scheduler(nam_ctx* ctx) {
   ServeState* S = ctx->serve;
   DeviceGuard g(ctx->device);
+#ifdef __linux__
+  // timed waits wake within a microsecond of their deadline (the default
+  // slack of 50 us would delay paced arrivals and completions)
+  prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);
+#endif
   std::unique_lock<std::mutex> lk(S->mu);
   while (true) {
     bool progressed = false;
@@ -194,24 +244,39 @@ static void scheduler(nam_ctx* ctx) {
       S->in_flight--;
       budget_release(ctx, j->bytes);
       S->serving_bytes -= j->bytes;
+      if (q == cudaSuccess) {
+        j->st.gpu_begin_s = device_time(S, sl.begin);
+        j->st.gpu_kernel_begin_s = device_time(S, sl.k_begin);
+        j->st.gpu_kernel_end_s = device_time(S, sl.k_end);
+        j->st.gpu_end_s = device_time(S, sl.done);
+      }
       finish_job(S, j, q == cudaSuccess ? NAM_OK : NAM_ERR_CUDA);
       progressed = true;
     }
     if (S->stop && S->in_flight == 0) break;
-    // admissions, in arrival order
+    // admissions, in submission order, each once its arrival time has come
+    double next_arrival = 0.0;
     if (!S->stop && !ctx->fault_stall.load()) {
       for (Slot& sl : S->slots) {
         if (sl.job || S->queue.empty()) continue;
         Job* j = S->queue.front();
+        const double now = nam_now();
+        if (j->st.arrival_s > now) {
+          next_arrival = j->st.arrival_s;
+          break;
+        }
         if (!budget_reserve(ctx, j->bytes)) break;  // head of line waits for memory
         S->queue.pop_front();
         S->serving_bytes += j->bytes;
+        j->st.in_flight_at_admit = (int32_t)S->in_flight;
         S->in_flight++;
-        j->st.admit_s = nam_now();
+        j->st.admit_s = now;
+        j->st.slot = (int32_t)(&sl - S->slots.data());
         sl.job = j;
         lk.unlock();
         j->st.start_s = nam_now();
         nam_status st = launch_job(ctx, sl, j);
+        j->st.enqueued_s = nam_now();
         lk.lock();
         if (st != NAM_OK) {
           if (j->dev) cudaFreeAsync(j->dev, sl.stream);
@@ -225,7 +290,16 @@ static void scheduler(nam_ctx* ctx) {
         progressed = true;
       }
     }
-    if (!progressed) S->cv.wait_for(lk, std::chrono::microseconds(S->in_flight ? 20 : 2000));
+    if (progressed) continue;
+    const double now = nam_now();
+    // idle GPU: refresh the device-time anchor every 10 s (the events'
+    // FP32 millisecond offsets stay well below a microsecond)
+    if (S->in_flight == 0 && (!S->anchored || now - S->anchor_host_s > 10.0) &&
+        (next_arrival == 0.0 || next_arrival - now > 1e-3))
+      take_anchor(S);
+    double wait_s = S->in_flight ? 20e-6 : 2e-3;
+    if (next_arrival > 0.0) wait_s = std::min(wait_s, std::max(next_arrival - nam_now(), 0.0));
+    if (wait_s > 0.0) S->cv.wait_for(lk, std::chrono::nanoseconds((int64_t)(wait_s * 1e9)));
   }
 }
 
@@ -235,31 +309,34 @@ static nam_status ensure_serving(nam_ctx* ctx) {
   DeviceGuard g(ctx->device);
   ServeState* S = new ServeState();
   S->slots.resize(ctx->serve_streams);
+  auto release = [](ServeState* X) {
+    for (Slot& x : X->slots) {
+      if (x.stream) cudaStreamDestroy(x.stream);
+      for (cudaEvent_t ev : {x.done, x.begin, x.k_begin, x.k_end})
+        if (ev) cudaEventDestroy(ev);
+      if (x.host_tab) cudaFreeHost(x.host_tab);
+    }
+    if (X->prime_stream) cudaStreamDestroy(X->prime_stream);
+    if (X->anchor_stream) cudaStreamDestroy(X->anchor_stream);
+    if (X->anchor_ev) cudaEventDestroy(X->anchor_ev);
+    delete X;
+  };
+  cudaError_t e = cudaSuccess;
   for (Slot& sl : S->slots) {
-    cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&sl.done, &sl.begin, &sl.k_begin, &sl.k_end})
+      if (e == cudaSuccess) e = cudaEventCreate(ev);  // timing events
     if (e == cudaSuccess) e = cudaMallocHost(&sl.host_tab, kTableBytes);
     if (e == cudaSuccess) sl.host_tab_bytes = kTableBytes;
-    if (e != cudaSuccess) {
-      for (Slot& x : S->slots) {
-        if (x.stream) cudaStreamDestroy(x.stream);
-        if (x.done) cudaEventDestroy(x.done);
-        if (x.host_tab) cudaFreeHost(x.host_tab);
-      }
-      delete S;
-      return cuda_fail((int)e, "serving: stream creation");
-    }
   }
-  cudaError_t pe = cudaStreamCreateWithFlags(&S->prime_stream, cudaStreamNonBlocking);
-  if (pe != cudaSuccess) {
-    for (Slot& x : S->slots) {
-      cudaStreamDestroy(x.stream);
-      cudaEventDestroy(x.done);
-      cudaFreeHost(x.host_tab);
-    }
-    delete S;
-    return cuda_fail((int)pe, "serving: stream creation");
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->prime_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&S->anchor_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&S->anchor_ev);
+  if (e != cudaSuccess) {
+    release(S);
+    return cuda_fail((int)e, "serving: stream creation");
   }
+  take_anchor(S);
   ctx->serve = S;
   S->thread = std::thread(scheduler, ctx);
   return NAM_OK;
@@ -288,11 +365,13 @@ void nam::serve_stop(nam_ctx* ctx) {
   for (Slot& sl : S->slots) {
     cudaStreamSynchronize(sl.stream);
     cudaStreamDestroy(sl.stream);
-    cudaEventDestroy(sl.done);
+    for (cudaEvent_t ev : {sl.done, sl.begin, sl.k_begin, sl.k_end}) cudaEventDestroy(ev);
     if (sl.host_tab) cudaFreeHost(sl.host_tab);
     for (void* t : sl.retired_tabs) cudaFreeHost(t);
   }
   cudaStreamDestroy(S->prime_stream);
+  cudaStreamDestroy(S->anchor_stream);
+  cudaEventDestroy(S->anchor_ev);
   for (auto& kv : S->jobs) delete kv.second;
   delete S;
   ctx->serve = nullptr;
@@ -323,8 +402,10 @@ extern "C" nam_status nam_submit(nam_ctx* ctx, const nam_frame* f, nam_ticket* o
   const int64_t n = f->n_queries;
   j->bytes = ((uint64_t)n * 4 * j->nf + (uint64_t)n * 12 + 15) / 16 * 16 + j->chunks.size() * sizeof(Chunk) +
              2 * j->mats.size() * sizeof(void*) + 256;
-  j->st.arrival_s = f->arrival_s > 0 ? f->arrival_s : nam_now();
+  j->st.submit_s = nam_now();
+  j->st.arrival_s = f->arrival_s > 0 ? f->arrival_s : j->st.submit_s;
   j->st.n_queries = n;
+  j->st.slot = -1;
   st = ensure_serving(ctx);
   if (st) {
     delete j;

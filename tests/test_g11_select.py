@@ -1,15 +1,13 @@
 """Per-tile selection between code paths (nam_eval_select, Sec. 7.1).  A
 tile of 128 queries with at most NAM_SELECT_MAX_PASSES distinct materials
-runs as one masked tensor-core pass per material: every such query must be
-bitwise nam_eval on its material.  A tile with more materials runs on the
-divergent path, one query per thread in FP32 on the values the material's
-tensor-core blob holds: those queries must match the FP64 oracle evaluating
-the same values (params "fp16": binary16-rounded weights and biases; "fp8":
-frame in binary16, decoder weights E4M3 times the layer scale, FP32 decoder
-biases) with no activation rounding, to the FP32 path's bound (1e-5 against
-max(|o|, RMS), conditioning-aware beyond kappa = 50).  Plus ragged sizes,
-coherent, few-material and many-material tiles, the paper's decoder shapes,
-the stochastic filter, the cosine factor and out-of-range ids."""
+runs as one masked tensor-core pass per material; the queries of tiles with
+more are binned by material (the SER analogue, Sec. 7.3) and run in
+material-coherent chunks.  Either way every query must be bitwise nam_eval
+on its material, so the whole output equals nam_eval_binned's; one case per
+precision is also graded against the FP64 oracle (FP16 bound 2e-3, FP8
+3e-2, conditioning-aware beyond kappa = 50).  Plus ragged sizes, coherent,
+few-material and many-material tiles, the paper's decoder shapes, the
+stochastic filter, the cosine factor and out-of-range ids."""
 import numpy as np
 import pytest
 
@@ -18,8 +16,7 @@ from conftest import to_device
 
 pytestmark = pytest.mark.gpu
 
-TOL_F32 = 1e-5
-FP8_SCALE = np.array([0.004, 0.003, 0.0025], np.float32)
+TOL = {1: 2e-3, 2: 3e-2}
 
 
 def _materials(gctx, oracle, seed, k, precision=1, filt=0, W0=128, L=8, H=64, NH=2, frame="mlp", cos=False):
@@ -31,7 +28,12 @@ def _materials(gctx, oracle, seed, k, precision=1, filt=0, W0=128, L=8, H=64, NH
     for j in range(k):
         pyr = W.make_pyramid(rng[j], W0, W0, L, dtype=np.float16)
         model = W.make_model(rng[k + j], (nin,) + (H,) * NH + (3,), fw)
-        kw = {"act_scale": FP8_SCALE} if precision == B.NAM_PREC_FP8 else {}
+        kw = {}
+        if precision == B.NAM_PREC_FP8:
+            # calibrated input scales of the decoder layers (max |input| / 448)
+            om = oracle.Model(W0, W0, L, pyr, model["frame"], model["decoder"], filter=filt)
+            amax = oracle.decoder_input_absmax(om, W.uniform_queries(np.random.default_rng(seed + j), 4096, 6.0))
+            kw["act_scale"] = np.where(amax > 0, amax / 448.0, 1.0).astype(np.float32)
         mats.append(gctx.material(W0, W0, L, pyr, model["frame"], model["decoder"], precision=precision,
                                   filter=filt, **kw))
         params = "fp8" if precision == B.NAM_PREC_FP8 else "fp16"
@@ -59,7 +61,7 @@ def _tile_ids(rng, n, k, mixed_frac, many_frac=0.0):
 
 def _on_passes(ids, nmat, max_passes):
     """Per query: does its tile run as tensor-core passes (at most
-    max_passes distinct valid materials), rather than on the divergent path?"""
+    max_passes distinct valid materials), rather than through binning?"""
     n = len(ids)
     out = np.zeros(n, bool)
     for t in range((n + 127) // 128):
@@ -77,29 +79,32 @@ def _run(gctx, mats, dq, ids, n, flags=0):
     return out.cpu().numpy()
 
 
-def _check(gctx, oracle, mats, models, q, ids, n, flags=0, label=""):
+def _check(gctx, oracle, mats, models, q, ids, n, flags=0, label="", precision=None):
+    """Every valid query bitwise nam_eval on its material, the output
+    bitwise nam_eval_binned's; with `precision`, also graded against the
+    oracle."""
     import torch
     from paper_2305_02678_gb300 import binding as B
     dq = to_device(q)
     got = _run(gctx, mats, dq, ids, n, flags)
     gctx.check()
     tc = _on_passes(ids, len(mats), B.NAM_SELECT_MAX_PASSES)
-    n_div = 0
     for k, (m, om) in enumerate(zip(mats, models)):
-        sel = np.nonzero((ids == k) & tc)[0]
-        if sel.size:
-            idx = torch.from_numpy(sel).cuda()
-            ref = m.eval({f: t[idx].contiguous() for f, t in dq.items()}, flags=flags).cpu().numpy()
-            assert np.array_equal(got[sel], ref), (label, k)
-        sel = np.nonzero((ids == k) & ~tc)[0]
-        if sel.size:
+        sel = np.nonzero(ids == k)[0]
+        if sel.size == 0:
+            continue
+        idx = torch.from_numpy(sel).cuda()
+        ref = m.eval({f: t[idx].contiguous() for f, t in dq.items()}, flags=flags).cpu().numpy()
+        assert np.array_equal(got[sel], ref), (label, k)
+        if precision is not None:
             sq = {f: v[sel] for f, v in q.items()}
-            ok, st = oracle.parity(got[sel], oracle.eval(om, sq), oracle.frame_condition(om, sq), TOL_F32)
-            print(f"{label} material {k}: {sel.size} divergent-path queries, max {st['max_rel']:.2e} "
-                  f"(well-conditioned {st['max_rel_well_conditioned']:.2e})")
+            ok, st = oracle.parity(got[sel], oracle.eval(om, sq), oracle.frame_condition(om, sq), TOL[precision])
             assert ok, (label, k, st)
-            n_div += sel.size
-    print(f"{label}: {int(tc.sum())} queries on tensor-core passes, {n_div} on the divergent path")
+    binned = torch.full((n, 3), -7.0, device="cuda")
+    B.nam_eval_binned(gctx.h, [m.h for m in mats], dq, torch.from_numpy(ids).cuda(), n, binned,
+                      torch.cuda.current_stream(), flags)
+    assert np.array_equal(got, binned.cpu().numpy()), label
+    print(f"{label}: {int(tc.sum())} queries on tensor-core passes, {int((~tc).sum())} binned")
     return got, tc
 
 
@@ -108,7 +113,7 @@ def test_select_tiles(gctx, oracle, n):
     mats, models, rng = _materials(gctx, oracle, 101, 12, W0=64, L=7)
     q = W.uniform_queries(rng, n, 6.0)
     ids = _tile_ids(rng, n, 12, 0.3, 0.2)
-    _, tc = _check(gctx, oracle, mats, models, q, ids, n, label=f"n={n}")
+    _, tc = _check(gctx, oracle, mats, models, q, ids, n, label=f"n={n}", precision=1 if n == 5000 else None)
     if n >= 5000:
         assert tc.any() and not tc.all()
     for m in mats:
@@ -130,23 +135,19 @@ def test_select_all_coherent_few_and_many(gctx, oracle):
     ids = rng.integers(0, 3, n).astype(np.int32)
     _, tc = _check(gctx, oracle, mats, models, q, ids, n, label="3 per tile")
     assert tc.all()
-    # exactly NAM_SELECT_MAX_PASSES materials per tile: still passes; one more: divergent
+    # exactly NAM_SELECT_MAX_PASSES materials per tile: still passes; one more: binned
     for k, on_passes in ((B.NAM_SELECT_MAX_PASSES, True), (B.NAM_SELECT_MAX_PASSES + 1, False)):
         ids = (np.arange(n) % k).astype(np.int32)
         _, tc = _check(gctx, oracle, mats, models, q, ids, n, label=f"{k} per tile")
         assert tc.all() == on_passes and tc.any() == on_passes
-    # twelve materials per query at random: every tile divergent
+    # twelve materials per query at random: every tile binned
     ids = rng.integers(0, 12, n).astype(np.int32)
     _, tc = _check(gctx, oracle, mats, models, q, ids, n, label="12 per tile")
     assert not tc.any()
-    # a mixed batch and nam_eval_binned agree on every tensor-core query
+    # a mixed batch of all three kinds of tile
     ids = _tile_ids(rng, n, 12, 0.5, 0.2)
-    got = _run(gctx, mats, dq, ids, n)
-    binned = torch.full((n, 3), -7.0, device="cuda")
-    B.nam_eval_binned(gctx.h, [m.h for m in mats], dq, torch.from_numpy(ids).cuda(), n, binned,
-                      torch.cuda.current_stream())
-    tc = _on_passes(ids, 12, B.NAM_SELECT_MAX_PASSES)
-    assert np.array_equal(got[tc], binned.cpu().numpy()[tc])
+    _, tc = _check(gctx, oracle, mats, models, q, ids, n, label="mixed")
+    assert tc.any() and not tc.all()
     for m in mats:
         m.destroy()
     gctx.check()
@@ -172,7 +173,8 @@ def test_select_fp8_stochastic_cosine(gctx, oracle):
         n = 4097
         q = W.uniform_queries(rng, n, 6.0)
         _check(gctx, oracle, mats, models, q, _tile_ids(rng, n, 10, 0.4, 0.3), n,
-               flags=B.NAM_OUT_COSINE if cos else 0, label=f"precision {prec} filter {filt} cosine {cos}")
+               flags=B.NAM_OUT_COSINE if cos else 0, label=f"precision {prec} filter {filt} cosine {cos}",
+               precision=prec)
         for m in mats:
             m.destroy()
     gctx.check()
@@ -185,7 +187,7 @@ def test_select_out_of_range_ids(gctx, oracle):
     n = 1000
     q = W.uniform_queries(rng, n, 6.0)
     ids = _tile_ids(rng, n, 10, 0.0)
-    ids[256:384] = rng.integers(0, 10, 128)   # tile 2: divergent
+    ids[256:384] = rng.integers(0, 10, 128)   # tile 2: binned
     ids[[5, 300, 500, 999]] = [7 + 10, -1, 10, -5]
     dq = to_device(q)
     got = _run(gctx, mats, dq, ids, n)
@@ -199,16 +201,11 @@ def test_select_out_of_range_ids(gctx, oracle):
     tc = _on_passes(ids, 10, B.NAM_SELECT_MAX_PASSES)
     assert tc[5] and not tc[300] and tc[500]
     for k, (m, om) in enumerate(zip(mats, models)):
-        sel = np.nonzero(ok & tc & (ids == k))[0]
+        sel = np.nonzero(ok & (ids == k))[0]
         if sel.size:
             idx = torch.from_numpy(sel).cuda()
             ref = m.eval({f: t[idx].contiguous() for f, t in dq.items()}).cpu().numpy()
             assert np.array_equal(got[sel], ref)
-        sel = np.nonzero(ok & ~tc & (ids == k))[0]
-        if sel.size:
-            sq = {f: v[sel] for f, v in q.items()}
-            good, st = oracle.parity(got[sel], oracle.eval(om, sq), oracle.frame_condition(om, sq), TOL_F32)
-            assert good, st
     for m in mats:
         m.destroy()
     gctx.check()

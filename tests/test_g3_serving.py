@@ -113,6 +113,63 @@ def test_frames_match_direct_evaluation_alone_and_in_a_mix(scene):
     ctx.close()
 
 
+def test_served_frame_matches_the_oracle(scene, oracle):
+    """One frame through nam_submit, every query checked against the FP64
+    oracle of its tile's material (FP16 parameters, Sec. 5.2) at the FP16
+    bound 2e-3 on the max, with the frame-conditioning band of the parity
+    tests; the frame's recorded timeline is ordered."""
+    from paper_2305_02678_gb300 import binding as B
+    ctx = _ctx(serve_streams=2)
+    mats = _materials(ctx, scene)
+    q, tiles, mt = scene[1][0]
+    fr = _Frame(B, q, tiles, mt, mats)
+    t = B.nam_submit(ctx.h, fr.f)
+    st, fs = B.nam_wait(ctx.h, t, 30_000_000_000)
+    assert st == 0 and fs.status == 0
+    g = fr.out.numpy().copy()
+    ctx.close()
+    n = len(q["u"])
+    o = np.zeros((n, 3))
+    kappa = np.zeros(n)
+    for k, (pyr, model) in enumerate(scene[0]):
+        idx = np.concatenate([np.arange(s, s + c) for (s, c), m in zip(tiles, mt) if m == k] or [np.zeros(0, int)])
+        if len(idx) == 0:
+            continue
+        om = oracle.Model(256, 256, 9, pyr, model["frame"], model["decoder"], params="fp16")
+        qk = {f: v[idx] for f, v in q.items()}
+        o[idx] = oracle.eval(om, qk)
+        kappa[idx] = oracle.frame_condition(om, qk)
+    ok, s = oracle.parity(g, o, kappa, 2e-3)
+    print(f"served frame {n} queries: max {s['max_rel']:.3e} (kappa <= 50: {s['max_rel_well_conditioned']:.3e}), "
+          f"ill-conditioned {s['ill_conditioned']}")
+    assert ok, s
+    assert fs.submit_s <= fs.admit_s <= fs.start_s <= fs.enqueued_s <= fs.finish_s
+    assert fs.slot in (0, 1) and fs.in_flight_at_admit == 0
+    assert 0 < fs.gpu_begin_s <= fs.gpu_kernel_begin_s <= fs.gpu_kernel_end_s <= fs.gpu_end_s
+    # device times sit on the host clock to within the anchor's error
+    assert fs.start_s - 1e-3 <= fs.gpu_begin_s and fs.gpu_end_s <= fs.finish_s + 1e-3
+
+
+def test_future_arrival_is_held_until_then(scene):
+    """A frame whose arrival time lies ahead waits in the queue until then."""
+    from paper_2305_02678_gb300 import binding as B
+    ctx = _ctx(serve_streams=2)
+    mats = _materials(ctx, scene)
+    q, tiles, mt = scene[1][1]
+    arrival = B.nam_now() + 0.25
+    fr = _Frame(B, q, tiles, mt, mats, arrival=arrival)
+    t = B.nam_submit(ctx.h, fr.f)
+    time.sleep(0.05)
+    done, st = B.nam_poll(ctx.h, t)
+    assert not done and ctx.stats().queued == 1
+    st_code, fs = B.nam_wait(ctx.h, t, 30_000_000_000)
+    assert st_code == 0
+    assert fs.arrival_s == arrival and fs.admit_s >= arrival
+    assert fs.admit_s - arrival < 0.05
+    assert np.array_equal(fr.out.numpy(), _direct(ctx, mats, q, tiles, mt))
+    ctx.close()
+
+
 def test_frames_overlap_on_the_gpu(scene):
     """With several stream slots, a frame is admitted while another is still
     in flight (admission of frame k+1 precedes completion of frame k)."""
