@@ -1118,14 +1118,21 @@ def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_
         frames.append((wd * ht, pinned, out, tiles))
     runs = [_serving_stream(B, C, ctx, mats, mat_arr, frames, rngs[2 * n_mat + 1 + r], total, warmup_frames, rate,
                             n_mat, lead_s) for r in range(repeats)]
+    # the same streams with the frames' queries and RGB in device memory (a
+    # renderer's G-buffer): no host link in the loop
+    dframes = [(n, {k: v.to(f"cuda:{device}") for k, v in pinned.items()},
+                torch.empty((n, 3), device=f"cuda:{device}"), tiles) for n, pinned, _, tiles in frames]
+    druns = [_serving_stream(B, C, ctx, mats, mat_arr, dframes, rngs[2 * n_mat + 1 + r], total, warmup_frames, rate,
+                             n_mat, lead_s, flags=B.NAM_FRAME_DEVICE) for r in range(repeats)]
     for m in mats:
         m.destroy()
     ctx.close()
     if trace:
         # columns: resolution index, arrival, submit, admit, start, enqueued, gpu begin, kernel begin, kernel end,
         # gpu end, finish (s), queries, slot, in flight at admission; one array per stream
-        np.savez(trace, **{f"run{r}": x.pop("_rows") for r, x in enumerate(runs)})
-    for x in runs:
+        np.savez(trace, **{f"run{r}": x.pop("_rows") for r, x in enumerate(runs)},
+                 **{f"device_run{r}": x.pop("_rows") for r, x in enumerate(druns)})
+    for x in runs + druns:
         x.pop("_rows", None)
     out = dict(runs[0])
     out.update({"frames": n_frames, "warmup_frames": warmup_frames, "rate_fps": rate, "materials": n_mat,
@@ -1135,11 +1142,18 @@ def run_serving(device, n_frames, rate=240.0, n_mat=16, budget=40 << 30, warmup_
                 "p99_frame_ms_runs": [r["p99_frame_ms"] for r in runs],
                 "p99_spread": round(max(r["p99_frame_ms"] for r in runs) / min(r["p99_frame_ms"] for r in runs), 3),
                 "runs": runs[1:],
+                "device_frames": {
+                    "p50_frame_ms_runs": [r["p50_frame_ms"] for r in druns],
+                    "p99_frame_ms_runs": [r["p99_frame_ms"] for r in druns],
+                    "p99_spread": round(max(r["p99_frame_ms"] for r in druns) / min(r["p99_frame_ms"] for r in druns), 3),
+                    "evals_per_s_runs": [r["evals_per_s"] for r in druns],
+                    "breakdown": druns[0]["breakdown"], "slowest_frames": druns[0]["slowest_frames"],
+                    "note": "NAM_FRAME_DEVICE: queries and RGB in device memory, only the work table is uploaded"},
                 "latency": "finish - scheduled Poisson arrival on the nam_now() clock; host->device copy of the "
                            "frame's inputs, kernel and device->host copy of its RGB included"})
     return out
 
-def _serving_stream(B, C, ctx, mats, mat_arr, frames, rng, total, warmup_frames, rate, n_mat, lead_s):
+def _serving_stream(B, C, ctx, mats, mat_arr, frames, rng, total, warmup_frames, rate, n_mat, lead_s, flags=0):
     """One Poisson stream of `total` frames through nam_submit; see run_serving."""
     arrivals = np.cumsum(rng.exponential(1.0 / rate, total))
     which = rng.integers(0, len(frames), total)
@@ -1164,7 +1178,7 @@ def _serving_stream(B, C, ctx, mats, mat_arr, frames, rng, total, warmup_frames,
         f.n_materials = n_mat
         f.materials = C.addressof(mat_arr)
         f.rgb_out = out.data_ptr()
-        f.flags = 0
+        f.flags = flags
         f.arrival_s = t0 + arrivals[i]
         ahead = f.arrival_s - lead_s - B.nam_now()
         if ahead > 0:

@@ -227,7 +227,9 @@ typedef struct {
 
 enum {
   NAM_OUT_COSINE = 1u << 0,  /* multiply the RGB by max(0, wi.z) (Eq. 1) */
-  NAM_HOST_STAGED = 1u << 8  /* nam_eval_host: always take the staged-copy path */
+  NAM_HOST_STAGED = 1u << 8,  /* nam_eval_host: always take the staged-copy path */
+  NAM_FRAME_DEVICE = 1u << 9  /* nam_submit: the frame's query arrays and rgb_out are
+                                 device memory (e.g. a renderer's G-buffer): no copies */
 };
 
 /* Evaluate n queries whose arrays are device memory; writes rgb_out (device,
@@ -561,13 +563,15 @@ typedef uint64_t nam_ticket;
 
 typedef struct {
   int64_t n_queries;          /* queries of the frame */
-  nam_queries q;              /* HOST arrays, n_queries each, valid until the ticket completes */
+  nam_queries q;              /* HOST arrays (device with NAM_FRAME_DEVICE), n_queries each,
+                                 valid until the ticket completes */
   const nam_work_item* items; /* HOST array: the frame's tiles, each one material */
   int32_t n_items;
   int32_t n_materials;
   const nam_material* materials; /* HOST array of n_materials handles, resident in this context */
-  float* rgb_out;             /* HOST [n_queries][3], written before the ticket completes */
-  uint32_t flags;             /* NAM_OUT_* */
+  float* rgb_out;             /* HOST [n_queries][3] (device with NAM_FRAME_DEVICE), written
+                                 before the ticket completes */
+  uint32_t flags;             /* NAM_OUT_*, NAM_FRAME_DEVICE */
   int32_t reserved0;
   double arrival_s;           /* arrival time on the nam_now() clock; <= 0 -> now.  A frame
                                  whose arrival lies in the future is held in the queue

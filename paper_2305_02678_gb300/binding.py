@@ -24,6 +24,7 @@ NAM_PREC_F32, NAM_PREC_F16, NAM_PREC_FP8 = 0, 1, 2
 NAM_FILTER_TRILINEAR, NAM_FILTER_STOCHASTIC = 0, 1
 NAM_ADDRESS_WRAP, NAM_ADDRESS_CLAMP = 0, 1
 NAM_HOST_STAGED = 1 << 8
+NAM_FRAME_DEVICE = 1 << 9
 NAM_OUT_COSINE = 1
 NAM_FAULT_NONE, NAM_FAULT_ALLOC, NAM_FAULT_LAUNCH, NAM_FAULT_STALL = 0, 1, 2, 3
 NAM_MAX_LEVELS, NAM_MAX_LAYERS = 16, 8
@@ -343,7 +344,7 @@ def nam_eval_binned(ctx, mats, q, material_ids, n, rgb_out, stream=None, flags=0
 
 
 def nam_eval_select(ctx, mats, q, material_ids, n, rgb_out, stream=None, flags=0):
-    """Per-tile coherent/divergent selection; arguments as nam_eval_binned."""
+    """Per-tile code-path selection (masked passes or binning); arguments as nam_eval_binned."""
     arr = (C.c_void_p * len(mats))(*mats)
     qs = make_queries(q)
     _check(_lib.nam_eval_select(ctx, arr, len(mats), C.byref(qs), ptr(material_ids), int(n), ptr(rgb_out),

@@ -761,7 +761,13 @@ constexpr int kF16Nwg = 5;
 
 template <int H, int FK, int NH, bool F16P, bool MULTI>
 constexpr int f16_nwg() {
-  // per-warpgroup weight copies of the largest shapes leave room for four
+  // A launch that mixes materials keeps one weight copy per warpgroup.  With
+  // five, shared memory leaves 60 KB of the SM's L1 for the texel gathers and
+  // its launch took 2.1x a single-material launch over as many tiles; the
+  // whole binned call for 16 materials drawn per pixel at 1080p took
+  // 0.41 ms with five warpgroups, 0.31 ms with four (92 KB of L1), 0.33 ms
+  // with three
+  if (MULTI) return kF16Nwg - 1;
   return F16Smem<H, FK, NH, F16P, MULTI, kF16Nwg>::BYTES <= 227 * 1024 ? kF16Nwg : kF16Nwg - 1;
 }
 

@@ -1,7 +1,6 @@
-// The per-query body of the FP32 evaluation, shared by the staged kernel
-// (weights in shared memory) and the divergent kernel of per-tile selection
-// (weights read from each material's global image): the parameter image
-// layout, its loader, and one query's evaluation.
+// The per-query body of the FP32 evaluation (weights staged in shared
+// memory): the parameter image layout, its loader, and one query's
+// evaluation.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -83,8 +82,7 @@ __device__ __forceinline__ float dot_row(const float* __restrict__ row, const fl
   return s0 + s1;
 }
 
-// One query's evaluation from a parameter image S (shared memory in the
-// staged kernel, a material's global image in the divergent one): latent
+// One query's evaluation from the parameter image S in shared memory: latent
 // fetch, frame, direction transform, decoder; y = RGB.  With `calib` the
 // maxima of |layer input| are folded into am0..am2; with `alb` the albedo
 // head's outputs (no cosine factor: the albedo depends on x and wo alone)

@@ -21,7 +21,6 @@ struct nam_material_s {
   int64_t n_params = 0;
   void* pyramid = nullptr;    // device pyramid (FP16 or FP32 texels)
   void* blob = nullptr;       // tensor-core weight blob (F16 / FP8)
-                              // for the divergent path of per-tile selection
   float* params = nullptr;    // FP32 masters (frame then decoder)
   float* sampler = nullptr;   // FP32 importance-sampler weights, or null
   int64_t pyr_off = 0;        // trainable: offset of the pyramid block in

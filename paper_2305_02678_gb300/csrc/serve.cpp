@@ -7,7 +7,8 @@
 // multi-material tensor-core launch over the frame's tiles (each tile one
 // material, so every 128-query MMA tile is material-coherent, the analogue
 // of the paper's coherent warps, Sec. 7.3) and the device->host copy of the
-// RGB.  Frames on different slots run concurrently on the GPU, so a frame
+// RGB; a frame whose queries and output already live in device memory
+// (NAM_FRAME_DEVICE, the renderer's case) needs no copies.  Frames on different slots run concurrently on the GPU, so a frame
 // that arrives while others are in flight starts as soon as a slot frees up.
 // Completion is observed with CUDA events; per-frame latency is
 // finish - arrival on the nam_now() clock.  A frame whose arrival time lies
@@ -162,13 +163,15 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
   if (e != cudaSuccess) return cuda_fail((int)e, "serving: frame buffers");
   uint8_t* base = (uint8_t*)j->dev;
   const int64_t nfield = j->nf;
+  const bool on_device = (j->frame.flags & NAM_FRAME_DEVICE) != 0;
   e = cudaEventRecord(slot.begin, s);
   if (e != cudaSuccess) return cuda_fail((int)e, "serving: event");
-  float* rgb = (float*)(base + (size_t)nfield * n * 4);
-  // work table (int64 fields) at the next 16-byte boundary after the RGB;
-  // uploaded first, from the slot's pinned buffer (free: the slot's previous
-  // frame has completed)
-  uint8_t* tab = base + (((size_t)nfield * n * 4 + (size_t)n * 12 + 15) / 16 * 16);
+  // host frames: query fields, then the RGB, then the work table (int64
+  // fields) at the next 16-byte boundary; device frames: the table alone.
+  // The table goes first, from the slot's pinned buffer (free: the slot's
+  // previous frame has completed)
+  float* rgb = on_device ? j->frame.rgb_out : (float*)(base + (size_t)nfield * n * 4);
+  uint8_t* tab = on_device ? base : base + (((size_t)nfield * n * 4 + (size_t)n * 12 + 15) / 16 * 16);
   const size_t cb = j->chunks.size() * sizeof(Chunk);
   const size_t pb = j->mats.size() * sizeof(void*);
   const size_t tb = cb + 2 * pb;
@@ -194,14 +197,17 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
   const float* src[10] = {j->frame.q.u, j->frame.q.v, j->frame.q.lod, j->frame.q.wix, j->frame.q.wiy,
                           j->frame.q.wiz, j->frame.q.wox, j->frame.q.woy, j->frame.q.woz, j->frame.q.xi};
   float* dst[10] = {nullptr};
-  for (int f = 0; f < j->nf; ++f) {
-    dst[f] = (float*)(base + (size_t)f * n * 4);
-    e = cudaMemcpyAsync(dst[f], src[f], (size_t)n * 4, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_fail((int)e, "serving: H2D");
+  nam_queries dq = j->frame.q;
+  if (!on_device) {
+    for (int f = 0; f < j->nf; ++f) {
+      dst[f] = (float*)(base + (size_t)f * n * 4);
+      e = cudaMemcpyAsync(dst[f], src[f], (size_t)n * 4, cudaMemcpyHostToDevice, s);
+      if (e != cudaSuccess) return cuda_fail((int)e, "serving: H2D");
+    }
+    dq = nam_queries{dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], dst[7], dst[8], dst[9]};
   }
-  nam_queries dq{dst[0], dst[1], dst[2], dst[3], dst[4], dst[5], dst[6], dst[7], dst[8], dst[9]};
   LaunchCommon L;
-  fill_launch(ctx, j->mats[0], &dq, 0, rgb, j->frame.flags, &L);
+  fill_launch(ctx, j->mats[0], &dq, 0, rgb, j->frame.flags & ~(uint32_t)NAM_FRAME_DEVICE, &L);
   L.chunks = (const Chunk*)tab;
   L.n_chunks = (int32_t)j->chunks.size();
   L.mats.pyramid = (const void* const*)(tab + cb);
@@ -214,8 +220,10 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
   if (le) return cuda_fail(le, "serving: launch");
   e = cudaEventRecord(slot.k_end, s);
   if (e != cudaSuccess) return cuda_fail((int)e, "serving: event");
-  e = cudaMemcpyAsync(j->frame.rgb_out, rgb, (size_t)n * 12, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return cuda_fail((int)e, "serving: D2H");
+  if (!on_device) {
+    e = cudaMemcpyAsync(j->frame.rgb_out, rgb, (size_t)n * 12, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail((int)e, "serving: D2H");
+  }
   cudaFreeAsync(j->dev, s);
   j->dev = nullptr;
   e = cudaEventRecord(slot.done, s);
@@ -400,8 +408,10 @@ extern "C" nam_status nam_submit(nam_ctx* ctx, const nam_frame* f, nam_ticket* o
   build_chunks(f->items, f->n_items, &j->chunks);
   j->nf = f->materials[0]->desc.filter == NAM_FILTER_STOCHASTIC ? 10 : 9;
   const int64_t n = f->n_queries;
-  j->bytes = ((uint64_t)n * 4 * j->nf + (uint64_t)n * 12 + 15) / 16 * 16 + j->chunks.size() * sizeof(Chunk) +
-             2 * j->mats.size() * sizeof(void*) + 256;
+  // device buffers the frame needs from the pool: a host frame's copy of its
+  // query fields and its RGB, and the work table
+  const uint64_t io = (f->flags & NAM_FRAME_DEVICE) ? 0 : ((uint64_t)n * 4 * j->nf + (uint64_t)n * 12 + 15) / 16 * 16;
+  j->bytes = io + j->chunks.size() * sizeof(Chunk) + 2 * j->mats.size() * sizeof(void*) + 256;
   j->st.submit_s = nam_now();
   j->st.arrival_s = f->arrival_s > 0 ? f->arrival_s : j->st.submit_s;
   j->st.n_queries = n;

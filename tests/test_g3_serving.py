@@ -150,6 +150,37 @@ def test_served_frame_matches_the_oracle(scene, oracle):
     assert fs.start_s - 1e-3 <= fs.gpu_begin_s and fs.gpu_end_s <= fs.finish_s + 1e-3
 
 
+def test_device_frame_needs_no_copies(scene):
+    """NAM_FRAME_DEVICE: queries and RGB in device memory; the result is
+    bitwise the direct evaluation, and the frame's device time from its first
+    operation to its kernel holds only the work-table upload."""
+    import torch
+    from paper_2305_02678_gb300 import binding as B
+    ctx = _ctx(serve_streams=2)
+    mats = _materials(ctx, scene)
+    q, tiles, mt = scene[1][2]
+    n = len(q["u"])
+    dq = {k: torch.from_numpy(v).cuda() for k, v in q.items()}
+    out = torch.full((n, 3), float("nan"), device="cuda")
+    items = (B.nam_work_item * len(tiles))(*[B.nam_work_item(s, c, int(m)) for (s, c), m in zip(tiles, mt)])
+    mat_arr = (C.c_void_p * len(mats))(*[m.h for m in mats])
+    f = B.nam_frame()
+    f.n_queries = n
+    f.q = B.make_queries(dq)
+    f.items = C.addressof(items)
+    f.n_items = len(tiles)
+    f.n_materials = len(mats)
+    f.materials = C.addressof(mat_arr)
+    f.rgb_out = out.data_ptr()
+    f.flags = B.NAM_FRAME_DEVICE
+    t = B.nam_submit(ctx.h, f)
+    st, fs = B.nam_wait(ctx.h, t, 30_000_000_000)
+    assert st == 0
+    assert np.array_equal(out.cpu().numpy(), _direct(ctx, mats, q, tiles, mt))
+    assert fs.gpu_kernel_begin_s - fs.gpu_begin_s < 2e-3
+    ctx.close()
+
+
 def test_future_arrival_is_held_until_then(scene):
     """A frame whose arrival time lies ahead waits in the queue until then."""
     from paper_2305_02678_gb300 import binding as B
