@@ -171,7 +171,10 @@ typedef struct {
    * nine parameters of the analytic proxy density.  sampler_hidden = 0: no
    * sampler; 32: widths 11 -> 32 -> 32 -> 32 -> 9 with ReLU hidden layers,
    * FP32 weights per layer W (out x in) then b (out), layers in order (host
-   * or device memory as params_on_device says), copied at creation. */
+   * or device memory as params_on_device says), copied at creation
+   * (NAM_ERR_UNSUPPORTED for a weight of magnitude >= 32768: the network
+   * runs on the tensor cores with each weight split into two binary16
+   * values). */
   int32_t sampler_hidden;
   const float* sampler_weights;
   int32_t frame_form;         /* NAM_FRAME_MLP (0) or NAM_FRAME_PAPER (1) */
@@ -280,8 +283,10 @@ nam_status nam_fp8_calibrate(nam_ctx* ctx, nam_material m, const nam_queries* q,
  * (4 |wo . h|), h = normalize(wi + wo), v = M^-1 h, D_std(w) = max(0, w_z) /
  * pi, M = [[alpha_x, 0, -mu_sx], [alpha_y rho, alpha_y sqrt(1 - rho^2),
  * -mu_sy], [0, 0, 1]].  Directions are in the query's geometric frame (z up).
- * All arrays are device memory; FP32 arithmetic; asynchronous on `stream`;
- * NAM_ERR_UNSUPPORTED if the material has no sampler.
+ * All arrays are device memory; FP32 arithmetic (the network on the tensor
+ * cores with binary16 hi/lo splits of weights and activations, relative
+ * error ~2^-22 per product); asynchronous on `stream`; NAM_ERR_UNSUPPORTED
+ * if the material has no sampler.
  *
  * nam_sample: one direction per query from the variates u ([n][3] in
  * [0, 1)): u[2] < w_d picks the diffuse lobe, (u[0], u[1]) drive the cosine

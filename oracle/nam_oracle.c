@@ -788,6 +788,47 @@ static double frame_kappa(const orc_model* m, const trace* tr) {
   return isfinite(k) ? k : 1e300;
 }
 
+/* Sensitivity of the decoder's RGB to its direction inputs (the transformed
+ * wi', wo': 6 values, 12 in the paper's frame form): for each query and RGB
+ * channel c, sum over those inputs k of |d y_c / d x_k|, the Jacobian taken
+ * through the query's own ReLU pattern (ReLU'(0) = 0, reading 10) and the
+ * cosine factor.  A perturbation of every direction input by at most d moves
+ * y_c by at most d times this value (to first order).  Out [n][3]. */
+void orc_direction_gain(const orc_model* m, const orc_queries* q, int64_t n, double* gain_out) {
+  trace* tr = (trace*)malloc(sizeof(trace));
+  const int nd = m->frame_form == 1 ? 6 : 3;
+  const int ndir = 2 * nd;
+  double J[ORC_MAXW][12], Jn[ORC_MAXW][12];
+  for (int64_t i = 0; i < n; ++i) {
+    forward(m, q, i, tr);
+    const double* p = m->dec_params;
+    for (int l = 0; l < m->n_layers; ++l) {
+      const int in = m->widths[l], out = m->widths[l + 1];
+      const double* W = p;
+      p = W + (int64_t)in * out + out;
+      for (int j = 0; j < out; ++j)
+        for (int k = 0; k < ndir; ++k) {
+          double s = 0.0;
+          if (l == 0) {
+            s = W[j * in + ORC_C + k];
+          } else {
+            for (int t = 0; t < in; ++t)
+              if (tr->pre[l - 1][t] > 0.0) s += W[j * in + t] * J[t][k];
+          }
+          Jn[j][k] = s;
+        }
+      for (int j = 0; j < out; ++j)
+        for (int k = 0; k < ndir; ++k) J[j][k] = Jn[j][k];
+    }
+    for (int c = 0; c < 3; ++c) {
+      double g = 0.0;
+      for (int k = 0; k < ndir; ++k) g += fabs(J[c][k]);
+      gain_out[3 * i + c] = g * tr->cosf;
+    }
+  }
+  free(tr);
+}
+
 void orc_frame_condition(const orc_model* m, const orc_queries* q, int64_t n, double* kappa_out) {
   trace* tr = (trace*)malloc(sizeof(trace));
   for (int64_t i = 0; i < n; ++i) {

@@ -82,6 +82,7 @@ def lib():
         _lib.orc_grad.argtypes = [p, p, i64, p, p, p, p, p]
         _lib.orc_relu_pattern.argtypes = [p, p, i64, p]
         _lib.orc_frame_condition.argtypes = [p, p, i64, p]
+        _lib.orc_direction_gain.argtypes = [p, p, i64, p]
     return _lib
 
 
@@ -304,17 +305,43 @@ def frame_condition(model: Model, q) -> np.ndarray:
     return out
 
 
-def parity(g, o, kappa, tol, kappa_well=50.0, c=64.0, unit=2.0 ** -24, tau=None):
+def direction_gain(model: Model, q) -> np.ndarray:
+    """Per query and RGB channel: sum over the decoder's direction inputs of
+    |d y / d x| through the query's ReLU pattern (with the cosine factor):
+    a first-order bound on how far y moves per unit of direction error."""
+    n = _nq(q)
+    out = np.zeros((n, 3), dtype=np.float64)
+    if n:
+        qv = _QueryView(q, n)
+        lib().orc_direction_gain(C.byref(model._s), C.byref(qv.s), n, _ptr(out))
+    return out
+
+
+def band_gain(model: Model, q, kappa, kappa_well=50.0) -> np.ndarray:
+    """direction_gain for the queries beyond kappa_well (zeros elsewhere,
+    where parity does not read it)."""
+    kappa = np.asarray(kappa)
+    out = np.zeros((len(kappa), 3), dtype=np.float64)
+    idx = np.nonzero(kappa > kappa_well)[0]
+    if len(idx):
+        out[idx] = direction_gain(model, {k: np.asarray(v)[idx] for k, v in q.items() if v is not None})
+    return out
+
+
+def parity(g, o, kappa, tol, gain=None, kappa_well=50.0, eps=2.0 ** -18, tau=None):
     """Element-wise parity with a conditioning-aware bound.
 
-    rel_i = max_c |g - o| / max(|o|, tau), tau = RMS of o.  Queries whose
-    frame condition number is at most kappa_well must meet `tol`; beyond it
-    the bound is tol + c * kappa * unit: the evaluation's own error budget
-    plus the growth of the frame arithmetic's rounding (unit roundoff
-    `unit`) through an ill-conditioned frame, a relative error e of the raw
-    frame outputs moving the frame by up to (1 + 2 kappa) e.  `tau` overrides the
-    RMS floor (a few queries cut from a larger batch keep that batch's
-    floor).  Returns (ok, stats)."""
+    rel = |g - o| / max(|o|, tau) per channel, tau = RMS of o.  Queries whose
+    frame condition number kappa is at most kappa_well must meet `tol`.
+    Beyond it the bound adds the frame arithmetic's error as the decoder
+    sees it: the raw frame outputs carry a relative error of at most eps
+    (measured against the sum of their terms' magnitudes, which kappa
+    includes), which moves the frame, and so every transformed direction, by
+    at most (1 + 2 kappa) eps; the decoder turns that into at most
+    gain * (1 + 2 kappa) eps on the output (`gain` from direction_gain).
+    Without `gain` the decoder's gain relative to max(|o|, tau) is taken as
+    1/2.  `tau` overrides the RMS floor (a few queries cut from a larger
+    batch keep that batch's floor).  Returns (ok, stats)."""
     g = np.asarray(g, dtype=np.float64).reshape(-1, 3)
     o = np.asarray(o, dtype=np.float64).reshape(-1, 3)
     kappa = np.asarray(kappa, dtype=np.float64)
@@ -324,21 +351,24 @@ def parity(g, o, kappa, tol, kappa_well=50.0, c=64.0, unit=2.0 ** -24, tau=None)
         tau = float(np.sqrt(np.mean(o * o)))
     tau = max(tau, 1e-30)
     den = np.maximum(np.abs(o), tau)
-    rel = (np.abs(g - o) / den).max(axis=1)
+    relc = np.abs(g - o) / den
+    rel = relc.max(axis=1)
     well = kappa <= kappa_well
-    bound = np.where(well, tol, tol + c * kappa * unit)
-    ok = bool(np.all(rel <= bound)) and bool(np.all(np.isfinite(g)))
+    rel_gain = np.full_like(o, 0.5) if gain is None else np.asarray(gain, dtype=np.float64).reshape(-1, 3) / den
+    boundc = np.where(well[:, None], tol, tol + eps * (1.0 + 2.0 * kappa[:, None]) * rel_gain)
+    ok = bool(np.all(relc <= boundc)) and bool(np.all(np.isfinite(g)))
+    over = (relc / boundc).max(axis=1)
     bins = {}
     for lo, hi in ((0, 10), (10, 50), (50, 300), (300, 3000), (3000, np.inf)):
         sel = (kappa > lo) & (kappa <= hi)
         if sel.any():
             bins[f"({lo},{hi}]"] = {"n": int(sel.sum()), "max_rel": float(rel[sel].max()),
-                                   "max_rel_over_kappa_u": float((rel[sel] / (kappa[sel] * unit)).max())}
+                                   "max_over_bound": float(over[sel].max())}
     st = {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
           "max_rel_well_conditioned": float(rel[well].max()) if well.any() else 0.0,
           "max_rel_ill_conditioned": float(rel[~well].max()) if (~well).any() else 0.0,
           "ill_conditioned": int((~well).sum()), "n": int(len(rel)),
-          "worst_over_bound": float((rel / bound).max()), "by_kappa": bins}
+          "worst_over_bound": float(over.max()), "by_kappa": bins}
     return ok, st
 
 

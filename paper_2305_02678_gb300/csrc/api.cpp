@@ -327,12 +327,15 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
     for (float v : encw)
       if (!std::isfinite(v)) return fail(NAM_ERR_INVALID_ARG, "non-finite encoder weight");
   }
-  std::vector<float> smp;
+  std::vector<uint8_t> smp;
   if (d->sampler_hidden) {
-    smp.resize(kSamplerFloats);
-    cudaMemcpy(smp.data(), d->sampler_weights, kSamplerFloats * 4, kind);
-    for (float v : smp)
+    std::vector<float> w(kSamplerFloats);
+    cudaMemcpy(w.data(), d->sampler_weights, kSamplerFloats * 4, kind);
+    for (float v : w)
       if (!std::isfinite(v)) return fail(NAM_ERR_INVALID_ARG, "non-finite sampler weight");
+    smp.resize(sampler_blob_bytes());
+    if (pack_sampler_blob(w.data(), smp.data()) != 0)
+      return fail(NAM_ERR_UNSUPPORTED, "sampler weight of magnitude >= 32768");
   }
 
   nam_material m = new nam_material_s();
@@ -350,7 +353,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
       return fail(NAM_ERR_UNSUPPORTED, "no tensor-core kernel for this shape/precision");
     }
   }
-  uint64_t resident = pyr_bytes + blob_bytes + (uint64_t)np * 4 + (uint64_t)smp.size() * 4 +
+  uint64_t resident = pyr_bytes + blob_bytes + (uint64_t)np * 4 + (uint64_t)smp.size() +
                       4ull * encw.size() * 4;
   m->enc_in = d->encoder_inputs;
   m->enc_n = (int64_t)encw.size();
@@ -369,7 +372,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   int e = dev_alloc(ctx, &m->pyramid, pyr_bytes);
   if (!e) e = dev_alloc(ctx, (void**)&m->params, np * 4);
   if (!e && blob_bytes) e = dev_alloc(ctx, &m->blob, blob_bytes);
-  if (!e && !smp.empty()) e = dev_alloc(ctx, (void**)&m->sampler, smp.size() * 4);
+  if (!e && !smp.empty()) e = dev_alloc(ctx, &m->sampler, smp.size());
   if (!e && !encw.empty()) e = dev_alloc(ctx, (void**)&m->enc, 4 * encw.size() * 4);
   if (!e && d->trainable) {
     const size_t nb = (m->pyr_off + pd.texels * 8) * 4;
@@ -384,7 +387,7 @@ extern "C" nam_status nam_create_material(nam_ctx* ctx, const nam_material_desc*
   e = (int)cudaMemcpy(m->pyramid, d->pyramid, pyr_bytes,
                       d->params_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice);
   if (!e) e = (int)cudaMemcpy(m->params, master.data(), np * 4, cudaMemcpyHostToDevice);
-  if (!e && !smp.empty()) e = (int)cudaMemcpy(m->sampler, smp.data(), smp.size() * 4, cudaMemcpyHostToDevice);
+  if (!e && !smp.empty()) e = (int)cudaMemcpy(m->sampler, smp.data(), smp.size(), cudaMemcpyHostToDevice);
   if (!e && !encw.empty()) {
     e = (int)cudaMemcpy(m->enc, encw.data(), encw.size() * 4, cudaMemcpyHostToDevice);
     if (!e) e = (int)cudaMemset(m->enc + encw.size(), 0, 3 * encw.size() * 4);  // gradient, Adam m, v

@@ -22,7 +22,7 @@ struct nam_material_s {
   void* pyramid = nullptr;    // device pyramid (FP16 or FP32 texels)
   void* blob = nullptr;       // tensor-core weight blob (F16 / FP8)
   float* params = nullptr;    // FP32 masters (frame then decoder)
-  float* sampler = nullptr;   // FP32 importance-sampler weights, or null
+  void* sampler = nullptr;    // importance-sampler weights as tensor-core operands, or null
   int64_t pyr_off = 0;        // trainable: offset of the pyramid block in
                               // adam_m / adam_v / grad (n_params rounded up
                               // to 16 bytes, for the 16-byte vector atomics)

@@ -138,8 +138,12 @@ int pack_tc_blob(const Shape& s, int precision, const float* frame, const float*
 
 // Importance sampler (11 -> 32 -> 32 -> 32 -> 9 FP32 MLP + proxy density).
 constexpr int kSamplerFloats = (11 * 32 + 32) + 2 * (32 * 32 + 32) + (32 * 9 + 9);
+// The sampler's weights packed as tensor-core operands (binary16 hi/lo
+// splits of the FP32 masters); -1 if a weight is beyond the split's range.
+size_t sampler_blob_bytes();
+int pack_sampler_blob(const float* weights, uint8_t* out);
 // mode 0: density of each query's wo; mode 1: sample from u [n][3].
-int launch_sampler(const LaunchCommon& L, const float* sampler, int mode, const float* u, float* wo_out,
+int launch_sampler(const LaunchCommon& L, const void* sampler_blob, int mode, const float* u, float* wo_out,
                    float* pdf_out, void* stream);
 
 // Backward / training.

@@ -98,7 +98,9 @@ def _check(gctx, oracle, mats, models, q, ids, n, flags=0, label="", precision=N
         assert np.array_equal(got[sel], ref), (label, k)
         if precision is not None:
             sq = {f: v[sel] for f, v in q.items()}
-            ok, st = oracle.parity(got[sel], oracle.eval(om, sq), oracle.frame_condition(om, sq), TOL[precision])
+            kappa = oracle.frame_condition(om, sq)
+            ok, st = oracle.parity(got[sel], oracle.eval(om, sq), kappa, TOL[precision],
+                                   gain=oracle.band_gain(om, sq, kappa))
             assert ok, (label, k, st)
     binned = torch.full((n, 3), -7.0, device="cuda")
     B.nam_eval_binned(gctx.h, [m.h for m in mats], dq, torch.from_numpy(ids).cuda(), n, binned,

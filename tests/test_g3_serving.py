@@ -131,6 +131,7 @@ def test_served_frame_matches_the_oracle(scene, oracle):
     n = len(q["u"])
     o = np.zeros((n, 3))
     kappa = np.zeros(n)
+    gain = np.zeros((n, 3))
     for k, (pyr, model) in enumerate(scene[0]):
         idx = np.concatenate([np.arange(s, s + c) for (s, c), m in zip(tiles, mt) if m == k] or [np.zeros(0, int)])
         if len(idx) == 0:
@@ -139,7 +140,8 @@ def test_served_frame_matches_the_oracle(scene, oracle):
         qk = {f: v[idx] for f, v in q.items()}
         o[idx] = oracle.eval(om, qk)
         kappa[idx] = oracle.frame_condition(om, qk)
-    ok, s = oracle.parity(g, o, kappa, 2e-3)
+        gain[idx] = oracle.band_gain(om, qk, kappa[idx])
+    ok, s = oracle.parity(g, o, kappa, 2e-3, gain=gain)
     print(f"served frame {n} queries: max {s['max_rel']:.3e} (kappa <= 50: {s['max_rel_well_conditioned']:.3e}), "
           f"ill-conditioned {s['ill_conditioned']}")
     assert ok, s

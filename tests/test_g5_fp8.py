@@ -61,7 +61,7 @@ def _check_fp8(oracle, w, scales, g, filt=0, addr=0, label="fp8", q=None):
                       params="fp8")
     o = oracle.eval(om, q)
     kappa = oracle.frame_condition(om, q)
-    ok, st = oracle.parity(g, o, kappa, TOL_F8)
+    ok, st = oracle.parity(g, o, kappa, TOL_F8, gain=oracle.band_gain(om, q, kappa))
     print(f"{label}: vs oracle (E4M3 hidden weights, FP64 activations) max {st['max_rel']:.3e} "
           f"(well-conditioned {st['max_rel_well_conditioned']:.3e}) mean {st['mean_rel']:.3e}, "
           f"ill-conditioned {st['ill_conditioned']}/{st['n']}")

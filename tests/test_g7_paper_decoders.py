@@ -28,8 +28,10 @@ def _setup(seed, H, NH, frame, n=20000, latent="f16"):
     return W0, H0, L, pyr, model, q
 
 
-def _check(oracle, g, o, kappa, tol, label):
-    ok, st = oracle.parity(g, o, kappa, tol)
+def _check(oracle, g, om, q, tol, label):
+    o = oracle.eval(om, q)
+    kappa = oracle.frame_condition(om, q)
+    ok, st = oracle.parity(g, o, kappa, tol, gain=oracle.band_gain(om, q, kappa))
     print(f"{label}: max {st['max_rel']:.3e} (well-conditioned {st['max_rel_well_conditioned']:.3e}), "
           f"ill-conditioned {st['ill_conditioned']}/{st['n']}")
     assert ok, st
@@ -44,7 +46,7 @@ def test_fp32_paper_sizes(gctx, oracle, H, NH, frame):
     g = mat.eval(to_device(q)).cpu().numpy()
     mat.destroy()
     om = oracle.Model(W0, H0, L, pyr, model["frame"], model["decoder"])
-    _check(oracle, g, oracle.eval(om, q), oracle.frame_condition(om, q), 1e-5, f"fp32 {frame} {NH}x{H}")
+    _check(oracle, g, om, q, 1e-5, f"fp32 {frame} {NH}x{H}")
 
 
 @pytest.mark.parametrize("H,NH", SIZES)
@@ -58,7 +60,7 @@ def test_fp16_paper_sizes(gctx, oracle, H, NH, frame, latent):
     mat.destroy()
     gctx.check()
     om = oracle.Model(W0, H0, L, pyr, model["frame"], model["decoder"], params="fp16")
-    _check(oracle, g, oracle.eval(om, q), oracle.frame_condition(om, q), 2e-3, f"fp16 {frame} {NH}x{H} {latent}")
+    _check(oracle, g, om, q, 2e-3, f"fp16 {frame} {NH}x{H} {latent}")
 
 
 def test_paper_form_multi_material_and_ragged(gctx):

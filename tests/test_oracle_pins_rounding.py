@@ -136,3 +136,63 @@ def test_frame_condition_closed_forms(oracle, n_raw, t_raw, kappa):
     m = _model(oracle, _b1(1.0), frame=frame)
     k = oracle.frame_condition(m, _queries())
     assert np.allclose(k, kappa, rtol=1e-6)
+
+
+@pytest.mark.parametrize("cosine", [False, True])
+def test_direction_gain_matches_finite_differences(oracle, cosine):
+    """direction_gain is the sum over the six direction inputs of
+    |dy/dx| through the ReLU pattern: against central differences of the
+    oracle's decoder alone (no frame MLP, so the inputs are (z, wi, wo)),
+    with two step sizes that must agree (a pair straddling a ReLU kink is
+    skipped); with the cosine factor every channel scales by max(0, wi.z)."""
+    import workloads as W
+    rng = W.rng_streams(4242, 3)
+    pyr = W.make_pyramid(rng[0], 32, 32, 6, dtype=np.float16)
+    model = W.make_model(rng[1], (14, 32, 32, 3), None)
+    om = oracle.Model(32, 32, 6, pyr, model["frame"], model["decoder"], out_cosine=cosine)
+    q = W.uniform_queries(rng[2], 400, 5.0)
+    gain = oracle.direction_gain(om, q)
+    z = oracle.latent(om, q)
+    x = np.concatenate([z, np.stack([q["wix"], q["wiy"], q["wiz"], q["wox"], q["woy"], q["woz"]], 1)], 1)
+    x = x.astype(np.float64)
+
+    def fd(h):
+        J = np.zeros((len(x), 3, 6))
+        for k in range(6):
+            xp, xm = x.copy(), x.copy()
+            xp[:, 8 + k] += h
+            xm[:, 8 + k] -= h
+            J[:, :, k] = (oracle.mlp(om, xp)[:, :3] - oracle.mlp(om, xm)[:, :3]) / (2 * h)
+        return np.abs(J).sum(axis=2)
+
+    g1, g2 = fd(1e-6), fd(2.5e-7)
+    cosf = np.maximum(q["wiz"].astype(np.float64), 0.0)[:, None] if cosine else 1.0
+    g1, g2 = g1 * cosf, g2 * cosf
+    scale = np.maximum(np.abs(g1), 1e-3)
+    smooth = (np.abs(g1 - g2) / scale < 1e-6).all(axis=1)
+    assert smooth.mean() > 0.95
+    assert np.allclose(gain[smooth], g1[smooth], rtol=1e-6, atol=1e-9)
+    assert (gain > 0).any()
+
+
+def test_gain_bound_reduces_to_unit_gain_form(oracle):
+    """parity's band bound with gain = den / 2 equals the bound without a
+    gain; a larger gain loosens only the queries beyond kappa = 50."""
+    rng = np.random.default_rng(5)
+    o = rng.normal(size=(6, 3)) + 2.0
+    kappa = np.array([1.0, 10.0, 60.0, 100.0, 1000.0, 5e4])
+    tau = float(np.sqrt(np.mean(o * o)))
+    den = np.maximum(np.abs(o), tau)
+    eps = 2.0 ** -18
+    # errors placed exactly at 0.99 of the unit-gain bound
+    b = np.where(kappa[:, None] <= 50, 2e-3, 2e-3 + eps * (1 + 2 * kappa[:, None]) * 0.5)
+    g = o + 0.99 * b * den
+    ok0, st0 = oracle.parity(g, o, kappa, 2e-3)
+    ok1, st1 = oracle.parity(g, o, kappa, 2e-3, gain=den / 2)
+    assert ok0 and ok1 and abs(st0["worst_over_bound"] - st1["worst_over_bound"]) < 1e-12
+    g2 = o + 1.01 * b * den
+    assert not oracle.parity(g2, o, kappa, 2e-3)[0]
+    ok3, _ = oracle.parity(g2, o, kappa, 2e-3, gain=np.where(kappa[:, None] > 50, den, den / 2))
+    assert not ok3  # the well-conditioned rows still fail at 1.01 tol
+    g4 = np.where(kappa[:, None] > 50, g2, g)
+    assert oracle.parity(g4, o, kappa, 2e-3, gain=den)[0]
