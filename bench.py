@@ -16,7 +16,7 @@ stream's p50/p99 frame latency, the FP64 oracle on the host cores
 (cpu_baseline) and the clocks seen while timing.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--no-serve] [--serve-frames F] [--serve-repeats R] [--no-sweep]
+                  [--no-serve] [--serve-frames F] [--serve-repeats R] [--no-sweep] [--legs L]
 """
 from __future__ import annotations
 
@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--serve-repeats", type=int, default=4)
     ap.add_argument("--serve-trace", default=None, help="write every served frame's timeline (.npz) here")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--legs", default="precision,paper,binned,scene,sampling",
+                    help="which of the sweep legs run (comma list; --no-sweep runs none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-sweep4k", action="store_true")
     ap.add_argument("--train-steps", type=int, default=2000)
@@ -496,7 +498,8 @@ def run_ours(args):
     # ---- precision sweep on the same workload ----------------------------
     sweep = {}
     out8 = None
-    if not args.no_sweep:
+    legs = set() if args.no_sweep else set(args.legs.split(","))
+    if "precision" in legs:
         mat32 = ctx.material(w["W0"], w["H0"], w["L"], w["pyramid"], m["frame"], m["decoder"],
                              precision=B.NAM_PREC_F32)
         out32 = torch.empty((n, 3), device=dev)
@@ -533,19 +536,19 @@ def run_ours(args):
         sweep4k, outs4k = run_sweep_4k(ctx, dev, stream, flush, args)
     # ---- the paper's decoder sizes with its frame form ----------------------
     paper = None
-    if not args.no_sweep:
+    if "paper" in legs:
         paper = run_paper_decoders(ctx, dev, stream, flush, w, dq, n, args)
     # ---- per-pixel materials through the binning pre-pass ------------------
     binned = None
-    if not args.no_sweep:
+    if "binned" in legs:
         binned = run_binned(ctx, dev, stream, flush, w, dq, n, args)
     # ---- the synthetic-scene harness at 1080p --------------------------------
     scene = None
-    if not args.no_sweep:
+    if "scene" in legs:
         scene = run_scene(ctx, dev, stream, args)
     # ---- importance sampling on the 1080p frame ------------------------------
     sampling = None
-    if not args.no_sweep:
+    if "sampling" in legs:
         sampling = run_sampling(ctx, dev, stream, flush, w, dq, n, args, texel_bytes=texel_bytes)
     # ---- training: 2,000 Adam steps on the procedural GGX target ------------
     training = None
@@ -637,6 +640,13 @@ def run_sweep_4k(ctx, dev, stream, flush, args):
         outs[name] = out
     for name in ("fp16", "fp8"):
         res[f"{name}_speedup_vs_fp32"] = round(res["fp32_ms"] / res[f"{name}_ms"], 2)
+    # the FP16 launch against the same roofline as the 1080p headline
+    hbm, _, peak_kind = measured_peaks()
+    weight_bytes = int(mat16.info.resident_bytes - w["pyramid"].nbytes - mat16.info.n_params * 4)
+    alg = n * (9 * 4 + 12) + unique_texel_bytes(w) + weight_bytes
+    gbs = alg / (res["fp16_ms"] * 1e-3) / 1e9
+    res["fp16_roofline"] = {"bound": "hbm", "alg_bytes_per_launch": alg, "achieved": round(gbs, 1), "unit": "GB/s",
+                            "peak": hbm, "frac": round(gbs / hbm, 4), "peak_source": peak_kind}
     k = 1 << 20   # error sample: the first 1,048,576 queries
     host = {name: o[:k].cpu().numpy() for name, o in outs.items()}
     for mat in mats.values():
