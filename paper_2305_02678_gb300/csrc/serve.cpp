@@ -1,22 +1,22 @@
 // Serving: continuous batching of frames.
 //
-// nam_submit queues a frame (host arrays).  One scheduler thread per
-// context admits queued frames in arrival order as soon as a stream slot is
-// free and the frame's device buffers fit under the HBM budget; admission
-// enqueues, on that slot's stream, the host->device copies, one
-// multi-material tensor-core launch over the frame's tiles (each tile one
-// material, so every 128-query MMA tile is material-coherent, the analogue
-// of the paper's coherent warps, Sec. 7.3) and the device->host copy of the
-// RGB; a frame whose queries and output already live in device memory
-// (NAM_FRAME_DEVICE, the renderer's case) needs no copies.  Frames on different slots run concurrently on the GPU, so a frame
-// that arrives while others are in flight starts as soon as a slot frees up.
-// Completion is observed with CUDA events; per-frame latency is
-// finish - arrival on the nam_now() clock.  A frame whose arrival time lies
-// in the future waits in the queue until then, so that a paced stream does
-// not depend on when its caller gets to run.  Each frame's device timeline
-// (copies begin, kernel begins and ends, copies end) is taken with timing
-// events on its stream and mapped onto the nam_now() clock through an
-// anchor event recorded while no frame is on the GPU.
+// nam_submit queues a frame (host arrays, or device arrays with
+// NAM_FRAME_DEVICE).  One scheduler thread per context admits queued frames
+// in submission order, each once its arrival time has come (so that a paced
+// stream does not depend on when its caller gets to run), a stream slot is
+// free and the frame's device buffers fit under the HBM budget.  The slot's
+// launcher thread then enqueues on the slot's stream the host->device
+// copies, one multi-material tensor-core launch over the frame's tiles (each
+// tile one material, so every 128-query MMA tile is material-coherent, the
+// analogue of the paper's coherent warps, Sec. 7.3) and the device->host
+// copy of the RGB; a device frame (the renderer's case) needs no copies.
+// Frames on different slots run concurrently on the GPU, and a CUDA call
+// that sleeps inside the driver holds up only its own slot.  The scheduler
+// observes completion with CUDA events; per-frame latency is finish -
+// arrival on the nam_now() clock.  Each frame's device timeline (copies
+// begin, kernel begins and ends, copies end) is taken with timing events on
+// its stream and mapped onto the nam_now() clock through an anchor event
+// recorded while no frame is on the GPU.
 #include <cuda_runtime.h>
 #ifdef __linux__
 #include <sys/prctl.h>
@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <memory>
 
 #include "nam_ctx.h"
 
@@ -51,7 +52,10 @@ struct Slot {
   cudaEvent_t begin = nullptr;     // before the frame's first copy
   cudaEvent_t k_begin = nullptr;   // before its kernel
   cudaEvent_t k_end = nullptr;     // after its kernel
-  Job* job = nullptr;
+  Job* job = nullptr;        // admitted frame (the scheduler sets and clears it)
+  Job* pending = nullptr;    // handed to the slot's launcher thread
+  bool launched = false;     // the launcher has enqueued job's work (or failed)
+  nam_status launch_status = NAM_OK;
   // pinned staging for the frame's work table: an upload from pageable
   // memory could make the scheduler thread wait for the slot's stream.
   // Allocated with the slot (kTableBytes); a frame that outgrows it gets a
@@ -67,8 +71,10 @@ struct Slot {
 constexpr size_t kTableBytes = 4u << 20;
 
 struct ServeState {
-  std::mutex mu;
+  std::mutex mu;                    // guards everything below but the CUDA objects
   std::condition_variable cv;       // wakes the scheduler
+  std::unique_ptr<std::condition_variable[]> launcher_cv;  // one per slot
+  std::vector<std::thread> launchers;
   std::condition_variable done_cv;  // wakes nam_wait
   std::deque<Job*> queue;
   std::map<nam_ticket, Job*> jobs;
@@ -231,6 +237,35 @@ static nam_status launch_job(nam_ctx* ctx, Slot& slot, Job* j) {
   return NAM_OK;
 }
 
+// One launcher thread per slot enqueues its frames' work (launch_job), so
+// that a CUDA call that sleeps inside the driver delays only its own frame:
+// the scheduler thread never calls into a slot's stream.
+static void launcher(nam_ctx* ctx, int k) {
+  ServeState* S = ctx->serve;
+  Slot& sl = S->slots[k];
+  DeviceGuard g(ctx->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  while (true) {
+    S->launcher_cv[k].wait(lk, [&] { return S->stop || sl.pending != nullptr; });
+    if (!sl.pending) break;  // stopping, nothing handed over
+    Job* j = sl.pending;
+    sl.pending = nullptr;
+    lk.unlock();
+    j->st.start_s = nam_now();
+    nam_status st = launch_job(ctx, sl, j);
+    j->st.enqueued_s = nam_now();
+    if (st != NAM_OK) {
+      if (j->dev) cudaFreeAsync(j->dev, sl.stream);
+      j->dev = nullptr;
+      cudaStreamSynchronize(sl.stream);
+    }
+    lk.lock();
+    sl.launch_status = st;
+    sl.launched = true;
+    S->cv.notify_all();
+  }
+}
+
 static void scheduler(nam_ctx* ctx) {
   ServeState* S = ctx->serve;
   DeviceGuard g(ctx->device);
@@ -242,30 +277,37 @@ static void scheduler(nam_ctx* ctx) {
   std::unique_lock<std::mutex> lk(S->mu);
   while (true) {
     bool progressed = false;
-    // completions
+    // completions (and launches that failed)
     for (Slot& sl : S->slots) {
-      if (!sl.job) continue;
-      cudaError_t q = cudaEventQuery(sl.done);
-      if (q == cudaErrorNotReady) continue;
+      if (!sl.job || !sl.launched) continue;
+      nam_status st = sl.launch_status;
+      cudaError_t q = cudaSuccess;
+      if (st == NAM_OK) {
+        q = cudaEventQuery(sl.done);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) st = NAM_ERR_CUDA;
+      }
       Job* j = sl.job;
       sl.job = nullptr;
+      sl.launched = false;
       S->in_flight--;
       budget_release(ctx, j->bytes);
       S->serving_bytes -= j->bytes;
-      if (q == cudaSuccess) {
+      if (st == NAM_OK) {
         j->st.gpu_begin_s = device_time(S, sl.begin);
         j->st.gpu_kernel_begin_s = device_time(S, sl.k_begin);
         j->st.gpu_kernel_end_s = device_time(S, sl.k_end);
         j->st.gpu_end_s = device_time(S, sl.done);
       }
-      finish_job(S, j, q == cudaSuccess ? NAM_OK : NAM_ERR_CUDA);
+      finish_job(S, j, st);
       progressed = true;
     }
     if (S->stop && S->in_flight == 0) break;
     // admissions, in submission order, each once its arrival time has come
     double next_arrival = 0.0;
     if (!S->stop && !ctx->fault_stall.load()) {
-      for (Slot& sl : S->slots) {
+      for (size_t k = 0; k < S->slots.size(); ++k) {
+        Slot& sl = S->slots[k];
         if (sl.job || S->queue.empty()) continue;
         Job* j = S->queue.front();
         const double now = nam_now();
@@ -279,22 +321,11 @@ static void scheduler(nam_ctx* ctx) {
         j->st.in_flight_at_admit = (int32_t)S->in_flight;
         S->in_flight++;
         j->st.admit_s = now;
-        j->st.slot = (int32_t)(&sl - S->slots.data());
+        j->st.slot = (int32_t)k;
         sl.job = j;
-        lk.unlock();
-        j->st.start_s = nam_now();
-        nam_status st = launch_job(ctx, sl, j);
-        j->st.enqueued_s = nam_now();
-        lk.lock();
-        if (st != NAM_OK) {
-          if (j->dev) cudaFreeAsync(j->dev, sl.stream);
-          cudaStreamSynchronize(sl.stream);
-          sl.job = nullptr;
-          S->in_flight--;
-          budget_release(ctx, j->bytes);
-          S->serving_bytes -= j->bytes;
-          finish_job(S, j, st);
-        }
+        sl.pending = j;
+        sl.launched = false;
+        S->launcher_cv[k].notify_one();
         progressed = true;
       }
     }
@@ -345,7 +376,9 @@ static nam_status ensure_serving(nam_ctx* ctx) {
     return cuda_fail((int)e, "serving: stream creation");
   }
   take_anchor(S);
+  S->launcher_cv.reset(new std::condition_variable[S->slots.size()]);
   ctx->serve = S;
+  for (size_t k = 0; k < S->slots.size(); ++k) S->launchers.emplace_back(launcher, ctx, (int)k);
   S->thread = std::thread(scheduler, ctx);
   return NAM_OK;
 }
@@ -368,7 +401,12 @@ void nam::serve_stop(nam_ctx* ctx) {
   }
   ctx->fault_stall.store(false);
   S->cv.notify_all();
-  S->thread.join();
+  S->thread.join();  // returns once no frame is in flight
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    for (size_t k = 0; k < S->slots.size(); ++k) S->launcher_cv[k].notify_all();
+  }
+  for (std::thread& t : S->launchers) t.join();
   DeviceGuard g(ctx->device);
   for (Slot& sl : S->slots) {
     cudaStreamSynchronize(sl.stream);
