@@ -731,9 +731,9 @@ def run_binned(ctx, dev, stream, flush, w, dq, n, args, n_mat=16):
     return {"workload": f"fp16-2048sq-1920x1080, {n_mat} materials, material drawn per pixel",
             "binned_ms": round(t, 4), "binned_evals_per_s": round(n / (t * 1e-3), 1),
             "single_material_ms": round(t1, 4), "overhead_vs_single": round(t / t1, 3),
-            "note": "binning passes (count, plan, scatter of 40 B of query fields per query, unbin of the RGB) "
-                    "plus the chunked tensor-core launch, whose CTAs restage weights when a chunk's material "
-                    "changes",
+            "note": "binning passes (count, plan, a permutation of the query indices by material) plus the "
+                    "chunked tensor-core launch, which reads each query through the permutation, writes its RGB "
+                    "in place, and restages a warpgroup's weights when its chunk's material changes",
             "select": {
                 "per_pixel_ms": round(t_sel_pp, 4), "per_pixel_vs_binned": round(t_sel_pp / t, 3),
                 "regions_workload": f"{n_mat} screen regions (nearest of {n_mat} random sites), "

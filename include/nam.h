@@ -321,18 +321,20 @@ nam_status nam_eval_multi(nam_ctx* ctx, const nam_material* materials, int32_t n
 /* Evaluation of queries whose material varies per query, with no tile
  * coherence (Sec. 7.3: the paper has the ray tracer reorder shading work so
  * that threads evaluating the same material run together).  Bins the queries
- * by material on the device -- per-material histogram, exclusive scan,
- * scatter of each query into its material's contiguous range -- evaluates the
- * ranges in one chunked launch of the materials' kernel and writes rgb_out
- * [n][3] (device) in the caller's order.  Each query's result is bitwise
+ * by material on the device -- per-material histogram, exclusive scan, a
+ * permutation that puts each query's index in its material's contiguous
+ * range -- evaluates the ranges in one chunked launch of the materials'
+ * kernel, which reads each query through the permutation, and writes
+ * rgb_out [n][3] (device) in the caller's order.  Each query's result is bitwise
  * that of nam_eval on its material: no query's value depends on which others
  * share its range.  material_ids: device int32 [n], each in [0, nmat); a query
  * with an id outside that range is not evaluated (its rgb_out entries are
  * left as they were) and nam_check_device_error then reports
  * NAM_ERR_DEVICE_ASSERT.  Materials as for nam_eval_multi (tensor-core
  * precisions, one MLP shape and pyramid geometry); nmat <=
- * NAM_MAX_BIN_MATERIALS; n < 2^31.  Temporary device memory (≈ 56 bytes
- * per query) comes from the context's stream-ordered pool. */
+ * NAM_MAX_BIN_MATERIALS; n < 2^31.  Temporary device memory (≈ 4 bytes
+ * per query, 16 per 128-query chunk and 8 per material) comes from the
+ * context's stream-ordered pool. */
 #define NAM_MAX_BIN_MATERIALS 4096
 nam_status nam_eval_binned(nam_ctx* ctx, const nam_material* mats, int32_t n_materials, const nam_queries* q,
                            const int32_t* material_ids, int64_t n, float* rgb_out, void* stream, uint32_t flags);

@@ -1,21 +1,20 @@
 // Material binning for queries whose material varies per query (Sec. 7.3:
 // the paper has the ray tracer reorder shading work so that threads that
-// evaluate the same material run together).  Four passes on the device:
+// evaluate the same material run together).  Three passes on the device,
+// then the evaluation:
 //   count   per-material histogram (each block sums a segment of queries in
 //           shared memory and adds one count per material to the global
 //           histogram: same-address atomics serialise in L2);
 //   plan    exclusive scan of the counts into per-material cursors, and the
 //           chunk table of the tensor-core kernel (each material's range cut
-//           into 128-query chunks; empty slots have count 0);
-//   scatter each block reserves, per material, one run of slots for its
+//           into 128-query chunks; empty slots have count 0; the number of
+//           chunks in use for the kernel to read on the device);
+//   permute each block reserves, per material, one run of slots for its
 //           segment (one global atomic per block and material) and writes
-//           each query's fields, with the slot's original index, to a slot
-//           of its run: directly at its warp's bump for a segment of a few
-//           materials, else after ordering the segment's query indices by
-//           material in shared memory, so that each run is written to
-//           consecutive slots;
-//   unbin   the kernel's outputs, read in binned order, written back to the
-//           caller's order.
+//           each query's index to a slot of its run;
+//   launch  the chunked tensor-core kernel reads each slot's query through
+//           the permutation (its fields from the caller's arrays) and writes
+//           its RGB in the caller's order.
 // Inside a material's range, runs follow the order in which blocks reserve
 // them and slots inside a run the order in which warps claim them; neither
 // changes any result, since each query is evaluated on its own, and a run
@@ -128,25 +127,23 @@ __global__ void __launch_bounds__(1024) bin_plan_kernel(const uint32_t* __restri
   }
 }
 
-struct Binned {
-  float *u, *v, *lod, *xi, *wix, *wiy, *wiz, *wox, *woy, *woz;
-};
-
-// Scatter.  A segment of at most kDirectMaterials materials writes each query
-// at its warp's bump (a warp's lanes of one material take consecutive
-// slots).  A segment of more is ordered first: the indices of its valid
-// queries are placed in shared memory by material (a local counting sort),
-// then each material's run is written to consecutive slots, its fields read
-// from the segment (L1-resident), so that the global writes of a run are
-// coalesced instead of one sector per 4-byte field.
+// Permutation.  Each query's index goes to a slot of its material's range: a
+// segment of at most kDirectMaterials materials writes each index at its
+// warp's bump (a warp's lanes of one material take consecutive slots); a
+// segment of more is ordered first (the indices of its valid queries placed
+// in shared memory by material, a local counting sort), then each
+// material's run is written to consecutive slots.  Either way a run keeps
+// its segment's queries in their order, so that the chunked launch, which
+// reads every slot's query through the permutation, gathers from few
+// neighbourhoods of the caller's arrays.
 // Shared memory: cnt, run, excl [nmat] each, then the query index and the
 // material of each local position [kSeg] each.
 constexpr int kStage = 1;
 constexpr int kDirectMaterials = 4;  // segments of at most this many materials skip the ordering
 
-__global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, const int32_t* __restrict__ ids,
-                                                               int64_t n, int nmat, const int32_t* __restrict__ tile_k,
-                                                               uint32_t* __restrict__ cursors, Binned out,
+__global__ void __launch_bounds__(kThreads) bin_scatter_kernel(const int32_t* __restrict__ ids, int64_t n, int nmat,
+                                                               const int32_t* __restrict__ tile_k,
+                                                               uint32_t* __restrict__ cursors,
                                                                int32_t* __restrict__ orig) {
   extern __shared__ uint32_t sh[];
   uint32_t* cnt = sh;               // [nmat] this segment's queries per material, then a bump counter
@@ -210,16 +207,6 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, cons
       const uint32_t act = __ballot_sync(0xffffffffu, m >= 0);
       if (m < 0) continue;
       const uint32_t slot = run[m] + warp_bump(cnt, m, act);
-      out.u[slot] = __ldg(q.u + i);
-      out.v[slot] = __ldg(q.v + i);
-      out.lod[slot] = __ldg(q.lod + i);
-      if (q.xi) out.xi[slot] = __ldg(q.xi + i);
-      out.wix[slot] = __ldg(q.wix + i);
-      out.wiy[slot] = __ldg(q.wiy + i);
-      out.wiz[slot] = __ldg(q.wiz + i);
-      out.wox[slot] = __ldg(q.wox + i);
-      out.woy[slot] = __ldg(q.woy + i);
-      out.woz[slot] = __ldg(q.woz + i);
       orig[slot] = (int32_t)i;
     }
     return;
@@ -241,30 +228,10 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(QueryPtrs q, cons
     const int m = smat[p];
     const int64_t i = stage[p];
     const uint32_t slot = run[m] + (p - excl[m]);
-    out.u[slot] = __ldg(q.u + i);
-    out.v[slot] = __ldg(q.v + i);
-    out.lod[slot] = __ldg(q.lod + i);
-    if (q.xi) out.xi[slot] = __ldg(q.xi + i);
-    out.wix[slot] = __ldg(q.wix + i);
-    out.wiy[slot] = __ldg(q.wiy + i);
-    out.wiz[slot] = __ldg(q.wiz + i);
-    out.wox[slot] = __ldg(q.wox + i);
-    out.woy[slot] = __ldg(q.woy + i);
-    out.woz[slot] = __ldg(q.woz + i);
     orig[slot] = (int32_t)i;
   }
 }
 
-__global__ void __launch_bounds__(kThreads) unbin_kernel(const float* __restrict__ binned, const int32_t* __restrict__ orig,
-                                                         int64_t n, float* __restrict__ rgb) {
-  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t i = __ldg(orig + p);
-    if (i < 0) continue;  // slot of a query with an invalid material id
-    rgb[3 * (int64_t)i + 0] = binned[3 * p + 0];
-    rgb[3 * (int64_t)i + 1] = binned[3 * p + 1];
-    rgb[3 * (int64_t)i + 2] = binned[3 * p + 2];
-  }
-}
 
 // Per-tile selection (Sec. 7.1: the shader picks per warp between a code
 // path for coherent and one for divergent execution).  A tcgen05 MMA covers
@@ -409,9 +376,10 @@ __global__ void __launch_bounds__(kWriteThreads) select_write_kernel(const int32
 }  // namespace
 
 size_t bin_scratch_bytes(int64_t n, int nmat, bool xi) {
+  (void)xi;
   const size_t f = ((size_t)n * 4 + 255) / 256 * 256;
-  return (xi ? 10 : 9) * f + f /* orig */ + 3 * f /* binned rgb */ + 2 * (((size_t)nmat * 4 + 255) / 256 * 256) +
-         256 /* chunks in use */ + ((size_t)max_bin_chunks(n, nmat) * sizeof(Chunk) + 255) / 256 * 256;
+  return f /* slot -> query */ + 2 * (((size_t)nmat * 4 + 255) / 256 * 256) + 256 /* chunks in use */ +
+         ((size_t)max_bin_chunks(n, nmat) * sizeof(Chunk) + 255) / 256 * 256;
 }
 
 int32_t max_bin_chunks(int64_t n, int nmat) { return (int32_t)((n + 127) / 128 + nmat); }
@@ -423,23 +391,7 @@ static int bin_eval(const BinArgs& a, const int32_t* tile_k, cudaStream_t s) {
   const int64_t n = a.n;
   const size_t f = ((size_t)n * 4 + 255) / 256 * 256;
   uint8_t* p = (uint8_t*)a.scratch;
-  Binned b;
-  b.u = (float*)p; p += f;
-  b.v = (float*)p; p += f;
-  b.lod = (float*)p; p += f;
-  b.wix = (float*)p; p += f;
-  b.wiy = (float*)p; p += f;
-  b.wiz = (float*)p; p += f;
-  b.wox = (float*)p; p += f;
-  b.woy = (float*)p; p += f;
-  b.woz = (float*)p; p += f;
-  b.xi = nullptr;
-  if (a.L.q.xi) {
-    b.xi = (float*)p;
-    p += f;
-  }
   int32_t* orig = (int32_t*)p; p += f;
-  float* brgb = (float*)p; p += 3 * f;
   const size_t mb = ((size_t)a.nmat * 4 + 255) / 256 * 256;
   uint32_t* counts = (uint32_t*)p; p += mb;
   uint32_t* cursors = (uint32_t*)p; p += mb;
@@ -448,7 +400,6 @@ static int bin_eval(const BinArgs& a, const int32_t* tile_k, cudaStream_t s) {
   const int32_t maxc = max_bin_chunks(n, a.nmat);
 
   int e = (int)cudaMemsetAsync(counts, 0, (size_t)a.nmat * 4, s);
-  if (!e) e = (int)cudaMemsetAsync(orig, 0xff, (size_t)n * 4, s);
   if (e) return e;
   const int gseg = (int)((n + kSeg - 1) / kSeg);
   bin_count_kernel<<<gseg, kThreads, a.nmat * sizeof(uint32_t), s>>>(a.ids, n, a.nmat, tile_k, counts, a.L.err);
@@ -459,21 +410,19 @@ static int bin_eval(const BinArgs& a, const int32_t* tile_k, cudaStream_t s) {
     cudaFuncSetAttribute(bin_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (3 * NAM_MAX_BIN_MATERIALS + (kStage + 1) * kSeg) * (int)sizeof(uint32_t));
   });
-  bin_scatter_kernel<<<gseg, kThreads, scatter_smem, s>>>(a.L.q, a.ids, n, a.nmat, tile_k, cursors, b, orig);
+  bin_scatter_kernel<<<gseg, kThreads, scatter_smem, s>>>(a.ids, n, a.nmat, tile_k, cursors, orig);
   e = (int)cudaGetLastError();
   if (e) return e;
+  // the chunked launch reads each slot's query through the permutation and
+  // writes its RGB in the caller's order
   LaunchCommon L = a.L;
-  L.q = QueryPtrs{b.u, b.v, b.lod, b.wix, b.wiy, b.wiz, b.wox, b.woy, b.woz, b.xi};
-  L.rgb = brgb;
+  L.rgb = a.rgb_out;
   L.chunks = chunks;
   L.n_chunks = maxc;
   L.n_chunks_dev = n_used;
   L.row_ids = nullptr;
-  e = launch_material(L, a.precision, s);
-  if (e) return e;
-  // one thread per slot: the scattered 12-byte writes want many in flight
-  unbin_kernel<<<(int)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(brgb, orig, n, a.rgb_out);
-  return (int)cudaGetLastError();
+  L.gather = orig;
+  return launch_material(L, a.precision, s);
 }
 
 int launch_bin_eval(const BinArgs& a, void* stream) { return bin_eval(a, nullptr, (cudaStream_t)stream); }

@@ -361,6 +361,14 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
     ptx::tc_fence_after();
   };
 
+  // the query behind row k of the chunk table (binned launches read the
+  // caller's arrays through the binning permutation)
+  auto src = [&](int64_t k) -> int64_t {
+    if constexpr (MULTI) {
+      if (L.gather) return (int64_t)__ldg(L.gather + k);
+    }
+    return k;
+  };
   auto pyr_for = [&](const TileRef& t) -> const uint8_t* {
     return reinterpret_cast<const uint8_t*>(MULTI ? L.mats.pyramid[t.mat] : L.pyr0);
   };
@@ -371,12 +379,12 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
   if (c < c_end) {
     cur = tile_at(L, c);
     if (F16P && cur.count > 0) {
-      const QF q0 = load_qf(L.q, cur.start + (r < cur.count ? r : 0));
+      const QF q0 = load_qf(L.q, src(cur.start + (r < cur.count ? r : 0)));
       fetch_issue(L.pyr, pyr_for(cur), q0, stg);
     }
     if (c + NWG < c_end) {
       nxt = tile_at(L, c + NWG);
-      if (nxt.count > 0) q_nxt = load_qf(L.q, nxt.start + (r < nxt.count ? r : 0));
+      if (nxt.count > 0) q_nxt = load_qf(L.q, src(nxt.start + (r < nxt.count ? r : 0)));
     }
   }
   for (; c < c_end; c += NWG) {
@@ -389,7 +397,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
       if (F16P && has_next && nxt.count > 0) fetch_issue(L.pyr, pyr_for(nxt), q_nxt, stg);
       if (has_next2) {
         nxt2 = tile_at(L, c + 2 * NWG);
-        if (nxt2.count > 0) q_nxt2 = load_qf(L.q, nxt2.start + (r < nxt2.count ? r : 0));
+        if (nxt2.count > 0) q_nxt2 = load_qf(L.q, src(nxt2.start + (r < nxt2.count ? r : 0)));
       }
       cur = nxt;
       nxt = nxt2;
@@ -397,7 +405,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
       continue;
     }
     const bool valid = r < cur.count;
-    const int64_t i = cur.start + (valid ? r : 0);
+    const int64_t i = src(cur.start + (valid ? r : 0));
     // directions (used after the frame stages) and the masked-pass material
     // (issued here, ahead of the fetch and MMA 1, and kept here: a load the
     // compiler sinks to its first use would expose its full latency)
@@ -458,7 +466,7 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
     if (F16P && has_next && nxt.count > 0) fetch_issue(L.pyr, pyr_for(nxt), q_nxt, stg);
     if (has_next2) {
       nxt2 = tile_at(L, c + 2 * NWG);
-      if (nxt2.count > 0) q_nxt2 = load_qf(L.q, nxt2.start + (r < nxt2.count ? r : 0));
+      if (nxt2.count > 0) q_nxt2 = load_qf(L.q, src(nxt2.start + (r < nxt2.count ? r : 0)));
     }
     stage_wait();
 

@@ -83,6 +83,9 @@ struct LaunchCommon {
   const int32_t* row_ids;       // tensor-core kernel: if set, a chunk's row i
                                 // is stored only where row_ids[i] equals the
                                 // chunk's material (masked passes)
+  const int32_t* gather;        // tensor-core kernel, chunked launches: if set,
+                                // a chunk's row i is query gather[i] (its
+                                // fields read and its outputs written there)
   MatTable mats;         // single material: nmat = 1
   const void* pyr0;      // single material pyramid
   const void* w0;        // single material weight blob
