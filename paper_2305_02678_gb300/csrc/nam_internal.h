@@ -189,8 +189,9 @@ int launch_backward(const BackwardArgs& a, void* stream);
 // the evaluation launch for a material's precision (tensor-core or FP32 path)
 int launch_material(const LaunchCommon& L, int precision, void* stream);
 
-// Material binning (per-query material ids): count, plan, scatter into a
-// binned copy of the queries, one chunked launch, unbin the outputs.
+// Material binning (per-query material ids): count, plan, a permutation of
+// the query indices by material, one chunked launch that reads each query
+// through the permutation and writes its output in place.
 struct BinArgs {
   LaunchCommon L;          // caller's query pointers, flags, error word, materials table
   const int32_t* ids;      // [n] material of each query
