@@ -24,7 +24,9 @@
  * notes and restated at each function below.
  *
  * Pins: tests/test_oracle_pins*.py check every function here against closed
- * forms, invariants, library routines and brute force on tiny inputs.
+ * forms, invariants, library routines and brute force on tiny inputs.  The
+ * composed evaluation is parity unpinned end to end: the paper prints no
+ * worked example with values to compare against.
  */
 #include <math.h>
 #include <pthread.h>

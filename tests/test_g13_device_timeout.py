@@ -60,3 +60,35 @@ def test_short_wait_limit_reports_timeout_and_gpu_stays_usable(oracle, precision
     err = oracle.relative_error(g[:n], o)[0]
     assert np.isfinite(g).all()
     assert err <= (2e-3 if precision == B.NAM_PREC_F16 else 3e-2)
+
+
+def test_sampler_short_wait_limit_reports_timeout(oracle):
+    """The same for the tensor-core importance sampler: a 1 ns limit gives
+    NAM_ERR_TIMEOUT, and a context with the default limit then matches the
+    oracle's densities."""
+    import torch
+    from paper_2305_02678_gb300 import Context
+    from paper_2305_02678_gb300 import binding as B
+    W0, H0, L, pyr, model, q = _workload()
+    sampler = W.make_mlp(W.rng_streams(1302, 1)[0], (11, 32, 32, 32, 9))
+    dq = to_device(q)
+    n = len(q["u"])
+    out = torch.empty(n, device="cuda")
+    with Context(0, wait_timeout_ns=1) as short:
+        mat = short.material(W0, H0, L, pyr, model["frame"], model["decoder"], sampler=sampler)
+        for _ in range(3):
+            B.nam_sample_pdf(short.h, mat.h, dq, n, out)
+        with pytest.raises(B.NamError) as e:
+            short.check()
+        assert e.value.status == B.NAM_ERR_TIMEOUT
+        mat.destroy()
+    with Context(0) as ok:
+        mat = ok.material(W0, H0, L, pyr, model["frame"], model["decoder"], sampler=sampler)
+        B.nam_sample_pdf(ok.h, mat.h, dq, n, out)
+        ok.check()
+        g = out[:20000].cpu().numpy().astype(np.float64)
+        mat.destroy()
+    o = oracle.sampler_pdf(oracle.Model(W0, H0, L, pyr, model["frame"], model["decoder"]), sampler,
+                           W.slice_queries(q, 0, 20000))
+    rel = np.abs(g - o) / np.maximum(np.abs(o), 1e-3 * np.median(o))
+    assert np.isfinite(g).all() and np.percentile(rel, 99) < 1e-4
