@@ -363,7 +363,7 @@ nam_status nam_eval_binned(nam_ctx* ctx, const nam_material* mats, int32_t n_mat
  * untouched and makes nam_check_device_error report NAM_ERR_DEVICE_ASSERT)
  * and material requirements as nam_eval_binned.  Temporary device memory
  * (≈ 40 bytes per tile plus at most 16 bytes per query for the pass table,
- * the binning scratch of nam_eval_binned, and 16 bytes per material) comes
+ * the binning scratch of nam_eval_binned, and 20 bytes per material) comes
  * from the context's stream-ordered pool. */
 #define NAM_SELECT_MAX_PASSES 8
 nam_status nam_eval_select(nam_ctx* ctx, const nam_material* mats, int32_t n_materials, const nam_queries* q,

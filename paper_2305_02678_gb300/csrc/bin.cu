@@ -248,65 +248,59 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(const int32_t* __
 //                    to them) and run in material-coherent chunks: the
 //                    reordering the paper gets from SER (Sec. 7.3), which
 //                    here costs less than any per-thread path.
-// Three passes build the pass table in tile order: per-tile material lists
-// and per-group pass counts (one warp per tile, a group = one block's eight
-// tiles), an exclusive scan of the group counts (one block, which also
-// writes the table's length for the tensor-core kernel), and the table
-// itself; tile_k = -1 marks the tiles left to binning.
+// Three passes build the pass table grouped by material: per-tile material
+// lists and per-material pass counts (one warp per tile), an exclusive scan
+// of the counts (one block, which also writes the table's length for the
+// tensor-core kernel), and the table itself; tile_k = -1 marks the tiles
+// left to binning.
 constexpr int kTilesPerBlock = kThreads / 32;  // one tile per warp in the list pass
 constexpr int kWriteThreads = 256;             // one tile per thread in the write pass
 
+// One warp per tile: the tile's distinct materials in increasing order (at
+// most kSelectPasses; tile_k = -1 beyond), and one count per pass added to
+// its material's total.
 __global__ void __launch_bounds__(kThreads) select_tiles_kernel(const int32_t* __restrict__ ids, int64_t n,
                                                                 int nmat, int32_t* __restrict__ tile_k,
                                                                 int32_t* __restrict__ tile_mats,
-                                                                int32_t* __restrict__ block_sums, int* err) {
-  __shared__ int32_t sum;
-  if (threadIdx.x == 0) sum = 0;
-  __syncthreads();
+                                                                int32_t* __restrict__ mat_passes, int* err) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ntiles = (n + 127) / 128;
-  int32_t mine = 0;
-  for (int j = warp; j < kTilesPerBlock; j += kThreads / 32) {
-    const int64_t t = (int64_t)blockIdx.x * kTilesPerBlock + j;
-    if (t >= ntiles) break;  // uniform over the warp
-    const int64_t base = t * 128;
-    const int cnt = (int)(n - base < 128 ? n - base : 128);
-    int v[4];  // this lane's ids; INT_MAX once taken (or absent, or invalid)
+  const int64_t t = (int64_t)blockIdx.x * kTilesPerBlock + warp;
+  if (t >= ntiles) return;  // uniform over the warp
+  const int64_t base = t * 128;
+  const int cnt = (int)(n - base < 128 ? n - base : 128);
+  int v[4];  // this lane's ids; INT_MAX once taken (or absent, or invalid)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int r = lane + 32 * q;
-      v[q] = INT_MAX;
-      if (r < cnt) {
-        const int m = __ldg(ids + base + r);
-        if (m < 0 || m >= nmat) record_error(err, DEVERR_BOUNDS);
-        else v[q] = m;
-      }
-    }
-    // the tile's distinct materials in increasing order, at most kSelectPasses
-    int k = 0;
-    bool over = false;
-    for (;;) {
-      const int lm = min(min(v[0], v[1]), min(v[2], v[3]));
-      const int m = __reduce_min_sync(0xffffffffu, lm);
-      if (m == INT_MAX) break;
-      if (k == kSelectPasses) {
-        over = true;
-        break;
-      }
-      if (lane == 0) tile_mats[t * kSelectPasses + k] = m;
-      ++k;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (v[q] == m) v[q] = INT_MAX;
-    }
-    if (lane == 0) {
-      tile_k[t] = over ? -1 : k;
-      mine += over ? 0 : k;
+  for (int q = 0; q < 4; ++q) {
+    const int r = lane + 32 * q;
+    v[q] = INT_MAX;
+    if (r < cnt) {
+      const int m = __ldg(ids + base + r);
+      if (m < 0 || m >= nmat) record_error(err, DEVERR_BOUNDS);
+      else v[q] = m;
     }
   }
-  if (lane == 0 && mine) atomicAdd(&sum, mine);
-  __syncthreads();
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = sum;
+  int k = 0, mine = 0;  // mine: the material of this lane's pass (lane < k)
+  bool over = false;
+  for (;;) {
+    const int lm = min(min(v[0], v[1]), min(v[2], v[3]));
+    const int m = __reduce_min_sync(0xffffffffu, lm);
+    if (m == INT_MAX) break;
+    if (k == kSelectPasses) {
+      over = true;
+      break;
+    }
+    if (lane == k) mine = m;
+    if (lane == 0) tile_mats[t * kSelectPasses + k] = m;
+    ++k;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (v[q] == m) v[q] = INT_MAX;
+  }
+  if (lane == 0) tile_k[t] = over ? -1 : k;
+  // lane j counts the tile's pass j (same-address adds of one material
+  // from many tiles serialise in L2, a few thousand per frame)
+  if (!over && lane < k) atomicAdd(mat_passes + mine, 1);
 }
 
 // inclusive scan over a warp
@@ -320,48 +314,42 @@ __device__ __forceinline__ int32_t warp_scan(int32_t x) {
   return x;
 }
 
-// One block of 1024: block_offs = exclusive scan of block_sums; *total = sum.
-__global__ void __launch_bounds__(1024) select_scan_kernel(const int32_t* __restrict__ block_sums, int64_t nb,
-                                                           int32_t* __restrict__ block_offs,
+// One block of 1024: the material counts become cursors (exclusive scan, in
+// place) and *total their sum, the pass table's length.
+__global__ void __launch_bounds__(1024) select_scan_kernel(int32_t* __restrict__ counts, int nmat,
                                                            int32_t* __restrict__ total) {
   __shared__ int32_t wsum[32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int32_t carry = 0;
-  for (int64_t base = 0; base < nb; base += 1024) {
-    const int64_t i = base + threadIdx.x;
-    const int32_t v = i < nb ? block_sums[i] : 0;
+  for (int base = 0; base < nmat; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int32_t v = i < nmat ? counts[i] : 0;
     const int32_t x = warp_scan(v);
     if (lane == 31) wsum[warp] = x;
     __syncthreads();
     if (warp == 0) wsum[lane] = warp_scan(wsum[lane]);
     __syncthreads();
-    if (i < nb) block_offs[i] = carry + (warp ? wsum[warp - 1] : 0) + x - v;
+    if (i < nmat) counts[i] = carry + (warp ? wsum[warp - 1] : 0) + x - v;
     carry += wsum[31];
     __syncthreads();  // wsum is rewritten by the next iteration
   }
   if (threadIdx.x == 0) *total = carry;
 }
 
-// One thread per tile: the tile's passes at its offset (the group's offset
-// plus the passes of the group's earlier tiles); a tile left to binning has
-// none.
+// One thread per tile: each of its passes goes to the next slot of its
+// material's run, so that the pass table is grouped by material (a CTA's
+// range of it then meets few materials, and warpgroups share their weight
+// slots); the order inside a run does not change any result.  A tile left
+// to binning has no pass.
 __global__ void __launch_bounds__(kWriteThreads) select_write_kernel(const int32_t* __restrict__ tile_k,
                                                                      const int32_t* __restrict__ tile_mats,
-                                                                     int64_t n, const int32_t* __restrict__ block_offs,
+                                                                     int64_t n, int32_t* __restrict__ cursors,
                                                                      Chunk* __restrict__ passes) {
-  const int lane = threadIdx.x & 31;
   const int64_t ntiles = (n + 127) / 128;
   const int64_t t = (int64_t)blockIdx.x * kWriteThreads + threadIdx.x;
-  const int32_t kraw = t < ntiles ? __ldg(tile_k + t) : 0;
-  const int32_t k = kraw < 0 ? 0 : kraw;
-  int32_t x = k;  // inclusive scan inside the group of kTilesPerBlock lanes
-#pragma unroll
-  for (int o = 1; o < kTilesPerBlock; o <<= 1) {
-    const int32_t y = __shfl_up_sync(0xffffffffu, x, o, kTilesPerBlock);
-    if ((lane % kTilesPerBlock) >= o) x += y;
-  }
-  if (t >= ntiles || k == 0) return;
-  const int32_t o = block_offs[t / kTilesPerBlock] + x - k;
+  if (t >= ntiles) return;
+  const int32_t k = __ldg(tile_k + t);
+  if (k <= 0) return;
   const int64_t base = t * 128;
   const int cnt = (int)(n - base < 128 ? n - base : 128);
   for (int j = 0; j < k; ++j) {
@@ -369,7 +357,7 @@ __global__ void __launch_bounds__(kWriteThreads) select_write_kernel(const int32
     ch.start = base;
     ch.count = cnt;
     ch.material = __ldg(tile_mats + t * kSelectPasses + j);
-    passes[o + j] = ch;
+    passes[atomicAdd(cursors + ch.material, 1)] = ch;
   }
 }
 
@@ -428,12 +416,12 @@ static int bin_eval(const BinArgs& a, const int32_t* tile_k, cudaStream_t s) {
 int launch_bin_eval(const BinArgs& a, void* stream) { return bin_eval(a, nullptr, (cudaStream_t)stream); }
 
 // Scratch of a selection launch: tile_k [ntiles], tile_mats [ntiles][8],
-// group sums and offsets [nb] each, the pass count, the pass table (at most
-// one pass per query and kSelectPasses per tile), then the binning scratch
-// of the tiles left to binning (bin_scratch_bytes).
+// per material its pass count, then cursor [nmat], the pass count, the pass
+// table (at most one pass per query and kSelectPasses per tile), then the
+// binning scratch of the tiles left to binning (bin_scratch_bytes).
 namespace {
 struct SelectLayout {
-  size_t tile_k, tile_mats, sums, offs, total, passes, bin, bytes;
+  size_t tile_k, tile_mats, counts, total, passes, bin, bytes;
   int64_t ntiles, nb, cap;
 };
 SelectLayout select_layout(int64_t n, int nmat, bool xi) {
@@ -444,9 +432,8 @@ SelectLayout select_layout(int64_t n, int nmat, bool xi) {
   l.cap = l.ntiles * kSelectPasses < n ? l.ntiles * kSelectPasses : n;
   l.tile_k = 0;
   l.tile_mats = l.tile_k + r((size_t)l.ntiles * 4);
-  l.sums = l.tile_mats + r((size_t)l.ntiles * kSelectPasses * 4);
-  l.offs = l.sums + r((size_t)l.nb * 4);
-  l.total = l.offs + r((size_t)l.nb * 4);
+  l.counts = l.tile_mats + r((size_t)l.ntiles * kSelectPasses * 4);
+  l.total = l.counts + r((size_t)nmat * 4);
   l.passes = l.total + 256;
   l.bin = l.passes + r((size_t)l.cap * sizeof(Chunk));
   l.bytes = l.bin + bin_scratch_bytes(n, nmat, xi);
@@ -465,15 +452,16 @@ int launch_select_eval(const SelectArgs& a, void* stream) {
   uint8_t* p = (uint8_t*)a.scratch;
   int32_t* tile_k = (int32_t*)(p + l.tile_k);
   int32_t* tile_mats = (int32_t*)(p + l.tile_mats);
-  int32_t* sums = (int32_t*)(p + l.sums);
-  int32_t* offs = (int32_t*)(p + l.offs);
+  int32_t* counts = (int32_t*)(p + l.counts);
   int32_t* total = (int32_t*)(p + l.total);
   Chunk* passes = (Chunk*)(p + l.passes);
-  select_tiles_kernel<<<(int)l.nb, kThreads, 0, s>>>(a.ids, n, nmat, tile_k, tile_mats, sums, a.L.err);
-  select_scan_kernel<<<1, 1024, 0, s>>>(sums, l.nb, offs, total);
+  int e = (int)cudaMemsetAsync(counts, 0, (size_t)nmat * 4, s);
+  if (e) return e;
+  select_tiles_kernel<<<(int)l.nb, kThreads, 0, s>>>(a.ids, n, nmat, tile_k, tile_mats, counts, a.L.err);
+  select_scan_kernel<<<1, 1024, 0, s>>>(counts, nmat, total);
   select_write_kernel<<<(int)((l.ntiles + kWriteThreads - 1) / kWriteThreads), kWriteThreads, 0, s>>>(
-      tile_k, tile_mats, n, offs, passes);
-  int e = (int)cudaGetLastError();
+      tile_k, tile_mats, n, counts, passes);
+  e = (int)cudaGetLastError();
   if (e) return e;
   LaunchCommon L = a.L;
   L.chunks = passes;

@@ -241,20 +241,45 @@ __device__ __forceinline__ void fetch_finish(uint32_t stg, float z[8]) {
 // ---------------------------------------------------------------------------
 // kernel
 // ---------------------------------------------------------------------------
+// A launch that mixes materials keeps this many weight slots per CTA, shared
+// by its warpgroups: a warpgroup whose tile needs a material finds it in a
+// slot, or loads it into a slot no warpgroup is using.
+constexpr int kMultiSlots = 2;
+
 // Shared memory: constant block (1.0 in column 0 of every row) and zero block
-// (the A operand of the bias steps), the weight blob (one copy, or one per
-// warpgroup when a launch mixes materials), each warpgroup's fetch staging
-// (FP16 pyramids), then the mbarriers and the TMEM address slot.
+// (the A operand of the bias steps), the weight slots (one, or kMultiSlots
+// when a launch mixes materials), each warpgroup's fetch staging (FP16
+// pyramids), the mbarriers (one per warpgroup for its MMAs, one per slot for
+// its loads), the TMEM address, then the slot table: per slot its material,
+// users and load count, a lock, and one word per warpgroup to broadcast the
+// slot its leader acquired.
 template <int H, int FK, int NH, bool F16P, bool MULTI, int NWG>
 struct F16Smem {
   static constexpr F16Lay Y = f16_lay(H, FK, NH);
+  static constexpr int SLOTS = MULTI ? kMultiSlots : 1;
   static constexpr int BLOB_AL = (Y.BYTES + 127) / 128 * 128;
   static constexpr int W_OFF = 4096;
-  static constexpr int STG_OFF = W_OFF + (MULTI ? NWG : 1) * BLOB_AL;
+  static constexpr int STG_OFF = W_OFF + SLOTS * BLOB_AL;
   static constexpr int STG = F16P ? kStageBytes : 0;
   static constexpr int BAR_OFF = STG_OFF + NWG * STG;
-  static constexpr int BYTES = BAR_OFF + NWG * 16 + 16 + 16;
+  static constexpr int TSLOT_OFF = (BAR_OFF + 8 * (NWG + SLOTS) + 15) / 16 * 16;
+  static constexpr int TAB_OFF = TSLOT_OFF + 16;
+  static constexpr int BYTES = (TAB_OFF + 4 * (3 * SLOTS + 1 + NWG) + 15) / 16 * 16;
 };
+
+// A lock word in shared memory, taken with a time limit (false: not taken).
+__device__ __forceinline__ bool smem_lock(int* l, uint64_t t0, uint64_t timeout_ns) {
+  while (atomicCAS(l, 0, 1) != 0) {
+    if (ptx::globaltimer() - t0 > timeout_ns) return false;
+    __nanosleep(64);
+  }
+  __threadfence_block();
+  return true;
+}
+__device__ __forceinline__ void smem_unlock(int* l) {
+  __threadfence_block();
+  atomicExch(l, 0);
+}
 
 // TMEM columns of one warpgroup (H + 32):
 //   [0, H)        decoder accumulator (layer 1, hidden layers); later the low
@@ -279,19 +304,31 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
 
   const int tid = threadIdx.x, wg = tid >> 7, r = tid & 127, warp = tid >> 5;
   const uint32_t aConst = ptx::smem_u32(smem);
-  const uint32_t aW = ptx::smem_u32(smem + S::W_OFF + (MULTI ? wg * S::BLOB_AL : 0));
+  uint32_t aW = ptx::smem_u32(smem + S::W_OFF);  // the weight slot this warpgroup reads
   const uint32_t stg = ptx::smem_u32(smem + S::STG_OFF + wg * S::STG) + r * 16;  // this row's slot 0
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::BAR_OFF);
-  const uint32_t bar_m = ptx::smem_u32(&bars[2 * wg]);
-  const uint32_t bar_w = MULTI ? ptx::smem_u32(&bars[2 * wg + 1]) : ptx::smem_u32(&bars[2 * NWG]);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::BAR_OFF + NWG * 16 + 16);
+  const uint32_t bar_m = ptx::smem_u32(&bars[wg]);
+  const uint32_t bar_w = ptx::smem_u32(&bars[NWG]);  // slot 0's loads
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + S::TSLOT_OFF);
+  // slot table (mixed-material launches)
+  volatile int* slot_mat = reinterpret_cast<volatile int*>(smem + S::TAB_OFF);
+  volatile int* slot_users = slot_mat + S::SLOTS;
+  volatile int* slot_loads = slot_users + S::SLOTS;
+  int* slot_lock = const_cast<int*>(slot_loads + S::SLOTS);
+  volatile int* wg_word = slot_loads + S::SLOTS + 1;
   const uint32_t bar_id = 1 + wg;  // named barrier of this warpgroup
 
-  if (r == 0) {
-    ptx::mbar_init(bar_m, 1);
-    if (MULTI || tid == 0) ptx::mbar_init(bar_w, 1);
-    ptx::fence_mbar_init();
+  if (r == 0) ptx::mbar_init(bar_m, 1);
+  if (tid == 0) {
+    for (int k = 0; k < S::SLOTS; ++k) {
+      ptx::mbar_init(ptx::smem_u32(&bars[NWG + k]), 1);
+      slot_mat[k] = -1;
+      slot_users[k] = 0;
+      slot_loads[k] = 0;
+    }
+    *slot_lock = 0;
   }
+  if (r == 0) ptx::fence_mbar_init();
   if (warp == 0) {
     ptx::tmem_alloc(ptx::smem_u32(tslot), 512);
     ptx::tmem_relinquish();
@@ -317,9 +354,9 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
   const int64_t c_begin = (int64_t)blockIdx.x * per;
   const int64_t c_end = c_begin + per < ntiles ? c_begin + per : ntiles;
 
-  uint32_t ph_m = 0, ph_w = 0;
+  uint32_t ph_m = 0;
   bool bad = false, mma_pending = false, w_pending = false;
-  int cur_mat = -1;
+  int cur_mat = -1, my_slot = -1;
   const bool cosine = (L.flags & NAM_OUT_COSINE) != 0;
 
   // single material: one copy of the weights for the whole CTA
@@ -418,19 +455,63 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
     // restaged when the material changes (no MMA of the warpgroup in flight)
     if (MULTI) {
       if (cur.mat != cur_mat) {
+        // no MMA of this warpgroup is in flight: its leader gives up its
+        // slot and takes one holding the tile's material, or loads the
+        // material into a slot no warpgroup uses (waiting, with the time
+        // limit, while every slot is in use)
         if (ptx::bar_red_or(bar_id, 128, bad)) {
           bad = true;
           break;
         }
         if (r == 0) {
-          ptx::fence_proxy_async();
-          ptx::mbar_arrive_expect_tx(bar_w, Y.BYTES);
-          ptx::bulk_g2s(aW, L.mats.weights[cur.mat], Y.BYTES, bar_w);
+          const uint64_t t0 = ptx::globaltimer();
+          int sl = -1, gen = 0;
+          bool load = false, ok = smem_lock(slot_lock, t0, L.timeout_ns);
+          if (ok && my_slot >= 0) slot_users[my_slot] = slot_users[my_slot] - 1;
+          while (ok) {
+            for (int k = 0; k < S::SLOTS && sl < 0; ++k)
+              if (slot_mat[k] == cur.mat) {
+                sl = k;
+                slot_users[k] = slot_users[k] + 1;
+                gen = slot_loads[k];
+              }
+            for (int k = 0; k < S::SLOTS && sl < 0; ++k)
+              if (slot_users[k] == 0) {
+                sl = k;
+                load = true;
+                slot_mat[k] = cur.mat;
+                slot_users[k] = 1;
+                gen = slot_loads[k] + 1;
+                slot_loads[k] = gen;
+              }
+            smem_unlock(slot_lock);
+            if (sl >= 0) break;
+            __nanosleep(256);
+            ok = smem_lock(slot_lock, t0, L.timeout_ns);
+          }
+          if (load) {
+            const uint32_t bar = ptx::smem_u32(&bars[NWG + sl]);
+            ptx::fence_proxy_async();
+            ptx::mbar_arrive_expect_tx(bar, Y.BYTES);
+            ptx::bulk_g2s(ptx::smem_u32(smem + S::W_OFF + sl * S::BLOB_AL), L.mats.weights[cur.mat], Y.BYTES,
+                          bar);
+          }
+          wg_word[wg] = sl >= 0 ? (sl | (gen << 8)) : -1;
+          my_slot = sl;
         }
-        w_pending = true;
-        bad |= !ptx::mbar_wait(bar_w, ph_w, L.timeout_ns);
-        ph_w ^= 1;
-        if (!bad) w_pending = false;
+        // broadcast the slot (a failed acquire stops the warpgroup)
+        if (ptx::bar_red_or(bar_id, 128, false)) {
+          bad = true;
+          break;
+        }
+        const int word = wg_word[wg];
+        if (word < 0) {
+          bad = true;
+          break;
+        }
+        const int sl = word & 0xFF, gen = word >> 8;
+        aW = ptx::smem_u32(smem + S::W_OFF + sl * S::BLOB_AL);
+        bad |= !ptx::mbar_wait(ptx::smem_u32(&bars[NWG + sl]), (uint32_t)(gen - 1) & 1u, L.timeout_ns);
         cur_mat = cur.mat;
       }
     } else if (cur_mat < 0) {
@@ -745,11 +826,23 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
   // No cp.async may land in shared memory after the CTA exits; MMAs and bulk
   // copies still in flight after a wait gave up are waited for with the fixed
   // drain limit, and TMEM is freed only if they all completed.
+  // a warpgroup leaving its loop gives up its weight slot
+  if (MULTI && r == 0 && my_slot >= 0 && smem_lock(slot_lock, ptx::globaltimer(), L.timeout_ns)) {
+    slot_users[my_slot] = slot_users[my_slot] - 1;
+    smem_unlock(slot_lock);
+  }
   ptx::cp_async_wait_all();
   bool drained = true;
   if (r == 0 && mma_pending) drained &= ptx::mbar_wait(bar_m, ph_m ^ 1, ptx::kDrainTimeoutNs);
-  if (MULTI && r == 0 && w_pending) drained &= ptx::mbar_wait(bar_w, ph_w ^ 1, ptx::kDrainTimeoutNs);
   if (!MULTI && tid == 0 && w_pending) drained &= ptx::mbar_wait(bar_w, 0, ptx::kDrainTimeoutNs);
+  if (MULTI) {
+    __syncthreads();  // every warpgroup has left its loop: no slot is loaded after this
+    if (tid == 0)
+      for (int k = 0; k < S::SLOTS; ++k)
+        if (slot_loads[k] > 0)
+          drained &= ptx::mbar_wait(ptx::smem_u32(&bars[NWG + k]), (uint32_t)(slot_loads[k] - 1) & 1u,
+                                    ptx::kDrainTimeoutNs);
+  }
   if (bad) record_error(L.err, DEVERR_WAIT_TIMEOUT);
   if (!drained) record_error(L.err, DEVERR_DRAIN_TIMEOUT);
   ptx::tc_fence_before();
@@ -769,13 +862,8 @@ constexpr int kF16Nwg = 5;
 
 template <int H, int FK, int NH, bool F16P, bool MULTI>
 constexpr int f16_nwg() {
-  // A launch that mixes materials keeps one weight copy per warpgroup.  With
-  // five, shared memory leaves 60 KB of the SM's L1 for the texel gathers and
-  // its launch took 2.1x a single-material launch over as many tiles; the
-  // whole binned call for 16 materials drawn per pixel at 1080p took
-  // 0.41 ms with five warpgroups, 0.31 ms with four (92 KB of L1), 0.33 ms
-  // with three
-  if (MULTI) return kF16Nwg - 1;
+  // five warpgroups where the shared memory allows (the largest blobs with
+  // their staging leave room for four)
   return F16Smem<H, FK, NH, F16P, MULTI, kF16Nwg>::BYTES <= 227 * 1024 ? kF16Nwg : kF16Nwg - 1;
 }
 
