@@ -23,8 +23,9 @@
 // instead of the tensor core measured slower: their SIMT instructions cost
 // more than the MMA round trips they save.)
 // Latency hiding: the texel gathers of the next tile go to shared memory with
-// cp.async while the current tile's MMAs run, and each warpgroup's tile is
-// independent of the others'.
+// cp.async while the current tile's first MMA runs, and (single-material
+// launches) are filtered while its output MMA runs, z of the next tile then
+// waiting in registers; each warpgroup's tile is independent of the others'.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -413,11 +414,16 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
   int64_t c = c_begin + wg;
   TileRef cur{}, nxt{};
   QF q_nxt{};
+  // single-material launches filter the next tile while the output MMA runs
+  // (mixed-material launches, short of registers, filter at the tile's start)
+  constexpr bool SHADOW = F16P && !MULTI;
+  float zr[8];  // filtered latent of the tile about to start (SHADOW)
   if (c < c_end) {
     cur = tile_at(L, c);
     if (F16P && cur.count > 0) {
       const QF q0 = load_qf(L.q, src(cur.start + (r < cur.count ? r : 0)));
       fetch_issue(L.pyr, pyr_for(cur), q0, stg);
+      if (SHADOW) fetch_finish(stg, zr);
     }
     if (c + NWG < c_end) {
       nxt = tile_at(L, c + NWG);
@@ -431,7 +437,10 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
     QF q_nxt2{};
     if (cur.count <= 0) {
       // an empty slot of a chunk table (count is uniform over the warpgroup)
-      if (F16P && has_next && nxt.count > 0) fetch_issue(L.pyr, pyr_for(nxt), q_nxt, stg);
+      if (F16P && has_next && nxt.count > 0) {
+        fetch_issue(L.pyr, pyr_for(nxt), q_nxt, stg);
+        if (SHADOW) fetch_finish(stg, zr);
+      }
       if (has_next2) {
         nxt2 = tile_at(L, c + 2 * NWG);
         if (nxt2.count > 0) q_nxt2 = load_qf(L.q, src(nxt2.start + (r < nxt2.count ? r : 0)));
@@ -522,7 +531,11 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
 
     // ---- 1. latent z, split into FP16 halves -> MMA 1 ---------------------
     float z[8];
-    if (F16P) {
+    if (SHADOW) {
+      // filtered while the previous tile's output MMA ran
+#pragma unroll
+      for (int k = 0; k < 8; ++k) z[k] = zr[k];
+    } else if (F16P) {
       fetch_finish(stg, z);
     } else {
       QF q0 = load_qf(L.q, i);
@@ -781,6 +794,8 @@ __global__ void __launch_bounds__(NWG * 128, 1) eval_f16_kernel(const LaunchComm
             ptx::mma_f16_ts(tB + C::OUT, tB + C::LO + 8 * s, ptx::sdesc(aW + Y.BO + s * 512, 256, 128), ID16, 1u);
         }))
       break;
+    // the next tile's filter, while the output MMA runs
+    if (SHADOW && has_next && nxt.count > 0) fetch_finish(stg, zr);
     stage_wait();
 
     // ---- output ---------------------------------------------------------------
