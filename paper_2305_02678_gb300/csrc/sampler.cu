@@ -246,10 +246,14 @@ __global__ void __launch_bounds__(NWG * 128, 1)
   int64_t c = c_begin + wg;
   QF q_nxt{};
   bool w_ready = false;
+  float zr[8];  // filtered latent of the tile about to start (FP16 pyramids)
   if (c < c_end) {
     const int64_t i0 = c * 128 + r;
     const QF q0 = load_qf(L.q, i0 < L.n ? i0 : L.n - 1);
-    if (F16P) fetch_issue(L.pyr, reinterpret_cast<const uint8_t*>(L.pyr0), q0, stg);
+    if (F16P) {
+      fetch_issue(L.pyr, reinterpret_cast<const uint8_t*>(L.pyr0), q0, stg);
+      fetch_finish(stg, zr);
+    }
     if (c + NWG < c_end) {
       const int64_t i1 = (c + NWG) * 128 + r;
       q_nxt = load_qf(L.q, i1 < L.n ? i1 : L.n - 1);
@@ -270,7 +274,9 @@ __global__ void __launch_bounds__(NWG * 128, 1)
     // ---- layer 1 input (z, wi, 1) as (hi, lo) ------------------------------
     float x[16];
     if (F16P) {
-      fetch_finish(stg, x);
+      // filtered while the previous tile's last layer ran
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = zr[k];
     } else {
       const QF q0 = load_qf(L.q, i);
       fetch_latent<false>(L.pyr, L.pyr0, q0.u, q0.v, q0.lod, q0.xi, x);
@@ -312,6 +318,8 @@ __global__ void __launch_bounds__(NWG * 128, 1)
     stage_wait();
     hidden_operand();
     if (!stage_issue([&] { layer_mmas(kSA4, kSL4, 16, ID16); })) break;
+    // the next tile's filter, while the last layer runs
+    if (F16P && has_next) fetch_finish(stg, zr);
     stage_wait();
     // ---- proxy parameters, density or sample --------------------------------
     float o[9];
