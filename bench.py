@@ -719,7 +719,9 @@ def run_binned(ctx, dev, stream, flush, w, dq, n, args, n_mat=16):
         best[upd], reg[upd] = d[upd], k
     tiles = np.pad(reg, (0, (-n) % 128), mode="edge").reshape(-1, 128)
     coherent = float(np.mean(np.all(tiles == tiles[:, :1], axis=1)))
-    passes = float(np.mean([np.unique(t).size for t in tiles]))
+    kt = np.array([np.unique(t).size for t in tiles])
+    passes = float(np.mean(kt))
+    binned_tiles = float(np.mean(kt > B.NAM_SELECT_MAX_PASSES))
     rids = torch.from_numpy(reg).to(dev)
     t_sel = statistics.fmean(time_launches(lambda: B.nam_eval_select(ctx.h, handles, dq, rids, n, o, stream, 0),
                                            reps, 2, flush, stream))
@@ -738,12 +740,13 @@ def run_binned(ctx, dev, stream, flush, w, dq, n, args, n_mat=16):
                 "per_pixel_ms": round(t_sel_pp, 4), "per_pixel_vs_binned": round(t_sel_pp / t, 3),
                 "regions_workload": f"{n_mat} screen regions (nearest of {n_mat} random sites), "
                                     f"{coherent:.3f} of the 128-query tiles coherent, "
-                                    f"{passes:.3f} tensor-core passes per tile",
+                                    f"{passes:.3f} materials per tile",
+                "regions_tiles_binned_by_select": round(binned_tiles, 3),
                 "regions_select_ms": round(t_sel, 4), "regions_binned_ms": round(t_bin_reg, 4),
-                "note": "nam_eval_select, in place: a 128-query tile with k <= 8 materials runs as k masked "
-                        "tensor-core passes (one per material); the queries of tiles with more are binned by "
-                        "material (the binning passes limited to those tiles) and run in coherent chunks; three "
-                        "small passes build the pass table"}}
+                "note": f"nam_eval_select, in place: a 128-query tile with k <= {B.NAM_SELECT_MAX_PASSES} "
+                        "materials runs as k tensor-core passes (one per material); the queries of tiles with "
+                        "more are binned by material (the binning passes limited to those tiles) and run in "
+                        "coherent chunks; three small passes build the pass table"}}
 
 
 def run_scene(ctx, dev, stream, args, width=1920, height=1080):

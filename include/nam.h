@@ -346,26 +346,27 @@ nam_status nam_eval_binned(nam_ctx* ctx, const nam_material* mats, int32_t n_mat
  * caller's order).  A pass over material_ids lists each tile's distinct
  * materials:
  *   1 to NAM_SELECT_MAX_PASSES  one tensor-core pass over the tile per
- *       material, each storing only the rows of its own material (the way
- *       SIMT divergence runs a warp once per branch target, at tensor-core
- *       speed); every such query's result is bitwise that of nam_eval on its
- *       material;
+ *       material, each storing only the rows of its own material; every
+ *       such query's result is bitwise that of nam_eval on its material;
  *   more  the queries of all such tiles are binned by material (the
  *       passes of nam_eval_binned, limited to those tiles: the reordering
  *       the paper's renderer gets from SER, Sec. 7.3) and run in
- *       material-coherent 128-query chunks, then written back in place;
- *       every such query's result is likewise bitwise that of nam_eval on
- *       its material.
+ *       material-coherent 128-query chunks, their results written in
+ *       place; every such query's result is likewise bitwise that of
+ *       nam_eval on its material.
+ * NAM_SELECT_MAX_PASSES is 1: a tile whose queries share one material is
+ * one pass (the coherent path), every other tile is binned, which costs
+ * less than running even two masked passes over it.
  * So every result equals nam_eval's on the query's material; only the cost
  * differs: coherent ids (screen tiles of a few surfaces) move no query,
  * incoherent ones cost about what nam_eval_binned does.  Arguments, id
  * checks (an id outside [0, n_materials) leaves that query's rgb_out
  * untouched and makes nam_check_device_error report NAM_ERR_DEVICE_ASSERT)
  * and material requirements as nam_eval_binned.  Temporary device memory
- * (≈ 40 bytes per tile plus at most 16 bytes per query for the pass table,
+ * (24 bytes per tile: its material list and its entry of the pass table;
  * the binning scratch of nam_eval_binned, and 20 bytes per material) comes
  * from the context's stream-ordered pool. */
-#define NAM_SELECT_MAX_PASSES 8
+#define NAM_SELECT_MAX_PASSES 1
 nam_status nam_eval_select(nam_ctx* ctx, const nam_material* mats, int32_t n_materials, const nam_queries* q,
                            const int32_t* material_ids, int64_t n, float* rgb_out, void* stream, uint32_t flags);
 

@@ -332,7 +332,7 @@ def nam_eval_multi(ctx, mats, q, items, rgb_out, stream=None, flags=0):
 
 
 NAM_MAX_BIN_MATERIALS = 4096
-NAM_SELECT_MAX_PASSES = 8
+NAM_SELECT_MAX_PASSES = 1
 
 
 def nam_eval_binned(ctx, mats, q, material_ids, n, rgb_out, stream=None, flags=0):

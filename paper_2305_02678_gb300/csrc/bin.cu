@@ -237,17 +237,19 @@ __global__ void __launch_bounds__(kThreads) bin_scatter_kernel(const int32_t* __
 // path for coherent and one for divergent execution).  A tcgen05 MMA covers
 // the 128 rows of a CTA's tile, so the choice is made per 128-query tile, in
 // place (no query moves):
-//   k = 1 material   one tensor-core pass (the coherent path);
-//   2 <= k <= 8      k tensor-core passes over the whole tile, one per
-//                    material, each storing only its own material's rows:
-//                    SIMT divergence serialises a warp over its branch
-//                    targets, and these passes serialise a tile over its
-//                    materials the same way, at tensor-core speed;
-//   k > 8            the tile's queries are binned by material with those of
-//                    the other such tiles (the binning passes above, limited
-//                    to them) and run in material-coherent chunks: the
-//                    reordering the paper gets from SER (Sec. 7.3), which
-//                    here costs less than any per-thread path.
+//   k <= kSelectPasses   k tensor-core passes over the whole tile, one per
+//                        material, each storing only its own material's
+//                        rows (SIMT divergence serialises a warp over its
+//                        branch targets the same way); k = 1 is the
+//                        coherent path;
+//   k > kSelectPasses    the tile's queries are binned by material with those
+//                        of the other such tiles (the binning passes above,
+//                        limited to them) and run in material-coherent
+//                        chunks: the reordering the paper gets from SER
+//                        (Sec. 7.3).
+// With kSelectPasses = 1 every tile of two or more materials is binned:
+// even two masked passes over a tile cost more tensor-core time than the
+// binning of its queries.
 // Three passes build the pass table grouped by material: per-tile material
 // lists and per-material pass counts (one warp per tile), an exclusive scan
 // of the counts (one block, which also writes the table's length for the
@@ -415,7 +417,7 @@ static int bin_eval(const BinArgs& a, const int32_t* tile_k, cudaStream_t s) {
 
 int launch_bin_eval(const BinArgs& a, void* stream) { return bin_eval(a, nullptr, (cudaStream_t)stream); }
 
-// Scratch of a selection launch: tile_k [ntiles], tile_mats [ntiles][8],
+// Scratch of a selection launch: tile_k [ntiles], tile_mats [ntiles][kSelectPasses],
 // per material its pass count, then cursor [nmat], the pass count, the pass
 // table (at most one pass per query and kSelectPasses per tile), then the
 // binning scratch of the tiles left to binning (bin_scratch_bytes).
@@ -467,6 +469,8 @@ int launch_select_eval(const SelectArgs& a, void* stream) {
   L.chunks = passes;
   L.n_chunks = (int32_t)l.cap;
   L.n_chunks_dev = total;
+  // a pass stores only the rows of its material: the other materials of
+  // its tile, and ids out of range, are left alone
   L.row_ids = a.ids;
   e = launch_material(L, a.precision, stream);
   if (e) return e;

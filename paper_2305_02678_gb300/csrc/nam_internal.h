@@ -210,8 +210,9 @@ int launch_bin_eval(const BinArgs& a, void* stream);
 // queries with k <= kSelectPasses distinct materials runs as k tensor-core
 // passes (one per material, each storing its own material's rows); the
 // queries of tiles with more are binned by material and run in
-// material-coherent chunks.
-constexpr int kSelectPasses = 8;
+// material-coherent chunks.  One pass per tile at most: tiles of two or
+// more materials are binned (cheaper than two or more masked passes).
+constexpr int kSelectPasses = NAM_SELECT_MAX_PASSES;
 struct SelectArgs {
   LaunchCommon L;              // caller's queries, rgb, n, flags, materials table
   const int32_t* ids;          // [n] material of each query
