@@ -273,6 +273,41 @@ def test_host_path_pipelined_chunks_identical(gctx, w2, precision, n):
     gctx.check()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tile_partition_invariance(gctx, w2, precision):
+    """A query's value must not depend on how a launch spreads its tiles
+    over CTAs and warpgroups: which tile a warpgroup takes next, whether it
+    has a next tile whose texels it filters while the current tile's last
+    MMA runs, how many tiles a CTA gets.  Prefixes that end at and around
+    the partition boundaries of this GPU (tiles = warpgroups x SMs, +- one
+    tile or query), and windows that start inside a tile (so every query
+    moves to another row of another tile), give bitwise the values of the
+    whole batch."""
+    import torch
+    m = w2["model"]
+    nfull = 400_000
+    q = W.slice_queries(w2["queries"], 0, nfull)
+    mat = gctx.material(w2["W0"], w2["H0"], w2["L"], w2["pyramid"], m["frame"], m["decoder"], precision=precision)
+    dq = to_device(q)
+    full = mat.eval(dq).cpu().numpy()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sizes = set()
+    for tiles in (1, 4, 5, 6, sms, 4 * sms, 5 * sms - 1, 5 * sms, 5 * sms + 1, 10 * sms + 3):
+        for d in (-1, 0, 1):
+            n = tiles * 128 + d
+            if 0 < n <= nfull:
+                sizes.add(n)
+    for n in sorted(sizes):
+        out = mat.eval({k: v[:n] for k, v in dq.items()}).cpu().numpy()
+        assert np.array_equal(out, full[:n]), n
+    for off in (1, 64, 127):
+        n = 5 * sms * 128 + 77
+        out = mat.eval({k: v[off:off + n].contiguous() for k, v in dq.items()}).cpu().numpy()
+        assert np.array_equal(out, full[off:off + n]), off
+    mat.destroy()
+    gctx.check()
+
+
 def test_multi_material_matches_single(gctx, oracle):
     """Work items over several materials give bit-identical results to
     evaluating each item's queries with its material alone."""

@@ -134,6 +134,45 @@ def test_gpu_samples_follow_the_density(gctx, oracle):
     mat.destroy()
 
 
+def test_tile_partition_invariance(gctx):
+    """Densities and samples do not depend on how the launch spreads tiles
+    over CTAs and warpgroups (the next tile filtered while the current
+    tile's last layer runs, or not, at the end of a warpgroup's range):
+    prefixes around this GPU's partition boundaries, and a window that
+    starts inside a tile, give bitwise the values of the whole batch."""
+    import torch
+    from paper_2305_02678_gb300 import binding as B
+    nfull = 200_000
+    W0, H0, L, pyr, model, sampler, q, u = _setup(67, nfull)
+    mat = gctx.material(W0, H0, L, pyr, model["frame"], model["decoder"], sampler=sampler)
+    dq = to_device(q)
+    du = torch.from_numpy(u).cuda()
+
+    def run(lo, n):
+        d = {k: v[lo:lo + n].contiguous() for k, v in dq.items()}
+        pdf = torch.empty(n, device="cuda")
+        wo = torch.empty((n, 3), device="cuda")
+        pdf2 = torch.empty(n, device="cuda")
+        B.nam_sample_pdf(gctx.h, mat.h, d, n, pdf)
+        B.nam_sample(gctx.h, mat.h, d, n, du[lo:lo + n].contiguous(), wo, pdf2)
+        return pdf.cpu().numpy(), wo.cpu().numpy(), pdf2.cpu().numpy()
+
+    full = run(0, nfull)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for tiles in (1, 5, 6, 5 * sms - 1, 5 * sms, 5 * sms + 1):
+        for d in (-1, 0, 1):
+            n = tiles * 128 + d
+            if 0 < n <= nfull:
+                got = run(0, n)
+                for a, b in zip(got, full):
+                    assert np.array_equal(a, b[:n]), n
+    got = run(37, 5 * sms * 128 + 5)
+    for a, b in zip(got, full):
+        assert np.array_equal(a, b[37:37 + len(a)])
+    mat.destroy()
+    gctx.check()
+
+
 def test_sampler_errors(gctx):
     import torch
     from paper_2305_02678_gb300 import binding as B
