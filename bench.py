@@ -680,8 +680,10 @@ def run_binned(ctx, dev, stream, flush, w, dq, n, args, n_mat=16):
     """Per-query material ids with no tile coherence: 16 FP16 materials (the
     1080p pyramid, seeded decoders and frame MLPs of their own), a uniformly
     random material per pixel, evaluated through nam_eval_binned (device
-    histogram, scan, scatter into material ranges, one chunked launch,
-    unbin); against the single-material launch of the headline."""
+    histogram, scan, a permutation of the query indices by material, one
+    chunked launch that reads through it and writes in place); against the
+    single-material launch of the headline; then per-tile selection on the
+    same ids and both on 16 screen regions."""
     import torch
 
     import workloads as W
@@ -700,8 +702,8 @@ def run_binned(ctx, dev, stream, flush, w, dq, n, args, n_mat=16):
     t1 = statistics.fmean(time_launches(lambda: B.nam_eval(ctx.h, mats[0].h, dq, n, o, stream, 0),
                                         max(3, args.steps // 2), 2, flush, stream))
     reps = max(3, args.steps // 2)
-    # per-tile selection on the same per-pixel ids: every tile holds more
-    # than 8 of the 16 materials, so every query goes through binning
+    # per-tile selection on the same per-pixel ids: every tile holds several
+    # of the 16 materials, so every query goes through binning
     t_sel_pp = statistics.fmean(time_launches(lambda: B.nam_eval_select(ctx.h, handles, dq, ids, n, o, stream, 0),
                                               reps, 2, flush, stream))
     # screen regions: the pixels of the 1920x1080 frame (queries in row-major
